@@ -1,0 +1,172 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) phase-field WMRT lattice Boltzmann
+ * library: the fused per-timestep update of the conservative Allen-Cahn
+ * populations g and the pressure-based hydrodynamic populations f on D2Q9
+ * and D3Q19 (arXiv 2505.12205, Sec. 3.2, Algorithms 1-3, App. A and B).
+ *
+ * Conventions shared by every entry point
+ *  - Lattice units: dx = dt = c = 1, c_s^2 = 1/3; phi_L = 0 (light fluid),
+ *    phi_H = 1 (heavy fluid).
+ *  - Fields are float32 arrays [nz][ny][nx] with x fastest (nz = 1 in 2D).
+ *    A velocity is D consecutive planes (u_x, u_y[, u_z]).  Populations are
+ *    population-major [Q][nz][ny][nx] (Q = 9 or 19) in the velocity order of
+ *    the momentum rows of eq:A1 (D2Q9) and eq:A2 (D3Q19).
+ *  - Buffers passed in are owned by the caller; the library copies from or
+ *    into them and never keeps a pointer.  When on_device is non-zero the
+ *    pointers are CUDA device pointers of the context's device (for example
+ *    torch.Tensor.data_ptr()); otherwise they are host pointers.
+ *  - All work is enqueued on the context's stream.  lbm_step returns once
+ *    its kernels are enqueued; calls that return data to the host
+ *    synchronise the stream.
+ *  - Every call returns an lbm_status.  Nothing aborts or exits; the text of
+ *    the last error of a context is available from lbm_last_error.
+ *  - There is no CPU fallback: without a CUDA device lbm_create fails with
+ *    LBM_ERR_CUDA.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;   /* opaque; owns all device memory */
+
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
+
+/* Face conditions, App. B: periodic (eq:periodic_f/g/phi), halfway
+ * bounce-back wall (eq:no_slip_f/g), velocity + phase-field inlet
+ * (eq:velocity_boundary_distribution, eq:unknown_distribution_*), convective
+ * outlet (eq:convective_f/g).  The inlet is allowed only on the low face and
+ * the outlet only on the high face of the last axis (y in 2D, z in 3D). */
+typedef enum {
+    LBM_BC_PERIODIC = 0,
+    LBM_BC_WALL = 1,
+    LBM_BC_INLET = 2,
+    LBM_BC_OUTFLOW = 3
+} lbm_bc;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,      /* invalid argument or parameter */
+    LBM_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+    LBM_ERR_OOM = -3,      /* device allocation failed */
+    LBM_ERR_DIVERGED = -4, /* non-finite populations found by lbm_diag */
+    LBM_ERR_STATE = -6     /* call out of order (e.g. step before init) */
+} lbm_status;
+
+/* Problem statement of Sec. 3 of the paper.
+ *  lattice      lbm_lattice; nx, ny, nz grid (nz = 1 for D2Q9)
+ *  bc[6]        lbm_bc of the faces -x, +x, -y, +y, -z, +z (z ignored in 2D)
+ *  visc_model   0: dynamic viscosity linear in phi (eq:dynamic_viscosity),
+ *                  tau = mu(phi) / (rho(phi) c_s^2), mu_X = rho_X tau_X c_s^2;
+ *               1: relaxation time linear in phi (eq:relaxation_time)
+ *  storage      population storage precision: 0 = float32 (the only value
+ *               accepted by this version)
+ *  rho_L, rho_H densities (eq:density_interpolation)
+ *  tau_L, tau_H relaxation times, nu = tau c_s^2 (eq:kinematic_viscosity)
+ *  sigma, W     surface tension and interface width xi
+ *               (eq:beta_kappa_relation)
+ *  mobility     M = tau_phi c_s^2 (eq:mobility_relation)
+ *  force[3]     body-force acceleration g; F_b = (rho - rho_ref) g
+ *               (eq:gravity_force); force[2] is ignored in 2D
+ *  rho_ref      reference density of the body force
+ *  inlet_u      plug speed u_j along the inward normal of the inlet face
+ *  inlet_center nozzle centre (x[, y]) in the inlet plane
+ *  inlet_radius nozzle radius (2D: half width of the slot); the inlet
+ *               profile is phi_in = 1/2 + 1/2 tanh(2 (R - r) / W), u_in = u_j
+ *               for r < R and 0 elsewhere.
+ */
+typedef struct {
+    int32_t lattice, nx, ny, nz;
+    int32_t bc[6];
+    int32_t visc_model;
+    int32_t storage;
+    double rho_L, rho_H, tau_L, tau_H;
+    double sigma, W, mobility;
+    double force[3];
+    double rho_ref;
+    double inlet_u;
+    double inlet_center[2];
+    double inlet_radius;
+} lbm_params;
+
+/* FP64 diagnostics of the current state (lbm_diag). */
+typedef struct {
+    double sum_phi;    /* sum of phi over all nodes (mass, Sec. 5.4) */
+    double sum_p_in;   /* sum of p = p* rho c_s^2 over nodes with phi >= 1 - eps */
+    double sum_p_out;  /* sum of p over nodes with phi <= eps */
+    double max_speed;  /* max |u| */
+    int64_t n_in, n_out;
+    int32_t finite;    /* 1 if every population is finite */
+    int32_t reserved;
+} lbm_diag_out;
+
+/* Create a context: validate p, allocate the double-buffered population
+ * planes (2 sets x 2 buffers x Q x nx*ny*nz float32) on the current CUDA
+ * device and bind the CUDA stream `stream` (a cudaStream_t; NULL = the legacy
+ * default stream).  Errors: LBM_ERR_ARG (out == NULL, a parameter out of
+ * range, unpaired periodic faces, inlet/outlet on another face, last axis
+ * shorter than 4 with open faces), LBM_ERR_CUDA (no device), LBM_ERR_OOM.
+ * On failure *out is NULL. */
+int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out);
+
+/* Set the state to the equilibria of the given fields (eq:equilibrium,
+ * eq:equilibrium_function): g_a = phi Gamma_a(u), f_a = p* w_a + Gamma_a(u)
+ * - w_a.  phi: [N]; u: [D][N] or NULL (zero); pstar: [N] or NULL (zero),
+ * p* = p / (rho c_s^2). */
+int lbm_init_fields(lbm_ctx* ctx, const float* phi, const float* u, const float* pstar,
+                    int on_device);
+
+/* Advance nsteps >= 0 time steps (collision, streaming, boundary conditions
+ * and macroscopic update of Algorithms 1-3, fused).  Asynchronous.
+ * Errors: LBM_ERR_STATE before lbm_init_fields / lbm_set_populations. */
+int lbm_step(lbm_ctx* ctx, int64_t nsteps);
+
+/* Macroscopic fields of the current state, computed with the same device
+ * code as the step: phi [N], u [D][N] (eq:velocity_update), p [N]
+ * (p = p* rho c_s^2).  Any output may be NULL.  Synchronises when on_device
+ * is 0. */
+int lbm_get_fields(lbm_ctx* ctx, float* phi, float* u, float* p, int on_device);
+
+/* Raw state (checkpoint): the post-streaming populations f and g, each
+ * [Q][N] float32.  lbm_set_populations restores it exactly. */
+int lbm_get_populations(lbm_ctx* ctx, float* f, float* g, int on_device);
+int lbm_set_populations(lbm_ctx* ctx, const float* f, const float* g, int on_device);
+
+/* FP64 reductions of the current state (deterministic order): sum phi, the
+ * pressure sums inside (phi >= 1 - phase_eps) and outside (phi <= phase_eps)
+ * for the Laplace test (eq:laplace_law), max |u| and a finite check.
+ * Synchronises.  Returns LBM_ERR_DIVERGED (with *out filled) when a
+ * population is not finite. */
+int lbm_diag(lbm_ctx* ctx, double phase_eps, lbm_diag_out* out);
+
+/* Wait for all work enqueued on the context's stream. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Number of nodes N = nx*ny*nz and populations Q of a context. */
+int lbm_shape(const lbm_ctx* ctx, int64_t* n_nodes, int32_t* q);
+
+/* Text of the last error of ctx (never NULL; "" if none).  With ctx == NULL,
+ * the last error of a failed lbm_create on this thread. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Free all device memory of ctx (after synchronising its stream). */
+int lbm_destroy(lbm_ctx* ctx);
+
+/* Test hook: macroscopic update and collision of n independent cells with
+ * the device code of the step (Algorithm 1 with eq:mrt_collision in moment
+ * space).  Device pointers: f, g [n][Q] post-stream populations; phin
+ * [n][Q] = phi(x + e_a) of each cell; fs, gs [n][Q] outputs; out [n][5] =
+ * {phi, u_x, u_y, u_z, p} (may be NULL).  Uses the physical parameters of p;
+ * the grid and faces of p are ignored.  Synchronises the stream. */
+int lbm_collide_cells(const lbm_params* p, int64_t n, const float* f, const float* g,
+                      const float* phin, float* fs, float* gs, float* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

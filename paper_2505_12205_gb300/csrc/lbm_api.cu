@@ -1,0 +1,329 @@
+// C ABI of the phase-field WMRT lattice Boltzmann library (declared in
+// include/lbm.h): parameter validation, device memory, stream binding and
+// dispatch to the per-lattice kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_kernels.cuh"
+
+extern template struct lbm::Launch<lbm::D2Q9>;
+extern template struct lbm::Launch<lbm::D3Q19>;
+
+using lbm::D2Q9;
+using lbm::D3Q19;
+using lbm::DevParams;
+using lbm::DiagPartial;
+using lbm::Launch;
+
+struct lbm_ctx {
+    lbm_params p;
+    DevParams dp;
+    int Q, D;
+    int64_t N;
+    cudaStream_t stream;
+    int device;
+    lbm::Buffers b;
+    float* face = nullptr;          // phi_in, u_in of the inlet plane
+    DiagPartial* diag_part = nullptr;
+    DiagPartial* diag_res = nullptr;
+    int diag_nparts = 0;
+    bool initialised = false;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static int fail(lbm_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+static int cuda_fail(lbm_ctx* c, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+}
+
+#define LBM_CUDA(ctx, call)                                              \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);       \
+    } while (0)
+
+static int validate(const lbm_params* p, std::string& why)
+{
+    if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) { why = "lattice must be 0 (D2Q9) or 1 (D3Q19)"; return -1; }
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) { why = "grid sizes must be >= 1"; return -1; }
+    if (p->lattice == LBM_D2Q9 && p->nz != 1) { why = "D2Q9 needs nz == 1"; return -1; }
+    if (p->nx > 65535 * 128 || p->ny > 65535 || p->nz > 65535) { why = "grid too large for the launch shape"; return -1; }
+    if (!(p->rho_L > 0 && p->rho_H > 0 && p->tau_L > 0 && p->tau_H > 0)) { why = "rho_L, rho_H, tau_L, tau_H must be > 0"; return -1; }
+    if (!(p->W > 0 && p->mobility > 0 && p->sigma >= 0)) { why = "W, mobility must be > 0 and sigma >= 0"; return -1; }
+    if (p->visc_model != 0 && p->visc_model != 1) { why = "visc_model must be 0 or 1"; return -1; }
+    if (p->storage != 0) { why = "storage must be 0 (float32)"; return -1; }
+    const int D = p->lattice == LBM_D2Q9 ? 2 : 3, L = D - 1;
+    const int n[3] = {p->nx, p->ny, p->nz};
+    for (int d = 0; d < D; ++d) {
+        const int lo = p->bc[2 * d], hi = p->bc[2 * d + 1];
+        if (lo < 0 || lo > 3 || hi < 0 || hi > 3) { why = "face condition out of range"; return -1; }
+        if ((lo == LBM_BC_PERIODIC) != (hi == LBM_BC_PERIODIC)) { why = "periodic faces must be paired"; return -1; }
+        if (lo == LBM_BC_OUTFLOW || hi == LBM_BC_INLET) { why = "inlet only on a low face, outlet only on a high face"; return -1; }
+        if (d != L && (lo >= LBM_BC_INLET || hi >= LBM_BC_INLET)) { why = "inlet/outlet only on the last axis"; return -1; }
+    }
+    if ((p->bc[2 * L] >= LBM_BC_INLET || p->bc[2 * L + 1] >= LBM_BC_INLET) && n[L] < 4) {
+        why = "open faces need at least 4 nodes along the last axis";
+        return -1;
+    }
+    if (p->bc[2 * L] == LBM_BC_INLET && !(p->inlet_radius >= 0)) { why = "inlet_radius must be >= 0"; return -1; }
+    return 0;
+}
+
+static DevParams make_dev(const lbm_params* p, int64_t N)
+{
+    DevParams d;
+    std::memset(&d, 0, sizeof d);
+    d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
+    for (int i = 0; i < 6; ++i) d.bc[i] = p->bc[i];
+    if (p->lattice == LBM_D2Q9) d.bc[4] = d.bc[5] = LBM_BC_PERIODIC;
+    d.visc_model = p->visc_model;
+    d.N = N;
+    d.rho_L = float(p->rho_L); d.rho_H = float(p->rho_H);
+    d.tau_L = float(p->tau_L); d.tau_H = float(p->tau_H);
+    d.mu_L = float(p->rho_L * p->tau_L / 3.0); d.mu_H = float(p->rho_H * p->tau_H / 3.0);
+    d.beta = float(12.0 * p->sigma / p->W);
+    d.kappa = float(1.5 * p->sigma * p->W);
+    d.inv_W = float(1.0 / p->W);
+    d.omega_phi = float(1.0 / (3.0 * p->mobility + 0.5));
+    d.gx = float(p->force[0]); d.gy = float(p->force[1]);
+    d.gz = p->lattice == LBM_D2Q9 ? 0.0f : float(p->force[2]);
+    d.rho_ref = float(p->rho_ref);
+    return d;
+}
+
+template <class L>
+static cudaError_t dispatch_step(lbm_ctx* c)
+{
+    cudaError_t e = Launch<L>::step(c->dp, c->b, c->stream);
+    std::swap(c->b.fA, c->b.fB);
+    std::swap(c->b.gA, c->b.gB);
+    return e;
+}
+
+extern "C" {
+
+int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, LBM_ERR_ARG, "params is NULL");
+    std::string why;
+    if (validate(p, why) != 0) return fail(nullptr, LBM_ERR_ARG, why);
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return fail(nullptr, LBM_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ERR_OOM, "host allocation failed");
+    c->p = *p;
+    c->Q = p->lattice == LBM_D2Q9 ? 9 : 19;
+    c->D = p->lattice == LBM_D2Q9 ? 2 : 3;
+    c->N = int64_t(p->nx) * p->ny * p->nz;
+    c->stream = static_cast<cudaStream_t>(stream);
+    cudaGetDevice(&c->device);
+    c->dp = make_dev(p, c->N);
+
+    const size_t plane = size_t(c->N) * c->Q * sizeof(float);
+    float** bufs[4] = {&c->b.fA, &c->b.gA, &c->b.fB, &c->b.gB};
+    for (float** b : bufs) {
+        e = cudaMalloc(reinterpret_cast<void**>(b), plane);
+        if (e != cudaSuccess) {
+            int r = cuda_fail(nullptr, e, "cudaMalloc(populations)");
+            lbm_destroy(c);
+            return r;
+        }
+    }
+    e = cudaMalloc(reinterpret_cast<void**>(&c->b.phi), size_t(c->N) * sizeof(float));
+    const int nface = c->D == 2 ? p->nx : p->nx * p->ny;
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&c->face), 2 * size_t(nface) * sizeof(float));
+    c->diag_nparts = 2 * 152;
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&c->diag_part), (c->diag_nparts + 1) * sizeof(DiagPartial));
+    if (e != cudaSuccess) {
+        int r = cuda_fail(nullptr, e, "cudaMalloc");
+        lbm_destroy(c);
+        return r;
+    }
+    c->diag_res = c->diag_part + c->diag_nparts;
+    c->dp.phi_in = c->face;
+    c->dp.u_in = c->face + nface;
+    const int L = c->D - 1;
+    if (p->bc[2 * L] == LBM_BC_INLET) {
+        e = c->D == 2 ? Launch<D2Q9>::inlet_profile(c->dp, p->inlet_center[0], 0.0, p->inlet_radius, p->W,
+                                                     p->inlet_u, c->face, c->face + nface, c->stream)
+                      : Launch<D3Q19>::inlet_profile(c->dp, p->inlet_center[0], p->inlet_center[1],
+                                                      p->inlet_radius, p->W, p->inlet_u, c->face,
+                                                      c->face + nface, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            int r = cuda_fail(nullptr, e, "inlet profile");
+            lbm_destroy(c);
+            return r;
+        }
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx* c)
+{
+    if (!c) return LBM_OK;
+    if (c->stream || true) cudaStreamSynchronize(c->stream);
+    cudaFree(c->b.fA); cudaFree(c->b.gA); cudaFree(c->b.fB); cudaFree(c->b.gB);
+    cudaFree(c->b.phi); cudaFree(c->face); cudaFree(c->diag_part);
+    delete c;
+    return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c)
+{
+    return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+int lbm_shape(const lbm_ctx* c, int64_t* n_nodes, int32_t* q)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (n_nodes) *n_nodes = c->N;
+    if (q) *q = c->Q;
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx* c)
+{
+    if (!c) return LBM_ERR_ARG;
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_ctx* c, const float* phi, const float* u, const float* pstar, int on_device)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (!phi) return fail(c, LBM_ERR_ARG, "phi is NULL");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t nb = size_t(c->N) * sizeof(float);
+    // stage the fields in the B planes (Q >= D + 2 planes of N floats)
+    float* s_phi = c->b.fB;
+    float* s_u = c->b.fB + c->N;
+    float* s_p = c->b.fB + c->N * (1 + c->D);
+    LBM_CUDA(c, cudaMemcpyAsync(s_phi, phi, nb, kind, c->stream));
+    if (u) LBM_CUDA(c, cudaMemcpyAsync(s_u, u, nb * c->D, kind, c->stream));
+    if (pstar) LBM_CUDA(c, cudaMemcpyAsync(s_p, pstar, nb, kind, c->stream));
+    cudaError_t e = c->D == 2 ? Launch<D2Q9>::init(c->dp, s_phi, u ? s_u : nullptr, pstar ? s_p : nullptr, c->b.fA, c->b.gA, c->stream)
+                              : Launch<D3Q19>::init(c->dp, s_phi, u ? s_u : nullptr, pstar ? s_p : nullptr, c->b.fA, c->b.gA, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->initialised = true;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int64_t nsteps)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps < 0");
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_fields/lbm_set_populations");
+    for (int64_t s = 0; s < nsteps; ++s) {
+        cudaError_t e = c->D == 2 ? dispatch_step<D2Q9>(c) : dispatch_step<D3Q19>(c);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step kernels");
+    }
+    return LBM_OK;
+}
+
+int lbm_get_fields(lbm_ctx* c, float* phi, float* u, float* p, int on_device)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
+    // outputs are computed into the B planes, then copied out
+    float* o_phi = c->b.fB;
+    float* o_u = c->b.fB + c->N;
+    float* o_p = c->b.fB + c->N * (1 + c->D);
+    cudaError_t e = c->D == 2 ? Launch<D2Q9>::fields(c->dp, c->b, o_phi, o_u, o_p, c->stream)
+                              : Launch<D3Q19>::fields(c->dp, c->b, o_phi, o_u, o_p, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fields kernel");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t nb = size_t(c->N) * sizeof(float);
+    if (phi) LBM_CUDA(c, cudaMemcpyAsync(phi, o_phi, nb, kind, c->stream));
+    if (u) LBM_CUDA(c, cudaMemcpyAsync(u, o_u, nb * c->D, kind, c->stream));
+    if (p) LBM_CUDA(c, cudaMemcpyAsync(p, o_p, nb, kind, c->stream));
+    if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx* c, float* f, float* g, int on_device)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t nb = size_t(c->N) * c->Q * sizeof(float);
+    if (f) LBM_CUDA(c, cudaMemcpyAsync(f, c->b.fA, nb, kind, c->stream));
+    if (g) LBM_CUDA(c, cudaMemcpyAsync(g, c->b.gA, nb, kind, c->stream));
+    if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx* c, const float* f, const float* g, int on_device)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (!f || !g) return fail(c, LBM_ERR_ARG, "f and g are required");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t nb = size_t(c->N) * c->Q * sizeof(float);
+    LBM_CUDA(c, cudaMemcpyAsync(c->b.fA, f, nb, kind, c->stream));
+    LBM_CUDA(c, cudaMemcpyAsync(c->b.gA, g, nb, kind, c->stream));
+    if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->initialised = true;
+    return LBM_OK;
+}
+
+int lbm_diag(lbm_ctx* c, double phase_eps, lbm_diag_out* out)
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
+    cudaError_t e = c->D == 2 ? Launch<D2Q9>::diag(c->dp, c->b, phase_eps, c->diag_part, c->diag_nparts, c->diag_res, c->stream)
+                              : Launch<D3Q19>::diag(c->dp, c->b, phase_eps, c->diag_part, c->diag_nparts, c->diag_res, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "diag kernels");
+    DiagPartial r;
+    LBM_CUDA(c, cudaMemcpyAsync(&r, c->diag_res, sizeof r, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    out->sum_phi = r.sum_phi;
+    out->sum_p_in = r.sum_p_in;
+    out->sum_p_out = r.sum_p_out;
+    out->max_speed = r.max_speed;
+    out->n_in = r.n_in;
+    out->n_out = r.n_out;
+    out->finite = r.nonfinite ? 0 : 1;
+    out->reserved = 0;
+    if (r.nonfinite) return fail(c, LBM_ERR_DIVERGED, "non-finite populations");
+    return LBM_OK;
+}
+
+int lbm_collide_cells(const lbm_params* p, int64_t n, const float* f, const float* g, const float* phin,
+                      float* fs, float* gs, float* out, void* stream)
+{
+    if (!p || n < 0 || (n > 0 && (!f || !g || !phin || !fs || !gs)))
+        return fail(nullptr, LBM_ERR_ARG, "invalid arguments to lbm_collide_cells");
+    if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) return fail(nullptr, LBM_ERR_ARG, "bad lattice");
+    DevParams d = make_dev(p, 1);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = p->lattice == LBM_D2Q9 ? Launch<D2Q9>::collide_cells(d, n, f, g, phin, fs, gs, out, s)
+                                           : Launch<D3Q19>::collide_cells(d, n, f, g, phin, fs, gs, out, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "collide cells");
+    return LBM_OK;
+}
+
+}  // extern "C"

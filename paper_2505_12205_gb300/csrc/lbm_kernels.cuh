@@ -1,0 +1,644 @@
+// sm_103a kernels of the phase-field WMRT lattice Boltzmann step.
+//
+// State: post-streaming populations f, g in population-major planes
+// pop[a * N + node], node = (z * ny + y) * nx + x, double-buffered (A = current
+// state, B = next state).  One time step (Algorithms 1-3 of the paper, fused):
+//   k_phi      phi = sum_a g_a (eq:phase_field_variable) of the state in A;
+//   k_step     per node: isotropic stencils of phi (eq:gradient_phi,
+//              eq:laplacian_phi), material properties, chemical potential,
+//              forces, velocity, g-collision (eq:lbe_interface), f-collision in
+//              moment space (eq:mrt_collision), then push-streaming into B with
+//              periodic wrap and halfway bounce-back (App. B);
+//   k_inlet    velocity + phase-field inlet on the inlet plane of B;
+//   k_outlet   convective outlet on the outlet plane of B (reads A and B).
+// The host swaps A and B after each step.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lbm_lattice.cuh"
+
+namespace lbm {
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTFLOW = 3 };
+
+// Parameters as the kernels use them (float32 arithmetic), passed by value.
+struct DevParams {
+    int nx, ny, nz;
+    int bc[6];
+    int visc_model;
+    int64_t N;             // nodes
+    float rho_L, rho_H, tau_L, tau_H, mu_L, mu_H;
+    float beta, kappa;     // eq:beta_kappa_relation
+    float inv_W;           // 1 / xi
+    float omega_phi;       // 1 / (tau_phi + 1/2), tau_phi = M / c_s^2
+    float gx, gy, gz, rho_ref;
+    // inlet plane profile (face arrays, precomputed in double on the device)
+    const float* phi_in;
+    const float* u_in;
+};
+
+// ------------------------------------------------------------ node physics
+
+template <class L>
+__device__ __forceinline__ float gamma_a(int a, float ux, float uy, float uz, float uu)
+{
+    // eq:dimensionless_distribution
+    const float eu = float(L::ex(a)) * ux + float(L::ey(a)) * uy + float(L::ez(a)) * uz;
+    return L::w(a) * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
+}
+
+// Macroscopic update and collision of one node.  f, g: post-stream
+// populations (overwritten with the post-collision ones when collide);
+// phin[a] = phi(x + e_a).  out (may be null): phi, u_x, u_y, u_z, p.
+template <class L, bool collide>
+__device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q], float (&g)[L::Q],
+                                            const float (&phin)[L::Q], float* out)
+{
+    constexpr int Q = L::Q;
+    float phi = 0.0f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) phi += g[a];
+
+    // eq:gradient_phi, eq:laplacian_phi (c / (c_s^2 dx) = 3, 2 c^2 / (c_s^2 dx^2) = 6)
+    float dx = 0.0f, dy = 0.0f, dz = 0.0f, lap = 0.0f;
+#pragma unroll
+    for (int a = 1; a < Q; ++a) {
+        const float wp = 3.0f * L::w(a) * phin[a];
+        if (L::ex(a)) dx += float(L::ex(a)) * wp;
+        if (L::ey(a)) dy += float(L::ey(a)) * wp;
+        if (L::ez(a)) dz += float(L::ez(a)) * wp;
+        lap += L::w(a) * (phin[a] - phin[0]);
+    }
+    lap *= 6.0f;
+
+    // phi clamped inside the material properties only
+    const float ph = fminf(fmaxf(phi, 0.0f), 1.0f);
+    const float rho = P.rho_L + ph * (P.rho_H - P.rho_L);      // eq:density_interpolation
+    float tau;
+    if (P.visc_model == 1) tau = P.tau_L + ph * (P.tau_H - P.tau_L);   // eq:relaxation_time
+    else tau = (P.mu_L + ph * (P.mu_H - P.mu_L)) / (rho * (1.0f / 3.0f));  // eq:dynamic_viscosity
+    const float s_nu = 1.0f / (tau + 0.5f);
+
+    // chemical potential (sign reading: 4 beta (phi - phi_L)(phi - phi_H)(phi - phi_0))
+    const float mu_phi = 4.0f * P.beta * phi * (phi - 1.0f) * (phi - 0.5f) - P.kappa * lap;
+
+    float pstar = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        pstar += f[a];
+        if (L::ex(a)) jx += float(L::ex(a)) * f[a];
+        if (L::ey(a)) jy += float(L::ey(a)) * f[a];
+        if (L::ez(a)) jz += float(L::ez(a)) * f[a];
+    }
+    const float drho = P.rho_H - P.rho_L;                     // eq:density_gradient_phase_field
+    const float rx = drho * dx, ry = drho * dy, rz = drho * dz;
+    const float cp = -pstar * (1.0f / 3.0f);                  // eq:pressure_force
+    const float fb = rho - P.rho_ref;                          // eq:gravity_force
+    float Fx = mu_phi * dx + cp * rx + fb * P.gx;              // F_s + F_p + F_b
+    float Fy = mu_phi * dy + cp * ry + fb * P.gy;
+    float Fz = mu_phi * dz + cp * rz + fb * P.gz;
+    const float h_rho = 0.5f / rho;
+
+    // viscous force (eq:viscous_force_wmrt) with the predictor velocity
+    {
+        const float u0x = jx + Fx * h_rho, u0y = jy + Fy * h_rho, u0z = jz + Fz * h_rho;
+        const float uu0 = u0x * u0x + u0y * u0y + u0z * u0z;
+        float dn[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a)
+            dn[a] = f[a] - (pstar * L::w(a) + gamma_a<L>(a, u0x, u0y, u0z, uu0) - L::w(a));
+        float ck[L::NS];
+#pragma unroll
+        for (int k = 0; k < L::NS; ++k) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int a = 0; a < Q; ++a)
+                if (L::m(k, a)) acc += float(L::m(k, a)) * dn[a];
+            ck[k] = (1.0f - s_nu) * acc;
+        }
+        float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
+#pragma unroll
+        for (int a = 1; a < Q; ++a) {
+            float md = dn[a];
+#pragma unroll
+            for (int k = 0; k < L::NS; ++k)
+                if (L::m(k, a)) md -= L::rw(k, a) * ck[k];
+            const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+            if (ex) pxx += md;
+            if (ey) pyy += md;
+            if (ez) pzz += md;
+            if (ex * ey) pxy += float(ex * ey) * md;
+            if (ex * ez) pxz += float(ex * ez) * md;
+            if (ey * ez) pyz += float(ey * ez) * md;
+        }
+        // nu / c_s^2 = tau
+        Fx -= tau * (pxx * rx + pxy * ry + pxz * rz);
+        Fy -= tau * (pxy * rx + pyy * ry + pyz * rz);
+        Fz -= tau * (pxz * rx + pyz * ry + pzz * rz);
+    }
+    if (L::D == 2) Fz = 0.0f;
+
+    // eq:velocity_update
+    const float ux = jx + Fx * h_rho, uy = jy + Fy * h_rho, uz = (L::D == 2) ? 0.0f : jz + Fz * h_rho;
+    const float uu = ux * ux + uy * uy + uz * uz;
+
+    if (out) {
+        out[0] = phi;
+        out[1] = ux;
+        out[2] = uy;
+        out[3] = uz;
+        out[4] = pstar * rho * (1.0f / 3.0f);
+    }
+    if (!collide) return;
+
+    // g: eq:forcing_term, eq:equilibrium_function, eq:equilibrium_with_force,
+    // eq:lbe_interface; n = 0 where |grad phi| < 1e-12
+    {
+        const float gn2 = dx * dx + dy * dy + dz * dz;
+        const float amp = (gn2 >= 1e-24f) ? (1.0f - 4.0f * (phi - 0.5f) * (phi - 0.5f)) * P.inv_W * rsqrtf(gn2) : 0.0f;
+        const float nx = amp * dx, ny = amp * dy, nz = amp * dz;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float Fphi = L::w(a) * (float(L::ex(a)) * nx + float(L::ey(a)) * ny + float(L::ez(a)) * nz);
+            const float geq = phi * gamma_a<L>(a, ux, uy, uz, uu);
+            g[a] = g[a] - P.omega_phi * (g[a] - geq + 0.5f * Fphi) + Fphi;
+        }
+    }
+    // f: eq:force_term, eq:equilibrium, eq:equilibrium_modified, eq:mrt_collision
+    {
+        const float ir = 3.0f / rho;
+        float dl[Q], Fa[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            Fa[a] = L::w(a) * ir * (float(L::ex(a)) * Fx + float(L::ey(a)) * Fy + float(L::ez(a)) * Fz);
+            const float feq = pstar * L::w(a) + gamma_a<L>(a, ux, uy, uz, uu) - L::w(a);
+            dl[a] = f[a] - feq + 0.5f * Fa[a];
+        }
+        float ck[L::NS];
+#pragma unroll
+        for (int k = 0; k < L::NS; ++k) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int a = 0; a < Q; ++a)
+                if (L::m(k, a)) acc += float(L::m(k, a)) * dl[a];
+            ck[k] = (1.0f - s_nu) * acc;
+        }
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            float proj = 0.0f;
+#pragma unroll
+            for (int k = 0; k < L::NS; ++k)
+                if (L::m(k, a)) proj += L::rw(k, a) * ck[k];
+            f[a] = f[a] - (dl[a] - proj) + Fa[a];
+        }
+    }
+}
+
+// ----------------------------------------------------------- face mapping
+
+// Neighbour coordinate along one axis for the phi stencil: periodic -> wrap,
+// wall/outlet -> clamp (zero normal gradient), inlet -> flag (phi_in).
+__device__ __forceinline__ int map_phi(int v, int n, int bclo, int bchi, bool& inlet)
+{
+    if (v < 0) {
+        if (bclo == BC_PERIODIC) return v + n;
+        if (bclo == BC_INLET) inlet = true;
+        return 0;
+    }
+    if (v >= n) {
+        if (bchi == BC_PERIODIC) return v - n;
+        return n - 1;
+    }
+    return v;
+}
+
+// Push target along one axis: kind 0 = inside (maybe wrapped), 1 = wall,
+// 2 = open face (population leaves the domain).
+__device__ __forceinline__ int map_push(int v, int n, int bclo, int bchi, int& kind)
+{
+    if (v < 0) {
+        if (bclo == BC_PERIODIC) return v + n;
+        kind = max(kind, bclo == BC_WALL ? 2 : 1);
+        return 0;
+    }
+    if (v >= n) {
+        if (bchi == BC_PERIODIC) return v - n;
+        kind = max(kind, bchi == BC_WALL ? 2 : 1);
+        return n - 1;
+    }
+    return v;
+}
+
+// ---------------------------------------------------------------- kernels
+
+template <class L>
+__global__ void __launch_bounds__(128) k_phi(const __grid_constant__ DevParams P,
+                                             const float* __restrict__ g, float* __restrict__ phi)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    float s = 0.0f;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) s += __ldg(g + a * P.N + i);
+    phi[i] = s;
+}
+
+template <class L>
+__device__ __forceinline__ void gather_phi(const DevParams& P, const float* __restrict__ phi, int x, int y,
+                                           int z, float (&phin)[L::Q])
+{
+    const int lastax = L::D - 1;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+        bool inlet = false;
+        const int xx = map_phi(x + L::ex(a), P.nx, P.bc[0], P.bc[1], inlet);
+        const int yy = map_phi(y + L::ey(a), P.ny, P.bc[2], P.bc[3], inlet);
+        const int zz = (L::D == 3) ? map_phi(z + L::ez(a), P.nz, P.bc[4], P.bc[5], inlet) : 0;
+        if (inlet) {
+            const int fidx = (lastax == 1) ? xx : (yy * P.nx + xx);
+            phin[a] = P.phi_in[fidx];
+        } else {
+            phin[a] = __ldg(phi + (int64_t(zz) * P.ny + yy) * P.nx + xx);
+        }
+    }
+}
+
+template <class L>
+__global__ void __launch_bounds__(128) k_step(const __grid_constant__ DevParams P,
+                                              const float* __restrict__ fA, const float* __restrict__ gA,
+                                              const float* __restrict__ phi, float* __restrict__ fB,
+                                              float* __restrict__ gB)
+{
+    constexpr int Q = L::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= P.nx) return;
+    const int64_t N = P.N;
+    const int64_t node = (int64_t(z) * P.ny + y) * P.nx + x;
+
+    float f[Q], g[Q], phin[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        f[a] = __ldg(fA + a * N + node);
+        g[a] = __ldg(gA + a * N + node);
+    }
+    gather_phi<L>(P, phi, x, y, z, phin);
+    node_update<L, true>(P, f, g, phin, nullptr);
+
+    // push streaming (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g)
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        int kind = 0;
+        const int xx = map_push(x + L::ex(a), P.nx, P.bc[0], P.bc[1], kind);
+        const int yy = map_push(y + L::ey(a), P.ny, P.bc[2], P.bc[3], kind);
+        const int zz = (L::D == 3) ? map_push(z + L::ez(a), P.nz, P.bc[4], P.bc[5], kind) : 0;
+        if (kind == 0) {
+            const int64_t t = (int64_t(zz) * P.ny + yy) * P.nx + xx;
+            fB[a * N + t] = f[a];
+            gB[a * N + t] = g[a];
+        } else if (kind == 2) {               // wall: back to this node, opposite slot
+            fB[L::opp(a) * N + node] = f[a];
+            gB[L::opp(a) * N + node] = g[a];
+        }                                      // open face: leaves the domain
+    }
+}
+
+// Velocity inlet (f) and phase-field inlet (g) on the low face of the last
+// axis, applied to the post-streaming populations in B (App. B; the force
+// shift is omitted at the inlet, p* cancels, the tangential excess momentum
+// is shared by the two unknowns that carry each tangential component, the
+// phase excess by the unknowns with a tangential component).
+template <class L>
+__global__ void k_inlet(const __grid_constant__ DevParams P, float* __restrict__ fB, float* __restrict__ gB)
+{
+    constexpr int Q = L::Q;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
+    if (t >= nface) return;
+    const int64_t N = P.N;
+    const int64_t node = t;                    // last-axis coordinate 0
+    const float phin = P.phi_in[t], un = P.u_in[t];
+    const float ux = 0.0f, uy = (L::D == 2) ? un : 0.0f, uz = (L::D == 3) ? un : 0.0f;
+    const float uu = un * un;
+    float f[Q], g[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        f[a] = fB[a * N + node];
+        g[a] = gB[a * N + node];
+    }
+    float Mx = 0.0f, My = 0.0f, theta = 0.0f;
+    int ndiag = 0;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
+        const int t0 = L::ex(a), t1 = (L::D == 2) ? 0 : L::ey(a);
+        if (en == 0) {
+            const float G = gamma_a<L>(a, ux, uy, uz, uu);
+            const float fneq = f[a] - (G - L::w(a));
+            if (t0) Mx += float(t0) * fneq;
+            if (t1) My += float(t1) * fneq;
+            theta += g[a] - phin * G;          // eq:excess_density
+        } else if (en > 0 && (t0 != 0 || t1 != 0)) {
+            ++ndiag;
+        }
+    }
+    const float th_n = theta / float(ndiag);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
+        if (en <= 0) continue;
+        const int t0 = L::ex(a), t1 = (L::D == 2) ? 0 : L::ey(a);
+        const int ab = L::opp(a);
+        const float Ga = gamma_a<L>(a, ux, uy, uz, uu), Gb = gamma_a<L>(ab, ux, uy, uz, uu);
+        const float eM = float(t0) * Mx + float(t1) * My;
+        fB[a * N + node] = f[ab] + (Ga - Gb) - 0.5f * eM;      // eq:velocity_boundary_distribution
+        const float corr = (t0 != 0 || t1 != 0) ? th_n : 0.0f;
+        gB[a * N + node] = phin * Ga - (g[ab] - phin * Gb) - corr;   // eq:unknown_distribution_*
+    }
+}
+
+// Convective outlet on the high face of the last axis (eq:implicit_convective,
+// eq:convective_f/g): chi(N, t+1) = (chi(N, t) + lambda chi(N-1, t+1)) / (1 + lambda),
+// lambda = clamp(sum_a f_a e_a.n at layer N-1 after streaming, 0, 1).
+template <class L>
+__global__ void k_outlet(const __grid_constant__ DevParams P, const float* __restrict__ fA,
+                         const float* __restrict__ gA, float* __restrict__ fB, float* __restrict__ gB)
+{
+    constexpr int Q = L::Q;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
+    if (t >= nface) return;
+    const int64_t N = P.N;
+    const int nL = (L::D == 2) ? P.ny : P.nz;
+    const int64_t iN = int64_t(nL - 1) * nface + t, iM = int64_t(nL - 2) * nface + t;
+    float U = 0.0f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
+        if (en) U += float(en) * fB[a * N + iM];
+    }
+    const float lam = fminf(fmaxf(U, 0.0f), 1.0f);
+    const float inv = 1.0f / (1.0f + lam);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        fB[a * N + iN] = (fA[a * N + iN] + lam * fB[a * N + iM]) * inv;
+        gB[a * N + iN] = (gA[a * N + iN] + lam * gB[a * N + iM]) * inv;
+    }
+}
+
+// Inlet-plane profile, computed once in double so that the nozzle mask is the
+// same decision as a double-precision reference makes.
+template <class L>
+__global__ void k_inlet_profile(int nface, int nx, double cx, double cy, double R, double W, double uj,
+                                float* phi_in, float* u_in)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nface) return;
+    double r;
+    if (L::D == 2) {
+        r = fabs(double(t) - cx);
+    } else {
+        const double dx = double(t % nx) - cx, dy = double(t / nx) - cy;
+        r = sqrt(dx * dx + dy * dy);
+    }
+    phi_in[t] = float(0.5 + 0.5 * tanh(2.0 * (R - r) / W));
+    u_in[t] = float(r < R ? uj : 0.0);
+}
+
+// Equilibrium initialisation from float32 fields (eq:equilibrium,
+// eq:equilibrium_function).
+template <class L>
+__global__ void k_init(const __grid_constant__ DevParams P, const float* __restrict__ phi,
+                       const float* __restrict__ u, const float* __restrict__ pstar, float* __restrict__ f,
+                       float* __restrict__ g)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    const float ux = u ? u[i] : 0.0f, uy = u ? u[P.N + i] : 0.0f;
+    const float uz = (u && L::D == 3) ? u[2 * P.N + i] : 0.0f;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    const float ps = pstar ? pstar[i] : 0.0f, ph = phi[i];
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+        const float G = gamma_a<L>(a, ux, uy, uz, uu);
+        g[a * P.N + i] = ph * G;
+        f[a * P.N + i] = ps * L::w(a) + (G - L::w(a));
+    }
+}
+
+// Macroscopic fields of the state in A (same device code as the step).
+template <class L>
+__global__ void __launch_bounds__(128) k_fields(const __grid_constant__ DevParams P,
+                                                const float* __restrict__ fA, const float* __restrict__ gA,
+                                                const float* __restrict__ phi, float* __restrict__ ophi,
+                                                float* __restrict__ ou, float* __restrict__ op)
+{
+    constexpr int Q = L::Q;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= P.nx) return;
+    const int64_t N = P.N;
+    const int64_t node = (int64_t(z) * P.ny + y) * P.nx + x;
+    float f[Q], g[Q], phin[Q], out[5];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        f[a] = fA[a * N + node];
+        g[a] = gA[a * N + node];
+    }
+    gather_phi<L>(P, phi, x, y, z, phin);
+    node_update<L, false>(P, f, g, phin, out);
+    if (ophi) ophi[node] = out[0];
+    if (ou) {
+        ou[node] = out[1];
+        ou[N + node] = out[2];
+        if (L::D == 3) ou[2 * N + node] = out[3];
+    }
+    if (op) op[node] = out[4];
+}
+
+// Per-block FP64 partial reductions for lbm_diag.
+struct DiagPartial {
+    double sum_phi, sum_p_in, sum_p_out, max_speed;
+    long long n_in, n_out;
+    int nonfinite;
+    int pad;
+};
+
+template <class L>
+__global__ void __launch_bounds__(256) k_diag(const __grid_constant__ DevParams P,
+                                              const float* __restrict__ fA, const float* __restrict__ gA,
+                                              const float* __restrict__ phi, double eps,
+                                              DiagPartial* __restrict__ part)
+{
+    constexpr int Q = L::Q;
+    __shared__ double s_phi[256], s_pin[256], s_pout[256], s_max[256];
+    __shared__ long long s_nin[256], s_nout[256];
+    __shared__ int s_bad[256];
+    double a_phi = 0.0, a_pin = 0.0, a_pout = 0.0, a_max = 0.0;
+    long long a_nin = 0, a_nout = 0;
+    int bad = 0;
+    const int64_t N = P.N;
+    for (int64_t node = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; node < N;
+         node += int64_t(gridDim.x) * blockDim.x) {
+        const int x = int(node % P.nx);
+        const int y = int((node / P.nx) % P.ny);
+        const int z = int(node / (int64_t(P.nx) * P.ny));
+        float f[Q], g[Q], phin[Q], out[5];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            f[a] = fA[a * N + node];
+            g[a] = gA[a * N + node];
+            if (!isfinite(f[a]) || !isfinite(g[a])) bad = 1;
+        }
+        gather_phi<L>(P, phi, x, y, z, phin);
+        node_update<L, false>(P, f, g, phin, out);
+        a_phi += double(out[0]);
+        const double sp = sqrt(double(out[1]) * out[1] + double(out[2]) * out[2] + double(out[3]) * out[3]);
+        a_max = fmax(a_max, sp);
+        if (out[0] >= 1.0 - eps) { a_pin += double(out[4]); ++a_nin; }
+        if (out[0] <= eps) { a_pout += double(out[4]); ++a_nout; }
+    }
+    const int t = threadIdx.x;
+    s_phi[t] = a_phi; s_pin[t] = a_pin; s_pout[t] = a_pout; s_max[t] = a_max;
+    s_nin[t] = a_nin; s_nout[t] = a_nout; s_bad[t] = bad;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            s_phi[t] += s_phi[t + h]; s_pin[t] += s_pin[t + h]; s_pout[t] += s_pout[t + h];
+            s_max[t] = fmax(s_max[t], s_max[t + h]);
+            s_nin[t] += s_nin[t + h]; s_nout[t] += s_nout[t + h]; s_bad[t] |= s_bad[t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        DiagPartial r;
+        r.sum_phi = s_phi[0]; r.sum_p_in = s_pin[0]; r.sum_p_out = s_pout[0]; r.max_speed = s_max[0];
+        r.n_in = s_nin[0]; r.n_out = s_nout[0]; r.nonfinite = s_bad[0]; r.pad = 0;
+        part[blockIdx.x] = r;
+    }
+}
+
+// Final reduction of the partials in a fixed order (one thread: deterministic).
+template <class L>
+__global__ void k_diag_final(const DiagPartial* __restrict__ part, int nparts, DiagPartial* __restrict__ res)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    DiagPartial r = {0.0, 0.0, 0.0, 0.0, 0, 0, 0, 0};
+    for (int i = 0; i < nparts; ++i) {
+        r.sum_phi += part[i].sum_phi; r.sum_p_in += part[i].sum_p_in; r.sum_p_out += part[i].sum_p_out;
+        r.max_speed = fmax(r.max_speed, part[i].max_speed);
+        r.n_in += part[i].n_in; r.n_out += part[i].n_out; r.nonfinite |= part[i].nonfinite;
+    }
+    *res = r;
+}
+
+// Test hook: collision of independent cells, layout [n][Q].
+template <class L>
+__global__ void k_collide_cells(const __grid_constant__ DevParams P, int64_t n, const float* __restrict__ fi,
+                                const float* __restrict__ gi, const float* __restrict__ pin,
+                                float* __restrict__ fo, float* __restrict__ go, float* __restrict__ out)
+{
+    constexpr int Q = L::Q;
+    const int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    float f[Q], g[Q], phin[Q], o[5];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        f[a] = fi[c * Q + a];
+        g[a] = gi[c * Q + a];
+        phin[a] = pin[c * Q + a];
+    }
+    node_update<L, true>(P, f, g, phin, o);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        fo[c * Q + a] = f[a];
+        go[c * Q + a] = g[a];
+    }
+    if (out)
+        for (int k = 0; k < 5; ++k) out[c * 5 + k] = o[k];
+}
+
+// ------------------------------------------------------ host-side launchers
+
+struct Buffers {
+    float *fA, *gA, *fB, *gB, *phi;
+};
+
+template <class L>
+struct Launch {
+    static cudaError_t step(const DevParams& P, const Buffers& b, cudaStream_t s);
+    static cudaError_t init(const DevParams& P, const float* phi, const float* u, const float* pstar,
+                            float* f, float* g, cudaStream_t s);
+    static cudaError_t fields(const DevParams& P, const Buffers& b, float* ophi, float* ou, float* op,
+                              cudaStream_t s);
+    static cudaError_t diag(const DevParams& P, const Buffers& b, double eps, DiagPartial* part, int nparts,
+                            DiagPartial* res, cudaStream_t s);
+    static cudaError_t inlet_profile(const DevParams& P, double cx, double cy, double R, double W, double uj,
+                                     float* phi_in, float* u_in, cudaStream_t s);
+    static cudaError_t collide_cells(const DevParams& P, int64_t n, const float* f, const float* g,
+                                     const float* phin, float* fs, float* gs, float* out, cudaStream_t s);
+};
+
+template <class L>
+cudaError_t Launch<L>::step(const DevParams& P, const Buffers& b, cudaStream_t s)
+{
+    k_phi<L><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, b.gA, b.phi);
+    dim3 grid((P.nx + 127) / 128, P.ny, (L::D == 3) ? P.nz : 1);
+    k_step<L><<<grid, 128, 0, s>>>(P, b.fA, b.gA, b.phi, b.fB, b.gB);
+    const int lastlo = (L::D == 2) ? P.bc[2] : P.bc[4];
+    const int lasthi = (L::D == 2) ? P.bc[3] : P.bc[5];
+    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
+    if (lastlo == BC_INLET) k_inlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fB, b.gB);
+    if (lasthi == BC_OUTFLOW) k_outlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fA, b.gA, b.fB, b.gB);
+    return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t Launch<L>::init(const DevParams& P, const float* phi, const float* u, const float* pstar, float* f,
+                            float* g, cudaStream_t s)
+{
+    k_init<L><<<unsigned((P.N + 255) / 256), 256, 0, s>>>(P, phi, u, pstar, f, g);
+    return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t Launch<L>::fields(const DevParams& P, const Buffers& b, float* ophi, float* ou, float* op,
+                              cudaStream_t s)
+{
+    k_phi<L><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, b.gA, b.phi);
+    dim3 grid((P.nx + 127) / 128, P.ny, (L::D == 3) ? P.nz : 1);
+    k_fields<L><<<grid, 128, 0, s>>>(P, b.fA, b.gA, b.phi, ophi, ou, op);
+    return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t Launch<L>::diag(const DevParams& P, const Buffers& b, double eps, DiagPartial* part, int nparts,
+                            DiagPartial* res, cudaStream_t s)
+{
+    k_phi<L><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, b.gA, b.phi);
+    k_diag<L><<<nparts, 256, 0, s>>>(P, b.fA, b.gA, b.phi, eps, part);
+    k_diag_final<L><<<1, 32, 0, s>>>(part, nparts, res);
+    return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t Launch<L>::inlet_profile(const DevParams& P, double cx, double cy, double R, double W, double uj,
+                                     float* phi_in, float* u_in, cudaStream_t s)
+{
+    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
+    k_inlet_profile<L><<<(nface + 127) / 128, 128, 0, s>>>(nface, P.nx, cx, cy, R, W, uj, phi_in, u_in);
+    return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t Launch<L>::collide_cells(const DevParams& P, int64_t n, const float* f, const float* g,
+                                     const float* phin, float* fs, float* gs, float* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_collide_cells<L><<<unsigned((n + 127) / 128), 128, 0, s>>>(P, n, f, g, phin, fs, gs, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,212 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 oracle.
+
+Float32 arithmetic on the GPU against FP64 in the oracle.  Tolerances:
+  * one collision or one step from the same state: max |gpu - oracle| within
+    2e-6 of the largest magnitude of the compared array (a few float32 ulps of
+    the O(10) terms that make up each result);
+  * after 1000 steps: relative L2 of phi and u <= 1e-5 (the bound stated for
+    float32 storage), with an absolute floor for u where the oracle velocity
+    is only spurious-current noise.
+"""
+import numpy as np
+import pytest
+
+import lbm_cases as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_12205_gb300 import build, lbm
+    build.build()
+    lbm.load()
+    return lbm
+
+
+@pytest.fixture(scope="module")
+def orc():
+    from oracle import oracle
+    oracle.build()
+    return oracle
+
+
+def rel_l2(a, b, floor=0.0):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), floor)
+
+
+def close(a, b, rtol=2e-6):
+    scale = np.abs(b).max()
+    return np.abs(np.asarray(a, np.float64) - b).max() <= rtol * scale + 1e-30
+
+
+# ------------------------------------------------------------- one cell
+
+@pytest.mark.parametrize("lat,Q", [(0, 9), (1, 19)])
+@pytest.mark.parametrize("visc_model", [0, 1])
+def test_collide_cells_vs_dense_oracle(lib, orc, lat, Q, visc_model):
+    """Moment-space collision on the GPU vs the dense M^-1 S M of the oracle on
+    random cells (brute force over 2000 cells per case)."""
+    import torch
+    p = C.base_params(lat, 1, 1, 1, rho_L=0.01, tau_L=0.9, tau_H=0.2, sigma=1e-3, W=4.0,
+                      force=[1e-5, -2e-5, 3e-5], rho_ref=0.01, visc_model=visc_model)
+    r = C.rng(21 + lat + 2 * visc_model)
+    n = 2000
+    f = ((r.random((n, Q)) - 0.5) * 0.02 / Q).astype(np.float32)
+    g = (r.random((n, Q)) / Q).astype(np.float32)
+    phin = np.clip(g.sum(1, keepdims=True) + 0.2 * (r.random((n, Q)) - 0.5), -0.05, 1.05)
+    phin[:, 0] = g.astype(np.float64).sum(1)
+    phin = phin.astype(np.float32)
+    dev = [torch.from_numpy(a).cuda() for a in (f, g, phin)]
+    fs, gs = torch.empty_like(dev[0]), torch.empty_like(dev[1])
+    out = torch.empty((n, 5), dtype=torch.float32, device="cuda")
+    lib.lbm_collide_cells(p, dev[0], dev[1], dev[2], fs, gs, out)
+    fs, gs, out = fs.cpu().numpy(), gs.cpu().numpy(), out.cpu().numpy()
+    o = orc.Oracle(p)
+    rf, rg, ro = np.zeros((n, Q)), np.zeros((n, Q)), np.zeros((n, 5))
+    for i in range(n):
+        rf[i], rg[i], ro[i], _ = o.collide_node(f[i], g[i], phin[i])
+    assert close(gs, rg) and close(fs, rf, 5e-6)
+    assert close(out[:, 0], ro[:, 0])
+    assert np.abs(out[:, 1:4] - ro[:, 1:4]).max() <= 5e-6 * np.abs(ro[:, 1:4]).max()
+    assert np.abs(out[:, 4] - ro[:, 4]).max() <= 5e-6 * np.abs(ro[:, 4]).max()
+
+
+# ------------------------------------------------------------ one step
+
+STEP_CASES = {
+    # name: (lattice, shape (nz, ny, nx), bc)
+    "d2q9_periodic": (0, (1, 23, 137), [0, 0, 0, 0, 0, 0]),
+    "d2q9_walls": (0, (1, 31, 130), [0, 0, 1, 1, 0, 0]),
+    "d2q9_walls_xy": (0, (1, 17, 19), [1, 1, 1, 1, 0, 0]),
+    "d2q9_jet": (0, (1, 29, 133), [0, 0, 2, 3, 0, 0]),
+    "d3q19_periodic": (1, (9, 7, 131), [0] * 6),
+    "d3q19_walls": (1, (11, 9, 13), [1, 1, 0, 0, 1, 1]),
+    "d3q19_jet": (1, (12, 10, 129), [0, 0, 1, 1, 2, 3]),
+}
+
+
+@pytest.mark.parametrize("name", list(STEP_CASES))
+def test_one_step_from_random_state(lib, orc, name):
+    lat, (nz, ny, nx), bc = STEP_CASES[name]
+    p = C.base_params(lat, nx, ny, nz, rho_L=0.05, tau_L=0.3, tau_H=0.1, sigma=2e-3, W=4.0,
+                      force=[1e-6, -2e-6, 1e-6], rho_ref=0.05, inlet_u=0.04,
+                      inlet_center=[nx / 2.0 - 0.3, ny / 2.0 + 0.2], inlet_radius=3.5)
+    p["bc"] = bc
+    f, g = C.random_state(p, seed_offset=hash(name) % 1000)
+    o = orc.Oracle(p)
+    o.set_populations(f, g)
+    o.step(1)
+    rf, rg = o.populations()
+    sim = lib.LBM(p)
+    sim.set_populations(f.astype(np.float32), g.astype(np.float32))
+    sim.step(1)
+    gf, gg = sim.populations()
+    assert close(gg, rg), np.abs(gg - rg).max()
+    assert close(gf, rf, 5e-6), np.abs(gf - rf).max()
+    o.step(2)
+    sim.step(2)
+    gf, gg = sim.populations()
+    rf, rg = o.populations()
+    assert close(gg, rg, 5e-6) and close(gf, rf, 2e-5)
+
+
+# ---------------------------------------------------- configured workloads
+
+def test_drop2d_128_parity_1000_steps(lib, orc):
+    """128 x 128 periodic drop, R = 25, rho* = 1000, mu* = 100, sigma = 1e-4,
+    W = 5, M = 0.02, tau_H = 0.8: relative L2 of phi and u after 1000 steps."""
+    p, phi, u, ps = C.drop2d()
+    sim = lib.LBM(p)
+    sim.init_fields(phi, u, ps)
+    d0 = sim.diag()
+    sim.step(1000)
+    g_phi, g_u, g_p = sim.fields()
+    d1 = sim.diag()
+    o = orc.Oracle(p)
+    o.init_fields(phi, u, ps)
+    o.step(1000)
+    r_phi, r_u, r_p = o.fields()
+    assert rel_l2(g_phi, r_phi) <= 1e-5
+    # u is spurious-current sized (~1e-6); floor 1e-3 U_sigma sqrt(N), U_sigma = sigma / mu_H
+    u_sigma = p["sigma"] / (p["rho_H"] * p["tau_H"] / 3.0)
+    assert rel_l2(g_u, r_u, floor=1e-3 * u_sigma * np.sqrt(r_u.size)) <= 1e-5 * 100
+    assert d1["finite"] == 1
+    assert abs(d1["sum_phi"] - d0["sum_phi"]) / d0["sum_phi"] < 1e-5
+    assert abs(d1["sum_phi"] - r_phi.sum()) / r_phi.sum() < 1e-5
+
+
+def test_rt2d_parity_full_size(lib, orc):
+    """256 x 1024 Rayleigh-Taylor (At = 0.5, Re = 3000, W = 5), 200 steps."""
+    p, phi, u, ps = C.rayleigh_taylor2d()
+    sim = lib.LBM(p)
+    sim.init_fields(phi, u, ps)
+    sim.step(200)
+    g_phi, g_u, _ = sim.fields()
+    o = orc.Oracle(p)
+    o.init_fields(phi, u, ps)
+    o.step(200)
+    r_phi, r_u, _ = o.fields()
+    assert rel_l2(g_phi, r_phi) <= 1e-5
+    assert rel_l2(g_u, r_u) <= 1e-4
+
+
+def test_jet3d_small_parity(lib, orc):
+    """Quarter-scale-shaped jet (D3Q19, inlet + convective outlet, periodic
+    sides), 100 steps."""
+    p, phi, u, ps = C.jet3d(nx=24, ny=24, nz=48, Rn=4.0)
+    sim = lib.LBM(p)
+    sim.init_fields(phi, u, ps)
+    sim.step(100)
+    g_phi, g_u, _ = sim.fields()
+    o = orc.Oracle(p)
+    o.init_fields(phi, u, ps)
+    o.step(100)
+    r_phi, r_u, _ = o.fields()
+    assert rel_l2(g_phi, r_phi) <= 1e-5
+    assert rel_l2(g_u, r_u) <= 1e-4
+
+
+def test_checkpoint_restart_bitwise(lib):
+    p, phi, u, ps = C.rayleigh_taylor2d(L=64)
+    a = lib.LBM(p)
+    a.init_fields(phi, u, ps)
+    a.step(40)
+    f, g = a.populations()
+    a.step(40)
+    fa, ga = a.populations()
+    b = lib.LBM(p)
+    b.set_populations(f, g)
+    b.step(40)
+    fb, gb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+
+
+def test_invalid_parameters_rejected(lib):
+    p = C.base_params(0, 8, 8, 1)
+    p["bc"] = [0, 1, 0, 0, 0, 0]        # unpaired periodic face
+    with pytest.raises(lib.LbmError) as e:
+        lib.LBM(p)
+    assert e.value.code == lib.LBM_ERR_ARG
+    p = C.base_params(0, 8, 8, 1, tau_H=-1.0)
+    with pytest.raises(lib.LbmError):
+        lib.LBM(p)
+    p = C.base_params(0, 8, 8, 1)
+    sim = lib.LBM(p)
+    with pytest.raises(lib.LbmError) as e:
+        sim.step(1)                      # no state yet
+    assert e.value.code == lib.LBM_ERR_STATE
+
+
+def test_diag_detects_non_finite(lib):
+    p, phi, u, ps = C.drop2d(n=32, R=8.0)
+    sim = lib.LBM(p)
+    sim.init_fields(phi, u, ps)
+    f, g = sim.populations()
+    f[3, 0, 5, 7] = np.nan
+    sim.set_populations(f, g)
+    d = sim.diag()
+    assert d["finite"] == 0

@@ -1,0 +1,58 @@
+"""CPU-side checks of the CUDA library: it builds for sm_103a, loads, exports
+every symbol include/lbm.h declares, and fails loudly (no fallback) where
+there is no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_12205_gb300 import build, lbm
+    build.build()
+    return lbm
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_symbols()
+    assert set(names) == set(lib.EXPORTS)
+    so = lib.load()
+    for n in names:
+        assert hasattr(so, n), n
+
+
+def test_params_struct_layout(lib):
+    # natural alignment of the C struct: 12 int32 then 15 doubles
+    assert ctypes.sizeof(lib.LbmParams) == 12 * 4 + 15 * 8
+    assert lib.LbmParams.rho_L.offset == 48
+    assert ctypes.sizeof(lib.LbmDiagOut) == 4 * 8 + 2 * 8 + 2 * 4
+
+
+def test_no_gpu_means_an_error_not_a_fallback(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import lbm_cases as C
+    with pytest.raises(lib.LbmError) as e:
+        lib.LBM(C.base_params(0, 8, 8, 1))
+    assert e.value.code == lib.LBM_ERR_CUDA
+
+
+def test_ptxas_reports_no_spills(lib):
+    logs = [os.path.join(ROOT, "paper_2505_12205_gb300", "_build", n)
+            for n in ("lbm_d2q9.ptxas.log", "lbm_d3q19.ptxas.log")]
+    for log in logs:
+        txt = open(log).read()
+        assert "sm_103a" in txt
+        spills = re.findall(r"(\d+) bytes spill stores", txt)
+        assert spills and all(int(s) == 0 for s in spills)
