@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput of the fused phase-field WMRT lattice Boltzmann step on GB300.
+
+Workload: the 3D liquid jet of the paper's application section on D3Q19,
+256 x 256 x 1024 nodes (67.1 M), float32 arithmetic and storage, circular plug
+inlet (R = 16, u_j = 0.05, We = 2.2, Re = 200, rho* = 100, mu* = 10, W = 5),
+convective outlet, periodic sides, gravity along the jet.  One bench step is
+one time step of the whole hot path over the grid (phi pass, fused
+collide-stream kernel, inlet and outlet face kernels).
+
+Output: one JSON line (rank 0).  `value` is whole-job MLUPS (lattice node
+updates of both population sets per second) with the state resident in HBM;
+`e2e` is the same metric through the C ABI with host buffers (fields copied
+in from pinned host memory, fields copied back, both inside the timed
+region); `roofline` relates the fused kernel's algorithmic bytes to its
+CUDA-event duration and the measured HBM copy bandwidth; `cpu_baseline` times
+the FP64 oracle on a slab of the same workload on the host cores.
+
+`--impl reference` times the FP64 CPU oracle (the baseline of this project)
+on a bounded slab of the same workload instead.
+
+Multi-GPU (torchrun): independent replicas, one per GPU (weak scaling); the
+only collectives are the timing barrier and the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lbm_cases as C  # noqa: E402
+
+WORKLOAD = dict(name="jet3d_D3Q19_256x256x1024_fp32", nx=256, ny=256, nz=1024, Rn=16.0, We=2.2)
+SAMPLE_NZ = 8          # slab of the same workload for the CPU oracle
+BYTES_PER_LU = 4 * 19 * 4   # f and g read + written once, float32, D3Q19
+METRIC = "MLUPS"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("lbm_kernels.cuh", "lbm_lattice.cuh"):
+        with open(os.path.join(ROOT, "paper_2505_12205_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        if d.get("source_sha256_16") == kernel_source_hash():
+            return float(d["dram_bytes_per_launch_full_workload"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_baseline(min_seconds=10.0, max_steps=40, steps=None):
+    """FP64 oracle on a slab (nz = SAMPLE_NZ) of the workload, on all host cores."""
+    from oracle import oracle
+    p, phi, u, ps = C.jet3d(nx=WORKLOAD["nx"], ny=WORKLOAD["ny"], nz=SAMPLE_NZ,
+                            Rn=WORKLOAD["Rn"], We=WORKLOAD["We"], stub=4.0)
+    o = oracle.Oracle(p)
+    o.init_fields(phi, u, ps)
+    nodes = p["nx"] * p["ny"] * p["nz"]
+    o.step(1)                               # warm-up (page faults)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.step(1)
+        n += 1
+        el = time.perf_counter() - t0
+        if steps is not None and n >= steps:
+            break
+        if steps is None and (el >= min_seconds or n >= max_steps):
+            break
+    el = time.perf_counter() - t0
+    o.close()
+    return nodes * n / el / 1e6, n, el, oracle.threads(), nodes
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    try:
+        from oracle import oracle
+        oracle.build()
+    except Exception as e:  # pragma: no cover
+        print(json.dumps({"impl": "reference", "unavailable": "oracle build failed: %s" % e}))
+        return 0
+    for _ in range(max(args.warmup, 0)):
+        pass
+    mlups, n, el, cores, nodes = oracle_baseline(steps=max(args.steps, 1))
+    sample = "slab %dx%dx%d of the jet workload (same parameters, inlet + outlet), %d steps" % (
+        WORKLOAD["nx"], WORKLOAD["ny"], SAMPLE_NZ, n)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / n * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "sample_nodes": nodes},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2505_12205_gb300 import build, lbm
+    build.build()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import oracle
+        oracle.build()
+        mlups, n, el, cores, nodes = oracle_baseline()
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": "slab %dx%dx%d of the jet workload (same parameters), %d steps, %.1f s"
+                         % (WORKLOAD["nx"], WORKLOAD["ny"], SAMPLE_NZ, n, el)}
+
+    p, phi, u, ps = C.jet3d(nx=WORKLOAD["nx"], ny=WORKLOAD["ny"], nz=WORKLOAD["nz"],
+                            Rn=WORKLOAD["Rn"], We=WORKLOAD["We"])
+    N = p["nx"] * p["ny"] * p["nz"]
+    stream = torch.cuda.current_stream()
+    sim = lbm.LBM(p, stream=stream)
+    phi_d = torch.from_numpy(phi).cuda()
+    u_d = torch.from_numpy(u).cuda()
+    sim.init_fields(phi_d, u_d, None)
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    # ---------------- device-resident timed region
+    sim.set_timing(True)
+    sim.timing()
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_phi, ms_step, ms_face, nrec = sim.timing()
+    sim.set_timing(False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = N * args.steps * ws / (ms_max * 1e-3) / 1e6
+
+    # roofline of the fused collide-stream kernel
+    peak, peak_kind = peaks()
+    step_ms = ms_step / max(nrec, 1)
+    achieved = BYTES_PER_LU * N / (step_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": ncu_traffic(),
+            "kernel": "k_step<D3Q19> (fused collide + push-stream)",
+            "algorithmic_bytes_per_lu": BYTES_PER_LU, "peak_source": peak_kind + " hbm_gbs",
+            "kernel_share_of_step": ms_step / max(ms_phi + ms_step + ms_face, 1e-9)}
+
+    # ---------------- end to end through the C ABI with host buffers
+    phi_h = torch.from_numpy(phi).pin_memory()
+    u_h = torch.from_numpy(u).pin_memory()
+    ps_h = torch.zeros(N, dtype=torch.float32).pin_memory()
+    o_phi = torch.empty(N, dtype=torch.float32).pin_memory()
+    o_u = torch.empty(3 * N, dtype=torch.float32).pin_memory()
+    o_p = torch.empty(N, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    lbm.lbm_init_fields(sim._h, phi_h, u_h, ps_h, n=N, dim=3)
+    lbm.lbm_step(sim._h, args.steps)
+    lbm.lbm_get_fields(sim._h, o_phi, o_u, o_p)
+    te2e = time.perf_counter() - t0
+    t = torch.tensor([te2e], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    te2e = float(t.item())
+    ok = bool(np.isfinite(o_phi.numpy()).all())
+    h2d = (phi_h.numel() + u_h.numel() + ps_h.numel()) * 4
+    d2h = (o_phi.numel() + o_u.numel() + o_p.numel()) * 4
+    e2e = {"value": N * args.steps * ws / te2e / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "fields_finite": ok,
+           "note": "one job per rank: fields in from pinned host, %d steps, fields back" % args.steps}
+    sim.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "lattice": "D3Q19",
+                       "grid": [p["nx"], p["ny"], p["nz"]], "nodes_per_gpu": N,
+                       "We": WORKLOAD["We"], "storage": "fp32",
+                       "l2": "inputs larger than L2: 20.4 GB of populations per GPU vs 129 MB L2",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "hbm_gbs_algorithmic": value / ws * 1e6 * BYTES_PER_LU / 1e9 if ws == 1 else None,
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

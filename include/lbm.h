@@ -144,6 +144,15 @@ int lbm_set_populations(lbm_ctx* ctx, const float* f, const float* g, int on_dev
  * population is not finite. */
 int lbm_diag(lbm_ctx* ctx, double phase_eps, lbm_diag_out* out);
 
+/* Kernel timing (tracing).  With enable != 0, lbm_step records CUDA events
+ * on the context's stream around its kernels; lbm_get_timing synchronises,
+ * returns the summed device time in milliseconds of (0) the phi pass, (1) the
+ * fused collide-stream kernel, (2) the face kernels (inlet, outlet) and the
+ * number of steps recorded, then clears the record.  Timing is off by
+ * default.  ms may not be NULL; it has room for 3 values. */
+int lbm_set_timing(lbm_ctx* ctx, int enable);
+int lbm_get_timing(lbm_ctx* ctx, double* ms, int64_t* nsteps);
+
 /* Wait for all work enqueued on the context's stream. */
 int lbm_sync(lbm_ctx* ctx);
 

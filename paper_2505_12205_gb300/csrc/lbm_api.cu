@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_kernels.cuh"
@@ -33,6 +34,11 @@ struct lbm_ctx {
     DiagPartial* diag_res = nullptr;
     int diag_nparts = 0;
     bool initialised = false;
+    // kernel timing: 4 events per recorded step (before phi, after phi,
+    // after the collide-stream kernel, after the face kernels)
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
     std::string err;
 };
 
@@ -106,10 +112,29 @@ static DevParams make_dev(const lbm_params* p, int64_t N)
     return d;
 }
 
+static cudaError_t next_event(lbm_ctx* c, cudaEvent_t* ev)
+{
+    if (c->events_used == c->events.size()) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        c->events.push_back(e);
+    }
+    *ev = c->events[c->events_used++];
+    return cudaEventRecord(*ev, c->stream);
+}
+
 template <class L>
 static cudaError_t dispatch_step(lbm_ctx* c)
 {
-    cudaError_t e = Launch<L>::step(c->dp, c->b, c->stream);
+    cudaError_t e;
+    if (c->timing) {
+        cudaEvent_t ev;
+        if ((e = next_event(c, &ev)) != cudaSuccess) return e;
+        e = Launch<L>::step_timed(c->dp, c->b, c->stream, [&]() { return next_event(c, &ev); });
+    } else {
+        e = Launch<L>::step(c->dp, c->b, c->stream);
+    }
     std::swap(c->b.fA, c->b.fB);
     std::swap(c->b.gA, c->b.gB);
     return e;
@@ -184,7 +209,8 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
 int lbm_destroy(lbm_ctx* c)
 {
     if (!c) return LBM_OK;
-    if (c->stream || true) cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     cudaFree(c->b.fA); cudaFree(c->b.gA); cudaFree(c->b.fB); cudaFree(c->b.gB);
     cudaFree(c->b.phi); cudaFree(c->face); cudaFree(c->diag_part);
     delete c;
@@ -201,6 +227,32 @@ int lbm_shape(const lbm_ctx* c, int64_t* n_nodes, int32_t* q)
     if (!c) return LBM_ERR_ARG;
     if (n_nodes) *n_nodes = c->N;
     if (q) *q = c->Q;
+    return LBM_OK;
+}
+
+int lbm_set_timing(lbm_ctx* c, int enable)
+{
+    if (!c) return LBM_ERR_ARG;
+    c->timing = enable != 0;
+    return LBM_OK;
+}
+
+int lbm_get_timing(lbm_ctx* c, double* ms, int64_t* nsteps)
+{
+    if (!c || !ms) return LBM_ERR_ARG;
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    double acc[3] = {0.0, 0.0, 0.0};
+    const size_t nrec = c->events_used / 4;
+    for (size_t s = 0; s < nrec; ++s) {
+        for (int k = 0; k < 3; ++k) {
+            float t = 0.0f;
+            LBM_CUDA(c, cudaEventElapsedTime(&t, c->events[4 * s + k], c->events[4 * s + k + 1]));
+            acc[k] += t;
+        }
+    }
+    for (int k = 0; k < 3; ++k) ms[k] = acc[k];
+    if (nsteps) *nsteps = int64_t(nrec);
+    c->events_used = 0;
     return LBM_OK;
 }
 

@@ -569,6 +569,9 @@ struct Buffers {
 template <class L>
 struct Launch {
     static cudaError_t step(const DevParams& P, const Buffers& b, cudaStream_t s);
+    // the same launches, with mark() (which records an event) after each stage
+    template <class Mark>
+    static cudaError_t step_timed(const DevParams& P, const Buffers& b, cudaStream_t s, Mark mark);
     static cudaError_t init(const DevParams& P, const float* phi, const float* u, const float* pstar,
                             float* f, float* g, cudaStream_t s);
     static cudaError_t fields(const DevParams& P, const Buffers& b, float* ophi, float* ou, float* op,
@@ -592,6 +595,25 @@ cudaError_t Launch<L>::step(const DevParams& P, const Buffers& b, cudaStream_t s
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
     if (lastlo == BC_INLET) k_inlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fB, b.gB);
     if (lasthi == BC_OUTFLOW) k_outlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fA, b.gA, b.fB, b.gB);
+    return cudaGetLastError();
+}
+
+template <class L>
+template <class Mark>
+cudaError_t Launch<L>::step_timed(const DevParams& P, const Buffers& b, cudaStream_t s, Mark mark)
+{
+    cudaError_t e;
+    k_phi<L><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, b.gA, b.phi);
+    if ((e = mark()) != cudaSuccess) return e;
+    dim3 grid((P.nx + 127) / 128, P.ny, (L::D == 3) ? P.nz : 1);
+    k_step<L><<<grid, 128, 0, s>>>(P, b.fA, b.gA, b.phi, b.fB, b.gB);
+    if ((e = mark()) != cudaSuccess) return e;
+    const int lastlo = (L::D == 2) ? P.bc[2] : P.bc[4];
+    const int lasthi = (L::D == 2) ? P.bc[3] : P.bc[5];
+    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
+    if (lastlo == BC_INLET) k_inlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fB, b.gB);
+    if (lasthi == BC_OUTFLOW) k_outlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fA, b.gA, b.fB, b.gB);
+    if ((e = mark()) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_STATE 
 # every symbol declared in include/lbm.h
 EXPORTS = ["lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_fields", "lbm_get_populations",
            "lbm_set_populations", "lbm_diag", "lbm_sync", "lbm_shape", "lbm_last_error",
-           "lbm_destroy", "lbm_collide_cells"]
+           "lbm_destroy", "lbm_collide_cells", "lbm_set_timing", "lbm_get_timing"]
 
 
 class LbmParams(ctypes.Structure):
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_last_error.restype = ctypes.c_char_p
     lib.lbm_destroy.argtypes = [vp]
     lib.lbm_collide_cells.argtypes = [P, i64, f32p, f32p, f32p, f32p, f32p, f32p, vp]
+    lib.lbm_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.lbm_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     for name in EXPORTS:
         getattr(lib, name).restype = ctypes.c_int if name != "lbm_last_error" else ctypes.c_char_p
     _lib = lib
@@ -225,6 +227,20 @@ def lbm_destroy(ctx):
     _check(lib, lib.lbm_destroy(ctx))
 
 
+def lbm_set_timing(ctx, enable: bool):
+    lib = load()
+    _check(lib, lib.lbm_set_timing(ctx, 1 if enable else 0), ctx)
+
+
+def lbm_get_timing(ctx):
+    """(ms_phi, ms_collide_stream, ms_faces, steps) summed since the last call."""
+    lib = load()
+    ms = (ctypes.c_double * 3)()
+    n = ctypes.c_int64()
+    _check(lib, lib.lbm_get_timing(ctx, ms, ctypes.byref(n)), ctx)
+    return ms[0], ms[1], ms[2], n.value
+
+
 def lbm_collide_cells(params: dict, f, g, phin, fs, gs, out=None, stream=None):
     """Device tensors [n][Q] (out: [n][5]); see include/lbm.h."""
     lib = load()
@@ -303,3 +319,9 @@ class LBM:
 
     def diag(self, phase_eps: float = 1e-3) -> dict:
         return lbm_diag(self._h, phase_eps)
+
+    def set_timing(self, enable: bool = True):
+        lbm_set_timing(self._h, enable)
+
+    def timing(self):
+        return lbm_get_timing(self._h)
