@@ -41,12 +41,52 @@ struct DevParams {
 
 // ------------------------------------------------------------ node physics
 
+// Deviation of the dimensionless distribution from its weight,
+// Gamma_a(u) - w_a (eq:dimensionless_distribution, eq:equilibrium).  It is
+// formed directly, not as Gamma_a - w_a, so that float32 keeps the small
+// velocity-dependent part exactly instead of losing it to the O(w_a) term.
 template <class L>
-__device__ __forceinline__ float gamma_a(int a, float ux, float uy, float uz, float uu)
+__device__ __forceinline__ float gdev(int a, float ux, float uy, float uz, float uu)
 {
-    // eq:dimensionless_distribution
     const float eu = float(L::ex(a)) * ux + float(L::ey(a)) * uy + float(L::ez(a)) * uz;
-    return L::w(a) * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
+    return L::w(a) * (3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
+}
+
+// Equilibria of both sets (eq:equilibrium_function, eq:equilibrium):
+// geq_a = phi Gamma_a, feq_a = p* w_a + Gamma_a - w_a.  The rest population
+// takes the remainder so that sum_a geq_a = phi and sum_a feq_a = p* hold to
+// the rounding of one sum: float32 weights do not add up to exactly 1, and
+// without this every collision would create or destroy a little mass.
+template <class L>
+__device__ __forceinline__ void equilibria(float phi, float pstar, float ux, float uy, float uz,
+                                           float (&geq)[L::Q], float (&feq)[L::Q])
+{
+    const float uu = ux * ux + uy * uy + uz * uz;
+    float sg = 0.0f, sf = 0.0f;
+#pragma unroll
+    for (int a = 1; a < L::Q; ++a) {
+        const float d = gdev<L>(a, ux, uy, uz, uu);
+        geq[a] = phi * (L::w(a) + d);
+        feq[a] = pstar * L::w(a) + d;
+        sg += geq[a];
+        sf += feq[a];
+    }
+    geq[0] = phi - sg;
+    feq[0] = pstar - sf;
+}
+
+// Hydrodynamic equilibrium alone (for the viscous-force predictor).
+template <class L>
+__device__ __forceinline__ void f_equilibrium(float pstar, float ux, float uy, float uz, float (&feq)[L::Q])
+{
+    const float uu = ux * ux + uy * uy + uz * uz;
+    float sf = 0.0f;
+#pragma unroll
+    for (int a = 1; a < L::Q; ++a) {
+        feq[a] = pstar * L::w(a) + gdev<L>(a, ux, uy, uz, uu);
+        sf += feq[a];
+    }
+    feq[0] = pstar - sf;
 }
 
 // Macroscopic update and collision of one node.  f, g: post-stream
@@ -103,12 +143,11 @@ __device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q]
 
     // viscous force (eq:viscous_force_wmrt) with the predictor velocity
     {
-        const float u0x = jx + Fx * h_rho, u0y = jy + Fy * h_rho, u0z = jz + Fz * h_rho;
-        const float uu0 = u0x * u0x + u0y * u0y + u0z * u0z;
+        const float u0x = jx + Fx * h_rho, u0y = jy + Fy * h_rho, u0z = (L::D == 2) ? 0.0f : jz + Fz * h_rho;
         float dn[Q];
+        f_equilibrium<L>(pstar, u0x, u0y, u0z, dn);
 #pragma unroll
-        for (int a = 0; a < Q; ++a)
-            dn[a] = f[a] - (pstar * L::w(a) + gamma_a<L>(a, u0x, u0y, u0z, uu0) - L::w(a));
+        for (int a = 0; a < Q; ++a) dn[a] = f[a] - dn[a];
         float ck[L::NS];
 #pragma unroll
         for (int k = 0; k < L::NS; ++k) {
@@ -142,7 +181,6 @@ __device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q]
 
     // eq:velocity_update
     const float ux = jx + Fx * h_rho, uy = jy + Fy * h_rho, uz = (L::D == 2) ? 0.0f : jz + Fz * h_rho;
-    const float uu = ux * ux + uy * uy + uz * uz;
 
     if (out) {
         out[0] = phi;
@@ -153,8 +191,11 @@ __device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q]
     }
     if (!collide) return;
 
-    // g: eq:forcing_term, eq:equilibrium_function, eq:equilibrium_with_force,
-    // eq:lbe_interface; n = 0 where |grad phi| < 1e-12
+    float geq[Q], feq[Q];
+    equilibria<L>(phi, pstar, ux, uy, uz, geq, feq);
+
+    // g: eq:forcing_term, eq:equilibrium_with_force, eq:lbe_interface;
+    // n = 0 where |grad phi| < 1e-12
     {
         const float gn2 = dx * dx + dy * dy + dz * dz;
         const float amp = (gn2 >= 1e-24f) ? (1.0f - 4.0f * (phi - 0.5f) * (phi - 0.5f)) * P.inv_W * rsqrtf(gn2) : 0.0f;
@@ -162,19 +203,19 @@ __device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q]
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             const float Fphi = L::w(a) * (float(L::ex(a)) * nx + float(L::ey(a)) * ny + float(L::ez(a)) * nz);
-            const float geq = phi * gamma_a<L>(a, ux, uy, uz, uu);
-            g[a] = g[a] - P.omega_phi * (g[a] - geq + 0.5f * Fphi) + Fphi;
+            g[a] = g[a] - P.omega_phi * (g[a] - geq[a] + 0.5f * Fphi) + Fphi;
         }
     }
-    // f: eq:force_term, eq:equilibrium, eq:equilibrium_modified, eq:mrt_collision
+    // f: eq:force_term, eq:equilibrium_modified, eq:mrt_collision with
+    // M^-1 S M = I - (1 - s_nu) P:  f* = f - M^-1 S M (f - feq + F/2) + F
+    //                                  = feq + F/2 + (1 - s_nu) P (f - feq + F/2)
     {
         const float ir = 3.0f / rho;
         float dl[Q], Fa[Q];
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             Fa[a] = L::w(a) * ir * (float(L::ex(a)) * Fx + float(L::ey(a)) * Fy + float(L::ez(a)) * Fz);
-            const float feq = pstar * L::w(a) + gamma_a<L>(a, ux, uy, uz, uu) - L::w(a);
-            dl[a] = f[a] - feq + 0.5f * Fa[a];
+            dl[a] = f[a] - feq[a] + 0.5f * Fa[a];
         }
         float ck[L::NS];
 #pragma unroll
@@ -191,7 +232,7 @@ __device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q]
 #pragma unroll
             for (int k = 0; k < L::NS; ++k)
                 if (L::m(k, a)) proj += L::rw(k, a) * ck[k];
-            f[a] = f[a] - (dl[a] - proj) + Fa[a];
+            f[a] = feq[a] + 0.5f * Fa[a] + proj;
         }
     }
 }
@@ -322,6 +363,7 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, float* __restrict__
     const float phin = P.phi_in[t], un = P.u_in[t];
     const float ux = 0.0f, uy = (L::D == 2) ? un : 0.0f, uz = (L::D == 3) ? un : 0.0f;
     const float uu = un * un;
+    // Gamma_a = w_a + gdev_a; the inlet uses f^eq without p* (it cancels)
     float f[Q], g[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
@@ -335,11 +377,11 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, float* __restrict__
         const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
         const int t0 = L::ex(a), t1 = (L::D == 2) ? 0 : L::ey(a);
         if (en == 0) {
-            const float G = gamma_a<L>(a, ux, uy, uz, uu);
-            const float fneq = f[a] - (G - L::w(a));
+            const float d = gdev<L>(a, ux, uy, uz, uu);
+            const float fneq = f[a] - d;
             if (t0) Mx += float(t0) * fneq;
             if (t1) My += float(t1) * fneq;
-            theta += g[a] - phin * G;          // eq:excess_density
+            theta += g[a] - phin * (L::w(a) + d);     // eq:excess_density
         } else if (en > 0 && (t0 != 0 || t1 != 0)) {
             ++ndiag;
         }
@@ -351,11 +393,12 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, float* __restrict__
         if (en <= 0) continue;
         const int t0 = L::ex(a), t1 = (L::D == 2) ? 0 : L::ey(a);
         const int ab = L::opp(a);
-        const float Ga = gamma_a<L>(a, ux, uy, uz, uu), Gb = gamma_a<L>(ab, ux, uy, uz, uu);
+        const float da = gdev<L>(a, ux, uy, uz, uu), db = gdev<L>(ab, ux, uy, uz, uu);
         const float eM = float(t0) * Mx + float(t1) * My;
-        fB[a * N + node] = f[ab] + (Ga - Gb) - 0.5f * eM;      // eq:velocity_boundary_distribution
+        fB[a * N + node] = f[ab] + (da - db) - 0.5f * eM;      // eq:velocity_boundary_distribution
         const float corr = (t0 != 0 || t1 != 0) ? th_n : 0.0f;
-        gB[a * N + node] = phin * Ga - (g[ab] - phin * Gb) - corr;   // eq:unknown_distribution_*
+        // eq:unknown_distribution_*: g_a = geq_a - (g_abar - geq_abar) - corr, w_a = w_abar
+        gB[a * N + node] = phin * (2.0f * L::w(a) + da + db) - g[ab] - corr;
     }
 }
 
@@ -418,13 +461,13 @@ __global__ void k_init(const __grid_constant__ DevParams P, const float* __restr
     if (i >= P.N) return;
     const float ux = u ? u[i] : 0.0f, uy = u ? u[P.N + i] : 0.0f;
     const float uz = (u && L::D == 3) ? u[2 * P.N + i] : 0.0f;
-    const float uu = ux * ux + uy * uy + uz * uz;
     const float ps = pstar ? pstar[i] : 0.0f, ph = phi[i];
+    float geq[L::Q], feq[L::Q];
+    equilibria<L>(ph, ps, ux, uy, uz, geq, feq);
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-        const float G = gamma_a<L>(a, ux, uy, uz, uu);
-        g[a * P.N + i] = ph * G;
-        f[a * P.N + i] = ps * L::w(a) + (G - L::w(a));
+        g[a * P.N + i] = geq[a];
+        f[a * P.N + i] = feq[a];
     }
 }
 

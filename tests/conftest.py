@@ -18,3 +18,17 @@ def oracle_mod():
     from oracle import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def report():
+    """Append measured parity figures to $LBM_PARITY_REPORT (a JSON-lines file)
+    when that variable is set; a no-op otherwise."""
+    import json
+    path = os.environ.get("LBM_PARITY_REPORT")
+
+    def rec(name, **values):
+        if path:
+            with open(path, "a") as f:
+                f.write(json.dumps({"test": name, **{k: float(v) for k, v in values.items()}}) + "\n")
+    return rec

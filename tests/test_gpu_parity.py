@@ -51,7 +51,7 @@ def close(a, b, l2=1e-5, mx=5e-5):
 
 @pytest.mark.parametrize("lat,Q", [(0, 9), (1, 19)])
 @pytest.mark.parametrize("visc_model", [0, 1])
-def test_collide_cells_vs_dense_oracle(lib, orc, lat, Q, visc_model):
+def test_collide_cells_vs_dense_oracle(lib, orc, report, lat, Q, visc_model):
     """Moment-space collision on the GPU vs the dense M^-1 S M of the oracle on
     random cells (brute force over 2000 cells per case)."""
     import torch
@@ -73,6 +73,8 @@ def test_collide_cells_vs_dense_oracle(lib, orc, lat, Q, visc_model):
     rf, rg, ro = np.zeros((n, Q)), np.zeros((n, Q)), np.zeros((n, 5))
     for i in range(n):
         rf[i], rg[i], ro[i], _ = o.collide_node(f[i], g[i], phin[i])
+    report("collide_cells_%d_%d" % (lat, visc_model), g_l2=rel_l2(gs, rg), f_l2=rel_l2(fs, rf),
+           u_l2=rel_l2(out[:, 1:4], ro[:, 1:4]), p_l2=rel_l2(out[:, 4], ro[:, 4]))
     assert close(gs, rg), np.abs(gs - rg).max()
     assert close(fs, rf), np.abs(fs - rf).max()
     assert close(out[:, :4], ro[:, :4]), np.abs(out[:, :4] - ro[:, :4]).max()
@@ -94,7 +96,7 @@ STEP_CASES = {
 
 
 @pytest.mark.parametrize("name", list(STEP_CASES))
-def test_one_step_from_random_state(lib, orc, name):
+def test_one_step_from_random_state(lib, orc, report, name):
     lat, (nz, ny, nx), bc = STEP_CASES[name]
     p = C.base_params(lat, nx, ny, nz, rho_L=0.05, tau_L=0.3, tau_H=0.1, sigma=2e-3, W=4.0,
                       force=[1e-6, -2e-6, 1e-6], rho_ref=0.05, inlet_u=0.04,
@@ -109,6 +111,8 @@ def test_one_step_from_random_state(lib, orc, name):
     sim.set_populations(f.astype(np.float32), g.astype(np.float32))
     sim.step(1)
     gf, gg = sim.populations()
+    report("one_step_" + name, g_l2=rel_l2(gg, rg), f_l2=rel_l2(gf, rf),
+           g_max=np.abs(gg - rg).max() / np.abs(rg).max(), f_max=np.abs(gf - rf).max() / np.abs(rf).max())
     assert close(gg, rg), np.abs(gg - rg).max()
     assert close(gf, rf), np.abs(gf - rf).max()
     o.step(2)
@@ -120,7 +124,7 @@ def test_one_step_from_random_state(lib, orc, name):
 
 # ---------------------------------------------------- configured workloads
 
-def test_drop2d_128_parity_1000_steps(lib, orc):
+def test_drop2d_128_parity_1000_steps(lib, orc, report):
     """128 x 128 periodic drop, R = 25, rho* = 1000, mu* = 100, sigma = 1e-4,
     W = 5, M = 0.02, tau_H = 0.8: relative L2 of phi and u after 1000 steps."""
     p, phi, u, ps = C.drop2d()
@@ -134,16 +138,21 @@ def test_drop2d_128_parity_1000_steps(lib, orc):
     o.init_fields(phi, u, ps)
     o.step(1000)
     r_phi, r_u, r_p = o.fields()
-    assert rel_l2(g_phi, r_phi) <= 1e-5
-    # u is spurious-current sized (~1e-6); floor 1e-3 U_sigma sqrt(N), U_sigma = sigma / mu_H
+    # u is spurious-current sized (~1e-6): the relative L2 takes the floor
+    # 1e-3 U_sigma sqrt(N), U_sigma = sigma / mu_H
     u_sigma = p["sigma"] / (p["rho_H"] * p["tau_H"] / 3.0)
-    assert rel_l2(g_u, r_u, floor=1e-3 * u_sigma * np.sqrt(r_u.size)) <= 1e-5 * 100
+    e_u = rel_l2(g_u, r_u, floor=1e-3 * u_sigma * np.sqrt(r_u.size))
+    report("drop2d_1000", phi_l2=rel_l2(g_phi, r_phi), u_l2=e_u, u_l2_nofloor=rel_l2(g_u, r_u),
+           p_l2=rel_l2(g_p, r_p), mass_drift=(d1["sum_phi"] - d0["sum_phi"]) / d0["sum_phi"],
+           dp_gpu=d1["sum_p_in"] / max(d1["n_in"], 1) - d1["sum_p_out"] / max(d1["n_out"], 1))
+    assert rel_l2(g_phi, r_phi) <= 1e-5
+    assert e_u <= 1e-5
     assert d1["finite"] == 1
     assert abs(d1["sum_phi"] - d0["sum_phi"]) / d0["sum_phi"] < 1e-5
     assert abs(d1["sum_phi"] - r_phi.sum()) / r_phi.sum() < 1e-5
 
 
-def test_rt2d_parity_full_size(lib, orc):
+def test_rt2d_parity_full_size(lib, orc, report):
     """256 x 1024 Rayleigh-Taylor (At = 0.5, Re = 3000, W = 5), 200 steps."""
     p, phi, u, ps = C.rayleigh_taylor2d()
     sim = lib.LBM(p)
@@ -154,11 +163,12 @@ def test_rt2d_parity_full_size(lib, orc):
     o.init_fields(phi, u, ps)
     o.step(200)
     r_phi, r_u, _ = o.fields()
+    report("rt2d_200", phi_l2=rel_l2(g_phi, r_phi), u_l2=rel_l2(g_u, r_u))
     assert rel_l2(g_phi, r_phi) <= 1e-5
-    assert rel_l2(g_u, r_u) <= 1e-4
+    assert rel_l2(g_u, r_u) <= 1e-5
 
 
-def test_jet3d_small_parity(lib, orc):
+def test_jet3d_small_parity(lib, orc, report):
     """Quarter-scale-shaped jet (D3Q19, inlet + convective outlet, periodic
     sides), 100 steps."""
     p, phi, u, ps = C.jet3d(nx=24, ny=24, nz=48, Rn=4.0)
@@ -170,8 +180,9 @@ def test_jet3d_small_parity(lib, orc):
     o.init_fields(phi, u, ps)
     o.step(100)
     r_phi, r_u, _ = o.fields()
+    report("jet3d_small_100", phi_l2=rel_l2(g_phi, r_phi), u_l2=rel_l2(g_u, r_u))
     assert rel_l2(g_phi, r_phi) <= 1e-5
-    assert rel_l2(g_u, r_u) <= 1e-4
+    assert rel_l2(g_u, r_u) <= 1e-5
 
 
 def test_checkpoint_restart_bitwise(lib):
