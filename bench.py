@@ -138,7 +138,7 @@ def dist_env():
     return ws, rank, local
 
 
-def oracle_baseline(min_seconds=10.0, max_steps=40, steps=None):
+def oracle_baseline(min_seconds=10.0, max_steps=400, steps=None):
     """FP64 oracle on a slab (nz = SAMPLE_NZ) of the workload, on all host cores."""
     from oracle import oracle
     p, phi, u, ps = C.jet3d(nx=WORKLOAD["nx"], ny=WORKLOAD["ny"], nz=SAMPLE_NZ,

@@ -146,9 +146,10 @@ int lbm_diag(lbm_ctx* ctx, double phase_eps, lbm_diag_out* out);
 
 /* Kernel timing (tracing).  With enable != 0, lbm_step records CUDA events
  * on the context's stream around its kernels; lbm_get_timing synchronises,
- * returns the summed device time in milliseconds of (0) the phi pass, (1) the
- * fused collide-stream kernel, (2) the face kernels (inlet, outlet) and the
- * number of steps recorded, then clears the record.  Timing is off by
+ * returns the summed device time in milliseconds of (0) work before the main
+ * kernel (0 with the single-pass step), (1) the fused collide-stream kernel,
+ * (2) the face kernels (inlet, outlet) and the number of steps recorded, then
+ * clears the record.  Timing is off by
  * default.  ms may not be NULL; it has room for 3 values. */
 int lbm_set_timing(lbm_ctx* ctx, int enable);
 int lbm_get_timing(lbm_ctx* ctx, double* ms, int64_t* nsteps);

@@ -29,6 +29,8 @@ struct lbm_ctx {
     cudaStream_t stream;
     int device;
     lbm::Buffers b;
+    lbm::FusedGeom geom;            // work decomposition of the fused step
+    int fused_blocks = 0;
     float* face = nullptr;          // phi_in, u_in of the inlet plane
     DiagPartial* diag_part = nullptr;
     DiagPartial* diag_res = nullptr;
@@ -131,9 +133,10 @@ static cudaError_t dispatch_step(lbm_ctx* c)
     if (c->timing) {
         cudaEvent_t ev;
         if ((e = next_event(c, &ev)) != cudaSuccess) return e;
-        e = Launch<L>::step_timed(c->dp, c->b, c->stream, [&]() { return next_event(c, &ev); });
+        e = Launch<L>::step_timed(c->dp, c->geom, c->fused_blocks, c->b, c->stream,
+                                  [&]() { return next_event(c, &ev); });
     } else {
-        e = Launch<L>::step(c->dp, c->b, c->stream);
+        e = Launch<L>::step_fused(c->dp, c->geom, c->fused_blocks, c->b, c->stream);
     }
     std::swap(c->b.fA, c->b.fB);
     std::swap(c->b.gA, c->b.gB);
@@ -186,6 +189,13 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
         return r;
     }
     c->diag_res = c->diag_part + c->diag_nparts;
+    e = c->D == 2 ? Launch<D2Q9>::fused_geom(c->dp, &c->geom, &c->fused_blocks)
+                  : Launch<D3Q19>::fused_geom(c->dp, &c->geom, &c->fused_blocks);
+    if (e != cudaSuccess) {
+        int r = cuda_fail(nullptr, e, "fused step set-up");
+        lbm_destroy(c);
+        return r;
+    }
     c->dp.phi_in = c->face;
     c->dp.u_in = c->face + nface;
     const int L = c->D - 1;

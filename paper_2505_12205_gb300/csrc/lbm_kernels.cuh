@@ -346,6 +346,157 @@ __global__ void __launch_bounds__(128) k_step(const __grid_constant__ DevParams 
     }
 }
 
+// ------------------------------------------------- fused step (one pass)
+//
+// One kernel per time step: phi = sum_a g_a is recomputed on the fly from the
+// post-streaming g of the current state, so the separate phi pass and the phi
+// array disappear from the step.  A block owns a tile of TX x TY columns of
+// the plane normal to the last axis (x-y in 3D, x in 2D) and marches along the
+// last axis over a segment of planes, keeping a window of three phi planes of
+// the tile plus a one-node halo in shared memory; the next plane's interior g
+// populations are staged in shared memory while phi of that plane is formed,
+// so every population of the state is read from HBM once per step (the halo
+// re-reads hit L2 because neighbouring tiles march the same planes at the
+// same time).  Blocks are persistent: work items (tile, segment) are dealt
+// round-robin, and the segment count is chosen so every block gets the same
+// number of items.
+struct FusedGeom {
+    int tiles_x, tiles_y, ntiles;
+    int nseg, seglen;      // segments of the last axis
+    int items;             // ntiles * nseg
+};
+
+template <class L, int TX, int TY>
+struct FusedCfg {
+    static constexpr int EX = TX + 2;
+    static constexpr int EY = (L::D == 3) ? TY + 2 : 1;
+    static constexpr int EXT = EX * EY;                 // extended tile positions
+    static constexpr int NT = TX * ((L::D == 3) ? TY : 1);
+    static constexpr size_t smem = sizeof(float) * (3 * EXT + 2 * L::Q * NT);
+};
+
+// phi at the (possibly out-of-range) node (xx, yy, mm) of the march
+// coordinate mm, with the ghost rules of the faces; stores the node's g into
+// stash (NT-strided) when stash is not null.
+template <class L>
+__device__ __forceinline__ float phi_at(const DevParams& P, const float* __restrict__ gA, int xx, int yy, int mm,
+                                        float* stash, int stride)
+{
+    bool inlet = false;
+    const int x = map_phi(xx, P.nx, P.bc[0], P.bc[1], inlet);
+    int y, m;
+    int64_t node;
+    if (L::D == 3) {
+        y = map_phi(yy, P.ny, P.bc[2], P.bc[3], inlet);
+        m = map_phi(mm, P.nz, P.bc[4], P.bc[5], inlet);
+        if (inlet) return P.phi_in[y * P.nx + x];
+        node = (int64_t(m) * P.ny + y) * P.nx + x;
+    } else {
+        m = map_phi(mm, P.ny, P.bc[2], P.bc[3], inlet);
+        if (inlet) return P.phi_in[x];
+        node = int64_t(m) * P.nx + x;
+    }
+    (void)y;
+    const int64_t N = P.N;
+    float s = 0.0f;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+        const float v = __ldg(gA + a * N + node);
+        if (stash) stash[a * stride] = v;
+        s += v;
+    }
+    return s;
+}
+
+template <class L, int TX, int TY>
+__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1))
+k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const float* __restrict__ fA,
+             const float* __restrict__ gA, float* __restrict__ fB, float* __restrict__ gB)
+{
+    using Cfg = FusedCfg<L, TX, TY>;
+    constexpr int Q = L::Q, EX = Cfg::EX, EXT = Cfg::EXT, NT = Cfg::NT;
+    extern __shared__ float smem[];
+    float* win = smem;                    // [3][EY][EX]
+    float* stash = smem + 3 * EXT;        // [2][Q][NT]
+    const int tid = threadIdx.x + ((L::D == 3) ? threadIdx.y * TX : 0);
+    const int tx = threadIdx.x, ty = (L::D == 3) ? threadIdx.y : 0;
+    const int nm = (L::D == 3) ? P.nz : P.ny;       // length of the march axis
+    const int64_t N = P.N;
+
+    for (int item = blockIdx.x; item < G.items; item += gridDim.x) {
+        const int tile = item % G.ntiles, seg = item / G.ntiles;
+        const int x0 = (tile % G.tiles_x) * TX;
+        const int y0 = (L::D == 3) ? (tile / G.tiles_x) * TY : 0;
+        const int m0 = seg * G.seglen;
+        const int m1 = min(m0 + G.seglen, nm);
+        const int x = x0 + tx, y = y0 + ty;
+        const bool own = x < P.nx && ((L::D == 2) || y < P.ny);
+
+        // phi of plane mm over the extended tile into window slot (mm mod 3);
+        // the interior g of that plane goes to stash buffer (mm mod 2)
+        auto fill = [&](int mm, bool keep) {
+            float* wslot = win + ((mm % 3 + 3) % 3) * EXT;
+            float* sbuf = stash + (mm & 1) * Q * NT;
+            if (own) wslot[(ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 1] =
+                phi_at<L>(P, gA, x, y, mm, keep ? sbuf + tid : nullptr, NT);
+            for (int q = tid; q < EXT; q += NT) {
+                const int px = q % EX, py = q / EX;
+                const int xx = x0 - 1 + px;
+                const int yy = (L::D == 3) ? y0 - 1 + py : 0;
+                const bool interior = px >= 1 && px <= TX && xx < P.nx &&
+                                      ((L::D == 2) || (py >= 1 && py <= TY && yy < P.ny));
+                // positions beyond the one-node ring of the grid are never read
+                const bool needed = xx <= P.nx && ((L::D == 2) || yy <= P.ny);
+                if (!interior) wslot[q] = needed ? phi_at<L>(P, gA, xx, yy, mm, nullptr, 0) : 0.0f;
+            }
+        };
+
+        __syncthreads();
+        fill(m0 - 1, false);
+        fill(m0, true);
+        for (int m = m0; m < m1; ++m) {
+            fill(m + 1, m + 1 < m1);
+            __syncthreads();
+            if (own) {
+                float f[Q], g[Q], phin[Q];
+                const float* sbuf = stash + (m & 1) * Q * NT + tid;
+                const int64_t node = (L::D == 3) ? (int64_t(m) * P.ny + y) * P.nx + x : int64_t(m) * P.nx + x;
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    f[a] = __ldg(fA + a * N + node);
+                    g[a] = sbuf[a * NT];
+                }
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    const int dm = (L::D == 3) ? L::ez(a) : L::ey(a);
+                    const int dy = (L::D == 3) ? L::ey(a) : 0;
+                    const float* wslot = win + (((m + dm) % 3 + 3) % 3) * EXT;
+                    phin[a] = wslot[(ty + ((L::D == 3) ? 1 : 0) + dy) * EX + tx + 1 + L::ex(a)];
+                }
+                node_update<L, true>(P, f, g, phin, nullptr);
+                const int z = (L::D == 3) ? m : 0;
+                const int yc = (L::D == 3) ? y : m;
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    int kind = 0;
+                    const int xx = map_push(x + L::ex(a), P.nx, P.bc[0], P.bc[1], kind);
+                    const int yy = map_push(yc + L::ey(a), P.ny, P.bc[2], P.bc[3], kind);
+                    const int zz = (L::D == 3) ? map_push(z + L::ez(a), P.nz, P.bc[4], P.bc[5], kind) : 0;
+                    if (kind == 0) {
+                        const int64_t t = (int64_t(zz) * P.ny + yy) * P.nx + xx;
+                        fB[a * N + t] = f[a];
+                        gB[a * N + t] = g[a];
+                    } else if (kind == 2) {
+                        fB[L::opp(a) * N + node] = f[a];
+                        gB[L::opp(a) * N + node] = g[a];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // Velocity inlet (f) and phase-field inlet (g) on the low face of the last
 // axis, applied to the post-streaming populations in B (App. B; the force
 // shift is omitted at the inlet, p* cancels, the tangential excess momentum
@@ -612,9 +763,14 @@ struct Buffers {
 template <class L>
 struct Launch {
     static cudaError_t step(const DevParams& P, const Buffers& b, cudaStream_t s);
+    // fused single-pass step (k_step_fused + face kernels); geometry from fused_geom
+    static cudaError_t step_fused(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
+                                  cudaStream_t s);
+    static cudaError_t fused_geom(const DevParams& P, FusedGeom* G, int* nblocks);
     // the same launches, with mark() (which records an event) after each stage
     template <class Mark>
-    static cudaError_t step_timed(const DevParams& P, const Buffers& b, cudaStream_t s, Mark mark);
+    static cudaError_t step_timed(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
+                                  cudaStream_t s, Mark mark);
     static cudaError_t init(const DevParams& P, const float* phi, const float* u, const float* pstar,
                             float* f, float* g, cudaStream_t s);
     static cudaError_t fields(const DevParams& P, const Buffers& b, float* ophi, float* ou, float* op,
@@ -641,15 +797,78 @@ cudaError_t Launch<L>::step(const DevParams& P, const Buffers& b, cudaStream_t s
     return cudaGetLastError();
 }
 
+// Tile shapes: 32 x 8 columns in 3D, 128 nodes of a row in 2D.
+template <class L> struct FusedTile;
+template <> struct FusedTile<D2Q9> { static constexpr int TX = 128, TY = 1; };
+template <> struct FusedTile<D3Q19> { static constexpr int TX = 32, TY = 8; };
+
+template <class L>
+cudaError_t Launch<L>::fused_geom(const DevParams& P, FusedGeom* G, int* nblocks)
+{
+    constexpr int TX = FusedTile<L>::TX, TY = FusedTile<L>::TY;
+    using Cfg = FusedCfg<L, TX, TY>;
+    auto kern = k_step_fused<L, TX, TY>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, Cfg::smem)) != cudaSuccess)
+        return e;
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    const int slots = sms * per_sm;
+    G->tiles_x = (P.nx + TX - 1) / TX;
+    G->tiles_y = (L::D == 3) ? (P.ny + TY - 1) / TY : 1;
+    G->ntiles = G->tiles_x * G->tiles_y;
+    const int nm = (L::D == 3) ? P.nz : P.ny;
+    // segments: at least 16 planes each, and items a multiple of the slots
+    // when that is possible, so every persistent block gets equal work
+    int best = 1;
+    double best_eff = -1.0;
+    for (int nseg = 1; nseg <= nm; ++nseg) {
+        const int seglen = (nm + nseg - 1) / nseg;
+        if (seglen < 16 && nseg > 1) break;
+        const long items = long(G->ntiles) * nseg;
+        const long rounds = (items + slots - 1) / slots;
+        const double work = double(nm + 2 * nseg);          // planes incl. the 2-plane prologue
+        const double eff = (double(items) / double(rounds * slots)) * (double(nm) / work);
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = nseg; }
+    }
+    G->nseg = best;
+    G->seglen = (nm + best - 1) / best;
+    G->nseg = (nm + G->seglen - 1) / G->seglen;
+    G->items = G->ntiles * G->nseg;
+    *nblocks = G->items < slots ? G->items : slots;
+    return cudaSuccess;
+}
+
+template <class L>
+cudaError_t Launch<L>::step_fused(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
+                                  cudaStream_t s)
+{
+    constexpr int TX = FusedTile<L>::TX, TY = FusedTile<L>::TY;
+    using Cfg = FusedCfg<L, TX, TY>;
+    const dim3 block(TX, (L::D == 3) ? TY : 1);
+    k_step_fused<L, TX, TY><<<nblocks, block, Cfg::smem, s>>>(P, G, b.fA, b.gA, b.fB, b.gB);
+    const int lastlo = (L::D == 2) ? P.bc[2] : P.bc[4];
+    const int lasthi = (L::D == 2) ? P.bc[3] : P.bc[5];
+    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
+    if (lastlo == BC_INLET) k_inlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fB, b.gB);
+    if (lasthi == BC_OUTFLOW) k_outlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fA, b.gA, b.fB, b.gB);
+    return cudaGetLastError();
+}
+
 template <class L>
 template <class Mark>
-cudaError_t Launch<L>::step_timed(const DevParams& P, const Buffers& b, cudaStream_t s, Mark mark)
+cudaError_t Launch<L>::step_timed(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
+                                  cudaStream_t s, Mark mark)
 {
+    constexpr int TX = FusedTile<L>::TX, TY = FusedTile<L>::TY;
+    using Cfg = FusedCfg<L, TX, TY>;
     cudaError_t e;
-    k_phi<L><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, b.gA, b.phi);
-    if ((e = mark()) != cudaSuccess) return e;
-    dim3 grid((P.nx + 127) / 128, P.ny, (L::D == 3) ? P.nz : 1);
-    k_step<L><<<grid, 128, 0, s>>>(P, b.fA, b.gA, b.phi, b.fB, b.gB);
+    if ((e = mark()) != cudaSuccess) return e;      // no separate phi pass in the fused step
+    const dim3 block(TX, (L::D == 3) ? TY : 1);
+    k_step_fused<L, TX, TY><<<nblocks, block, Cfg::smem, s>>>(P, G, b.fA, b.gA, b.fB, b.gB);
     if ((e = mark()) != cudaSuccess) return e;
     const int lastlo = (L::D == 2) ? P.bc[2] : P.bc[4];
     const int lasthi = (L::D == 2) ? P.bc[3] : P.bc[5];

@@ -7,8 +7,11 @@ Float32 arithmetic on the GPU against FP64 in the oracle.  Tolerances:
     amplified by up to rho_H / rho_L through F / rho in the light phase
     (rho_H / rho_L = 20 .. 100 in these cases), which bounds the worst cells;
   * after 1000 steps: relative L2 of phi and u <= 1e-5 (the bound stated for
-    float32 storage), with an absolute floor for u where the oracle velocity
-    is only spurious-current noise.
+    float32 storage).  The one exception is u of the static drop: there u is
+    the spurious current (|u| ~ 2e-6), a residual of terms F / (2 rho) ~ 3e-3
+    that cancel to 1e-3 of their size, so float32 rounding alone (6e-8 of the
+    terms) leaves ~1e-4 of |u|.  That case is held to 2e-4 relative and to
+    1e-5 of the capillary velocity scale U_sigma = sigma / mu_H.
 """
 import numpy as np
 import pytest
@@ -138,18 +141,23 @@ def test_drop2d_128_parity_1000_steps(lib, orc, report):
     o.init_fields(phi, u, ps)
     o.step(1000)
     r_phi, r_u, r_p = o.fields()
-    # u is spurious-current sized (~1e-6): the relative L2 takes the floor
-    # 1e-3 U_sigma sqrt(N), U_sigma = sigma / mu_H
     u_sigma = p["sigma"] / (p["rho_H"] * p["tau_H"] / 3.0)
-    e_u = rel_l2(g_u, r_u, floor=1e-3 * u_sigma * np.sqrt(r_u.size))
-    report("drop2d_1000", phi_l2=rel_l2(g_phi, r_phi), u_l2=e_u, u_l2_nofloor=rel_l2(g_u, r_u),
+    e_u = rel_l2(g_u, r_u)
+    e_u_scale = np.linalg.norm(g_u - r_u) / (u_sigma * np.sqrt(r_u.size))
+    dp_gpu = d1["sum_p_in"] / d1["n_in"] - d1["sum_p_out"] / d1["n_out"]
+    inside, outside = r_phi >= 1 - 1e-3, r_phi <= 1e-3
+    dp_ref = r_p[inside].mean() - r_p[outside].mean()
+    report("drop2d_1000", phi_l2=rel_l2(g_phi, r_phi), u_l2=e_u, u_l2_capillary_scale=e_u_scale,
            p_l2=rel_l2(g_p, r_p), mass_drift=(d1["sum_phi"] - d0["sum_phi"]) / d0["sum_phi"],
-           dp_gpu=d1["sum_p_in"] / max(d1["n_in"], 1) - d1["sum_p_out"] / max(d1["n_out"], 1))
+           dp_gpu=dp_gpu, dp_ref=dp_ref)
     assert rel_l2(g_phi, r_phi) <= 1e-5
-    assert e_u <= 1e-5
+    assert e_u <= 2e-4 and e_u_scale <= 1e-5
+    assert rel_l2(g_p, r_p) <= 1e-5
+    assert abs(dp_gpu / dp_ref - 1) < 1e-3
     assert d1["finite"] == 1
-    assert abs(d1["sum_phi"] - d0["sum_phi"]) / d0["sum_phi"] < 1e-5
-    assert abs(d1["sum_phi"] - r_phi.sum()) / r_phi.sum() < 1e-5
+    # the paper's mass band is +-2e-6 (Sec. 5.4)
+    assert abs(d1["sum_phi"] - d0["sum_phi"]) / d0["sum_phi"] < 2e-6
+    assert abs(d1["sum_phi"] - r_phi.sum()) / r_phi.sum() < 2e-6
 
 
 def test_rt2d_parity_full_size(lib, orc, report):
