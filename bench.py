@@ -211,8 +211,8 @@ def run_gpu(args):
                "sample": "slab %dx%dx%d of the jet workload (same parameters), %d steps, %.1f s"
                          % (WORKLOAD["nx"], WORKLOAD["ny"], SAMPLE_NZ, n, el)}
 
-    p, phi, u, ps = C.jet3d(nx=WORKLOAD["nx"], ny=WORKLOAD["ny"], nz=WORKLOAD["nz"],
-                            Rn=WORKLOAD["Rn"], We=WORKLOAD["We"])
+    nx, ny, nz = args.grid if args.grid else (WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"])
+    p, phi, u, ps = C.jet3d(nx=nx, ny=ny, nz=nz, Rn=WORKLOAD["Rn"], We=WORKLOAD["We"])
     N = p["nx"] * p["ny"] * p["nz"]
     stream = torch.cuda.current_stream()
     sim = lbm.LBM(p, stream=stream)
@@ -294,10 +294,12 @@ def run_gpu(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "lattice": "D3Q19",
+            "config": {"workload": WORKLOAD["name"] if not args.grid else
+                       "jet3d_D3Q19_%dx%dx%d_fp32 (reduced grid)" % tuple(args.grid), "lattice": "D3Q19",
                        "grid": [p["nx"], p["ny"], p["nz"]], "nodes_per_gpu": N,
                        "We": WORKLOAD["We"], "storage": "fp32",
-                       "l2": "inputs larger than L2: 20.4 GB of populations per GPU vs 129 MB L2",
+                       "l2": "inputs larger than L2: %.1f GB of populations per GPU vs 129 MB L2"
+                             % (4 * 19 * 4 * N / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single"},
             "hbm_gbs_algorithmic": value / ws * 1e6 * BYTES_PER_LU / 1e9 if ws == 1 else None,
             "roofline": roof,
@@ -319,6 +321,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
+                    help="reduced grid of the same jet workload (profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
