@@ -5,8 +5,9 @@ Workload: the 3D liquid jet of the paper's application section on D3Q19,
 256 x 256 x 1024 nodes (67.1 M), float32 arithmetic and storage, circular plug
 inlet (R = 16, u_j = 0.05, We = 2.2, Re = 200, rho* = 100, mu* = 10, W = 5),
 convective outlet, periodic sides, gravity along the jet.  One bench step is
-one time step of the whole hot path over the grid (phi pass, fused
-collide-stream kernel, inlet and outlet face kernels).
+one time step of the whole hot path over the grid (the single-pass fused
+kernel that recomputes phi, collides and streams, then the inlet and outlet
+face kernels).
 
 Output: one JSON line (rank 0).  `value` is whole-job MLUPS (lattice node
 updates of both population sets per second) with the state resident in HBM;
@@ -256,7 +257,7 @@ def run_gpu(args):
     achieved = BYTES_PER_LU * N / (step_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": ncu_traffic(),
-            "kernel": "k_step<D3Q19> (fused collide + push-stream)",
+            "kernel": "k_step_fused<D3Q19,32,8> (phi + collide + push-stream, one pass)",
             "algorithmic_bytes_per_lu": BYTES_PER_LU, "peak_source": peak_kind + " hbm_gbs",
             "kernel_share_of_step": ms_step / max(ms_phi + ms_step + ms_face, 1e-9)}
 
@@ -304,7 +305,7 @@ def run_gpu(args):
             "hbm_gbs_algorithmic": value / ws * 1e6 * BYTES_PER_LU / 1e9 if ws == 1 else None,
             "roofline": roof,
             "e2e": e2e,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 3 * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

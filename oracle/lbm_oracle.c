@@ -43,8 +43,11 @@
  *   R6  ghost phi: periodic -> wrapped value; wall and outlet -> value of the
  *       adjacent fluid node (zero normal gradient); inlet -> phi_in.
  *   R7  n = grad(phi)/|grad(phi)| is taken as 0 where |grad(phi)| < 1e-12.
- *   R8  inlet: the force shift f' = f + F/2 is omitted at inlet nodes (the
- *       paper treats the inlet as single phase and skips its derivatives);
+ *   R8  inlet: derivatives of phi are not evaluated at inlet nodes (the
+ *       paper treats the inlet as single phase and skips the derivatives of
+ *       the macroscopic variables there): grad phi = lap phi = 0, so the
+ *       interfacial forces F_s, F_p, F_mu and F^phi vanish at inlet nodes,
+ *       and the force shift f' = f + F/2 of the velocity rule is omitted;
  *       p* cancels from eq:velocity_boundary_distribution; the tangential
  *       excess momentum is shared by the 2 unknown populations that carry each
  *       tangential component (factor 1/2, which makes
@@ -235,11 +238,11 @@ static void apply_MSM(const orc_ctx* c, double s_nu, const double* x, double* y)
 
 /* Macroscopic update and collision of one node.
  * f, g: the node's post-stream populations; phin[a] = phi(x + e_a) (phin[0] =
- * phi(x)).  Writes the post-collision populations fs, gs (either may be NULL),
+ * phi(x)); inlet_node: the node lies on an inlet face.  Writes the post-collision populations fs, gs (either may be NULL),
  * out = {phi, u_x, u_y, u_z, p} and terms = {phi, dphi/dx, dphi/dy, dphi/dz,
  * lap phi, rho, tau, mu_phi, p*, F_x, F_y, F_z, u_x, u_y, u_z} (may be NULL). */
 static void node_update(const orc_ctx* c, const double* f, const double* g, const double* phin,
-                        double* fs, double* gs, double* out, double* terms)
+                        int inlet_node, double* fs, double* gs, double* out, double* terms)
 {
     const orc_params* P = &c->p;
     int Q = c->Q;
@@ -248,12 +251,13 @@ static void node_update(const orc_ctx* c, const double* f, const double* g, cons
     double phi = 0.0;
     for (int a = 0; a < Q; ++a) phi += g[a];
 
-    /* eq:gradient_phi, eq:laplacian_phi */
+    /* eq:gradient_phi, eq:laplacian_phi (not evaluated at inlet nodes, R8) */
     double gphi[3] = {0, 0, 0}, lap = 0.0;
-    for (int a = 0; a < Q; ++a) {
-        for (int d = 0; d < 3; ++d) gphi[d] += c->e[a][d] * c->w[a] * phin[a] / CS2;
-        lap += 2.0 * c->w[a] * (phin[a] - phin[0]) / CS2;
-    }
+    if (!inlet_node)
+        for (int a = 0; a < Q; ++a) {
+            for (int d = 0; d < 3; ++d) gphi[d] += c->e[a][d] * c->w[a] * phin[a] / CS2;
+            lap += 2.0 * c->w[a] * (phin[a] - phin[0]) / CS2;
+        }
 
     /* Reading R4, eq:density_interpolation, eq:relaxation_time (R3) */
     double ph = phi < 0.0 ? 0.0 : (phi > 1.0 ? 1.0 : phi);
@@ -404,6 +408,13 @@ static double phi_at(const orc_ctx* c, const double* phi, const int v[3])
     return phi[nid(c, m[0], m[1], m[2])];
 }
 
+/* The node lies on the inlet face (first layer of the last axis). */
+static int is_inlet_node(const orc_ctx* c, int x, int y, int z)
+{
+    int v[3] = {x, y, z};
+    return c->p.bc[2 * c->L] == BC_INLET && v[c->L] == 0;
+}
+
 /* Fill phin[a] = phi(x + e_a) for node (x,y,z). */
 static void gather_phi(const orc_ctx* c, const double* phi, int x, int y, int z, double* phin)
 {
@@ -534,7 +545,8 @@ static void step_once(orc_ctx* c)
         int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
         double phin[QMAX];
         gather_phi(c, c->phi, x, y, z, phin);
-        node_update(c, c->fA + i * Q, c->gA + i * Q, phin, c->fs + i * Q, c->gs + i * Q, NULL, NULL);
+        node_update(c, c->fA + i * Q, c->gA + i * Q, phin, is_inlet_node(c, x, y, z), c->fs + i * Q,
+                    c->gs + i * Q, NULL, NULL);
     }
 
     /* eq:streaming_f/g with eq:periodic_f/g and eq:no_slip_f/g */
@@ -639,7 +651,7 @@ void orc_fields(orc_ctx* c, double* phi, double* u, double* p)
         int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
         double phin[QMAX], out[5];
         gather_phi(c, c->phi, x, y, z, phin);
-        node_update(c, c->fA + i * Q, c->gA + i * Q, phin, NULL, NULL, out, NULL);
+        node_update(c, c->fA + i * Q, c->gA + i * Q, phin, is_inlet_node(c, x, y, z), NULL, NULL, out, NULL);
         if (phi) phi[i] = out[0];
         if (u) for (int d = 0; d < c->D; ++d) u[(int64_t)d * c->N + i] = out[1 + d];
         if (p) p[i] = out[4];
@@ -722,5 +734,5 @@ int orc_collision_matrix(int lattice, double s_nu, double* C)
 void orc_collide_node(const orc_ctx* c, const double* f, const double* g, const double* phin,
                       double* fs, double* gs, double* out, double* terms)
 {
-    node_update(c, f, g, phin, fs, gs, out, terms);
+    node_update(c, f, g, phin, 0, fs, gs, out, terms);
 }

@@ -3,15 +3,17 @@
 // State: post-streaming populations f, g in population-major planes
 // pop[a * N + node], node = (z * ny + y) * nx + x, double-buffered (A = current
 // state, B = next state).  One time step (Algorithms 1-3 of the paper, fused):
-//   k_phi      phi = sum_a g_a (eq:phase_field_variable) of the state in A;
-//   k_step     per node: isotropic stencils of phi (eq:gradient_phi,
-//              eq:laplacian_phi), material properties, chemical potential,
-//              forces, velocity, g-collision (eq:lbe_interface), f-collision in
-//              moment space (eq:mrt_collision), then push-streaming into B with
-//              periodic wrap and halfway bounce-back (App. B);
-//   k_inlet    velocity + phase-field inlet on the inlet plane of B;
-//   k_outlet   convective outlet on the outlet plane of B (reads A and B).
-// The host swaps A and B after each step.
+//   k_step_fused  per node: phi = sum_a g_a (eq:phase_field_variable) on the
+//                 tile and its halo, isotropic stencils of phi
+//                 (eq:gradient_phi, eq:laplacian_phi), material properties,
+//                 chemical potential, forces, velocity, g-collision
+//                 (eq:lbe_interface), f-collision in moment space
+//                 (eq:mrt_collision), then push-streaming into B with periodic
+//                 wrap and halfway bounce-back (App. B);
+//   k_inlet       velocity + phase-field inlet on the inlet plane of B;
+//   k_outlet      convective outlet on the outlet plane of B (reads A and B).
+// The host swaps A and B after each step.  k_phi + k_fields / k_diag compute
+// the macroscopic fields and diagnostics of a state with the same node code.
 #pragma once
 
 #include <cstdint>
@@ -91,10 +93,13 @@ __device__ __forceinline__ void f_equilibrium(float pstar, float ux, float uy, f
 
 // Macroscopic update and collision of one node.  f, g: post-stream
 // populations (overwritten with the post-collision ones when collide);
-// phin[a] = phi(x + e_a).  out (may be null): phi, u_x, u_y, u_z, p.
+// phin[a] = phi(x + e_a); inlet_node: the node lies on the inlet face, where
+// derivatives of phi are not evaluated (the inlet is single phase in the
+// paper's treatment), so the interfacial forces vanish there.  out (may be
+// null): phi, u_x, u_y, u_z, p.
 template <class L, bool collide>
 __device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q], float (&g)[L::Q],
-                                            const float (&phin)[L::Q], float* out)
+                                            const float (&phin)[L::Q], bool inlet_node, float* out)
 {
     constexpr int Q = L::Q;
     float phi = 0.0f;
@@ -112,6 +117,7 @@ __device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q]
         lap += L::w(a) * (phin[a] - phin[0]);
     }
     lap *= 6.0f;
+    if (inlet_node) dx = dy = dz = lap = 0.0f;
 
     // phi clamped inside the material properties only
     const float ph = fminf(fmaxf(phi, 0.0f), 1.0f);
@@ -306,46 +312,6 @@ __device__ __forceinline__ void gather_phi(const DevParams& P, const float* __re
     }
 }
 
-template <class L>
-__global__ void __launch_bounds__(128) k_step(const __grid_constant__ DevParams P,
-                                              const float* __restrict__ fA, const float* __restrict__ gA,
-                                              const float* __restrict__ phi, float* __restrict__ fB,
-                                              float* __restrict__ gB)
-{
-    constexpr int Q = L::Q;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= P.nx) return;
-    const int64_t N = P.N;
-    const int64_t node = (int64_t(z) * P.ny + y) * P.nx + x;
-
-    float f[Q], g[Q], phin[Q];
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        f[a] = __ldg(fA + a * N + node);
-        g[a] = __ldg(gA + a * N + node);
-    }
-    gather_phi<L>(P, phi, x, y, z, phin);
-    node_update<L, true>(P, f, g, phin, nullptr);
-
-    // push streaming (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g)
-#pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        int kind = 0;
-        const int xx = map_push(x + L::ex(a), P.nx, P.bc[0], P.bc[1], kind);
-        const int yy = map_push(y + L::ey(a), P.ny, P.bc[2], P.bc[3], kind);
-        const int zz = (L::D == 3) ? map_push(z + L::ez(a), P.nz, P.bc[4], P.bc[5], kind) : 0;
-        if (kind == 0) {
-            const int64_t t = (int64_t(zz) * P.ny + yy) * P.nx + xx;
-            fB[a * N + t] = f[a];
-            gB[a * N + t] = g[a];
-        } else if (kind == 2) {               // wall: back to this node, opposite slot
-            fB[L::opp(a) * N + node] = f[a];
-            gB[L::opp(a) * N + node] = g[a];
-        }                                      // open face: leaves the domain
-    }
-}
-
 // ------------------------------------------------- fused step (one pass)
 //
 // One kernel per time step: phi = sum_a g_a is recomputed on the fly from the
@@ -473,7 +439,8 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const float
                     const float* wslot = win + (((m + dm) % 3 + 3) % 3) * EXT;
                     phin[a] = wslot[(ty + ((L::D == 3) ? 1 : 0) + dy) * EX + tx + 1 + L::ex(a)];
                 }
-                node_update<L, true>(P, f, g, phin, nullptr);
+                const bool inlet_node = m == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
+                node_update<L, true>(P, f, g, phin, inlet_node, nullptr);
                 const int z = (L::D == 3) ? m : 0;
                 const int yc = (L::D == 3) ? y : m;
 #pragma unroll
@@ -642,7 +609,8 @@ __global__ void __launch_bounds__(128) k_fields(const __grid_constant__ DevParam
         g[a] = gA[a * N + node];
     }
     gather_phi<L>(P, phi, x, y, z, phin);
-    node_update<L, false>(P, f, g, phin, out);
+    const bool inlet_node = ((L::D == 3) ? z : y) == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
+    node_update<L, false>(P, f, g, phin, inlet_node, out);
     if (ophi) ophi[node] = out[0];
     if (ou) {
         ou[node] = out[1];
@@ -687,7 +655,8 @@ __global__ void __launch_bounds__(256) k_diag(const __grid_constant__ DevParams 
             if (!isfinite(f[a]) || !isfinite(g[a])) bad = 1;
         }
         gather_phi<L>(P, phi, x, y, z, phin);
-        node_update<L, false>(P, f, g, phin, out);
+        const bool inlet_node = ((L::D == 3) ? z : y) == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
+        node_update<L, false>(P, f, g, phin, inlet_node, out);
         a_phi += double(out[0]);
         const double sp = sqrt(double(out[1]) * out[1] + double(out[2]) * out[2] + double(out[3]) * out[3]);
         a_max = fmax(a_max, sp);
@@ -744,7 +713,7 @@ __global__ void k_collide_cells(const __grid_constant__ DevParams P, int64_t n, 
         g[a] = gi[c * Q + a];
         phin[a] = pin[c * Q + a];
     }
-    node_update<L, true>(P, f, g, phin, o);
+    node_update<L, true>(P, f, g, phin, false, o);
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         fo[c * Q + a] = f[a];
@@ -762,7 +731,6 @@ struct Buffers {
 
 template <class L>
 struct Launch {
-    static cudaError_t step(const DevParams& P, const Buffers& b, cudaStream_t s);
     // fused single-pass step (k_step_fused + face kernels); geometry from fused_geom
     static cudaError_t step_fused(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
                                   cudaStream_t s);
@@ -782,20 +750,6 @@ struct Launch {
     static cudaError_t collide_cells(const DevParams& P, int64_t n, const float* f, const float* g,
                                      const float* phin, float* fs, float* gs, float* out, cudaStream_t s);
 };
-
-template <class L>
-cudaError_t Launch<L>::step(const DevParams& P, const Buffers& b, cudaStream_t s)
-{
-    k_phi<L><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, b.gA, b.phi);
-    dim3 grid((P.nx + 127) / 128, P.ny, (L::D == 3) ? P.nz : 1);
-    k_step<L><<<grid, 128, 0, s>>>(P, b.fA, b.gA, b.phi, b.fB, b.gB);
-    const int lastlo = (L::D == 2) ? P.bc[2] : P.bc[4];
-    const int lasthi = (L::D == 2) ? P.bc[3] : P.bc[5];
-    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
-    if (lastlo == BC_INLET) k_inlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fB, b.gB);
-    if (lasthi == BC_OUTFLOW) k_outlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fA, b.gA, b.fB, b.gB);
-    return cudaGetLastError();
-}
 
 // Tile shapes: 32 x 8 columns in 3D, 128 nodes of a row in 2D.
 template <class L> struct FusedTile;
