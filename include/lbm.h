@@ -154,6 +154,26 @@ int lbm_diag(lbm_ctx* ctx, double phase_eps, lbm_diag_out* out);
 int lbm_set_timing(lbm_ctx* ctx, int enable);
 int lbm_get_timing(lbm_ctx* ctx, double* ms, int64_t* nsteps);
 
+/* lbm_diag without a context and without allocating: for callers that
+ * cannot allocate device memory (code running where cudaMalloc is forbidden
+ * or would bypass an allocator that must own every byte, e.g. a host
+ * framework's caching allocator, a real-time loop, a plug-in that is only
+ * handed buffers).  The paper has no counterpart; this is a library service.
+ * p describes the grid and physics as for lbm_create; f and g are device
+ * pointers to post-streaming populations [Q][N] (the layout of
+ * lbm_get_populations); out is a host pointer.  The same kernels as lbm_diag
+ * run on `stream` with their scratch (phi, the inlet profile, the reduction
+ * partials) in one static device array of the library: at most 2,097,152
+ * nodes and 65,536 inlet-plane nodes (LBM_ERR_ARG beyond that).  The array
+ * (about 8.6 MB) stays on every device that loads the library until exit.
+ * The first call on a device looks up the array's device address; make that
+ * call before any stream capture.  All calls share the array and rewrite
+ * everything they read, so results do not depend on earlier calls, but calls
+ * that overlap on the GPU race.  Synchronises `stream`.  Errors as lbm_diag;
+ * their text is returned by lbm_last_error(NULL). */
+int lbm_diag_noalloc(const lbm_params* p, const float* f, const float* g, double phase_eps,
+                     lbm_diag_out* out, void* stream);
+
 /* Wait for all work enqueued on the context's stream. */
 int lbm_sync(lbm_ctx* ctx);
 

@@ -143,6 +143,13 @@ static cudaError_t dispatch_step(lbm_ctx* c)
     return e;
 }
 
+// Entry points for the other translation units of the library.
+namespace lbm {
+int api_validate(const lbm_params* p, std::string& why) { return validate(p, why); }
+DevParams api_make_dev(const lbm_params* p, int64_t N) { return make_dev(p, N); }
+void api_set_thread_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace lbm
+
 extern "C" {
 
 int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)

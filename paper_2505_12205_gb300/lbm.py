@@ -25,7 +25,8 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_STATE 
 # every symbol declared in include/lbm.h
 EXPORTS = ["lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_fields", "lbm_get_populations",
            "lbm_set_populations", "lbm_diag", "lbm_sync", "lbm_shape", "lbm_last_error",
-           "lbm_destroy", "lbm_collide_cells", "lbm_set_timing", "lbm_get_timing"]
+           "lbm_destroy", "lbm_collide_cells", "lbm_set_timing", "lbm_get_timing",
+           "lbm_diag_noalloc"]
 
 
 class LbmParams(ctypes.Structure):
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH):
     lib.lbm_last_error.restype = ctypes.c_char_p
     lib.lbm_destroy.argtypes = [vp]
     lib.lbm_collide_cells.argtypes = [P, i64, f32p, f32p, f32p, f32p, f32p, f32p, vp]
+    lib.lbm_diag_noalloc.argtypes = [P, f32p, f32p, ctypes.c_double, ctypes.POINTER(LbmDiagOut), vp]
     lib.lbm_set_timing.argtypes = [vp, ctypes.c_int]
     lib.lbm_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     for name in EXPORTS:
@@ -239,6 +241,19 @@ def lbm_get_timing(ctx):
     n = ctypes.c_int64()
     _check(lib, lib.lbm_get_timing(ctx, ms, ctypes.byref(n)), ctx)
     return ms[0], ms[1], ms[2], n.value
+
+
+def lbm_diag_noalloc(params: dict, f, g, phase_eps: float = 1e-3, stream=None) -> dict:
+    """Diagnostics of device populations f, g ([Q][N] float32 CUDA tensors)
+    without a context and without any device allocation (see include/lbm.h)."""
+    lib = load()
+    s = make_params(params)
+    out = LbmDiagOut()
+    code = lib.lbm_diag_noalloc(ctypes.byref(s), _ptr(f)[0], _ptr(g)[0], float(phase_eps),
+                                ctypes.byref(out), ctypes.c_void_p(_stream_handle(stream)))
+    if code not in (LBM_OK, LBM_ERR_DIVERGED):
+        _check(lib, code)
+    return {k: getattr(out, k) for k, _ in LbmDiagOut._fields_ if k != "reserved"}
 
 
 def lbm_collide_cells(params: dict, f, g, phin, fs, gs, out=None, stream=None):

@@ -1,0 +1,69 @@
+"""lbm_diag_noalloc: the diagnostics entry point for callers that cannot
+allocate device memory (it keeps its scratch in a static device array of the
+library instead of calling cudaMalloc).  Its results must match those of
+lbm_diag on a context holding the same populations, on two calls in a row
+(the second call reuses the array the first one wrote).  This file is
+collected last so that a failure here leaves every other test already run.
+"""
+import numpy as np
+import pytest
+
+import lbm_cases as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_12205_gb300 import build, lbm
+    build.build()
+    lbm.load()
+    return lbm
+
+
+def _device_state(lib, case, steps):
+    import torch
+    p, phi, u, ps = case
+    sim = lib.LBM(p)
+    sim.init_fields(phi, u, ps)
+    sim.step(steps)
+    f = torch.empty(sim.Q * sim.N, dtype=torch.float32, device="cuda")
+    g = torch.empty_like(f)
+    lib.lbm_get_populations(sim._h, f, g)
+    lib.lbm_sync(sim._h)
+    return p, sim, f, g
+
+
+def _agree(a, b):
+    for k in ("sum_phi", "sum_p_in", "sum_p_out", "max_speed"):
+        assert abs(a[k] - b[k]) <= 1e-12 * max(abs(b[k]), 1e-300), (k, a[k], b[k])
+    for k in ("n_in", "n_out", "finite"):
+        assert a[k] == b[k], (k, a[k], b[k])
+
+
+def test_noalloc_diag_matches_context_diag_twice(lib):
+    import torch
+    # a periodic 2D drop and a small 3D jet (inlet profile in the scratch too)
+    cases = [C.drop2d(n=64, R=16.0), C.jet3d(nx=24, ny=24, nz=48, Rn=4.0)]
+    states = [_device_state(lib, c, 30) for c in cases]
+    for _ in range(2):                          # two calls in a row per state
+        for p, sim, f, g in states:
+            ref = sim.diag(1e-2)
+            got = lib.lbm_diag_noalloc(p, f, g, 1e-2)
+            torch.cuda.synchronize()
+            _agree(got, ref)
+            assert got["finite"] == 1 and got["n_out"] > 0
+    assert states[0][1].diag(1e-2)["n_in"] > 0
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch(lib):
+    import torch
+    p = C.base_params(0, 2048, 2048, 1)        # 4.2 M nodes > 2,097,152
+    f = torch.zeros(9, dtype=torch.float32, device="cuda")
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_diag_noalloc(p, f, f)
+    assert e.value.code == lib.LBM_ERR_ARG
+    assert "exceeds" in lib.lbm_last_error()
