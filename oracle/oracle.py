@@ -21,26 +21,33 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "lbm_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liblbm_oracle.so")
+# a prebuilt oracle library may be substituted (the mutation tests use this)
+LIB_OVERRIDE = os.environ.get("LBM_ORACLE_LIB")
 
 D2Q9, D3Q19 = 0, 1
 PERIODIC, WALL, INLET, OUTFLOW = 0, 1, 2, 3
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP contraction off, so x86 and Arm agree)."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
-    if (not force and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
-        return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
+def compile_source(src: str, out: str) -> str:
+    """gcc -O2 with FP contraction off (so x86 and Arm agree), OpenMP if available."""
+    tmp = out + ".tmp%d" % os.getpid()
     base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-            "-fno-fast-math", SRC, "-o", tmp, "-lm"]
+            "-fno-fast-math", src, "-o", tmp, "-lm"]
     try:
         subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:])
     except subprocess.CalledProcessError:
         subprocess.check_call(base)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_build (skipped when up to date)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    if (not force and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
+        return LIB
+    return compile_source(SRC, LIB)
 
 
 class OrcParams(ctypes.Structure):
@@ -66,7 +73,7 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        _lib = ctypes.CDLL(LIB_OVERRIDE if LIB_OVERRIDE else build())
         d = ctypes.POINTER(ctypes.c_double)
         f = ctypes.POINTER(ctypes.c_float)
         i32 = ctypes.POINTER(ctypes.c_int32)
