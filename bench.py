@@ -139,6 +139,20 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float) -> float:
+    """Max of a per-rank float over the process group (identity without one).
+    The only collective of the bench besides the timing barrier; works on the
+    nccl (CUDA tensor) and gloo (CPU tensor) backends."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_baseline(min_seconds=10.0, max_steps=400, steps=None):
     """FP64 oracle on a slab (nz = SAMPLE_NZ) of the workload, on all host cores."""
     from oracle import oracle
@@ -245,10 +259,7 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     ms_phi, ms_step, ms_face, nrec = sim.timing()
     sim.set_timing(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms)
     value = N * args.steps * ws / (ms_max * 1e-3) / 1e6
 
     # roofline of the fused collide-stream kernel
@@ -276,10 +287,7 @@ def run_gpu(args):
     lbm.lbm_step(sim._h, args.steps)
     lbm.lbm_get_fields(sim._h, o_phi, o_u, o_p)
     te2e = time.perf_counter() - t0
-    t = torch.tensor([te2e], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    te2e = float(t.item())
+    te2e = max_over_ranks(te2e)
     ok = bool(np.isfinite(o_phi.numpy()).all())
     h2d = (phi_h.numel() + u_h.numel() + ps_h.numel()) * 4
     d2h = (o_phi.numel() + o_u.numel() + o_p.numel()) * 4

@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 #include "lbm_kernels.cuh"
 
 extern template struct lbm::Launch<lbm::D2Q9>;

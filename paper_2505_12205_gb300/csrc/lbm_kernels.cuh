@@ -77,44 +77,37 @@ __device__ __forceinline__ void equilibria(float phi, float pstar, float ux, flo
     feq[0] = pstar - sf;
 }
 
-// Hydrodynamic equilibrium alone (for the viscous-force predictor).
-template <class L>
-__device__ __forceinline__ void f_equilibrium(float pstar, float ux, float uy, float uz, float (&feq)[L::Q])
-{
-    const float uu = ux * ux + uy * uy + uz * uz;
-    float sf = 0.0f;
-#pragma unroll
-    for (int a = 1; a < L::Q; ++a) {
-        feq[a] = pstar * L::w(a) + gdev<L>(a, ux, uy, uz, uu);
-        sf += feq[a];
-    }
-    feq[0] = pstar - sf;
-}
-
-// Macroscopic update and collision of one node.  f, g: post-stream
-// populations (overwritten with the post-collision ones when collide);
-// phin[a] = phi(x + e_a); inlet_node: the node lies on the inlet face, where
-// derivatives of phi are not evaluated (the inlet is single phase in the
-// paper's treatment), so the interfacial forces vanish there.  out (may be
-// null): phi, u_x, u_y, u_z, p.
-template <class L, bool collide>
-__device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q], float (&g)[L::Q],
-                                            const float (&phin)[L::Q], bool inlet_node, float* out)
+// Macroscopic update and collision of one node, written as a stream over
+// the populations so that no per-population array has to live in registers:
+//   fa(a)   -> f_a,  ga(a) -> g_a   (post-streaming populations; ga is read
+//                                    twice, for phi and for the collision)
+//   pa(a)   -> phi(x + e_a)          (stencil values, pa(0) = phi(x))
+//   emit(a, f*_a, g*_a)              (post-collision populations, when collide)
+// inlet_node: the node lies on the inlet face, where derivatives of phi are
+// not evaluated (the inlet is single phase in the paper's treatment), so the
+// interfacial forces vanish there.  out (may be null): phi, u_x, u_y, u_z, p.
+template <class L, bool collide, class FA, class GA, class PA, class EM>
+__device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA pa, bool inlet_node,
+                                            float* out, EM emit)
 {
     constexpr int Q = L::Q;
     float phi = 0.0f;
 #pragma unroll
-    for (int a = 0; a < Q; ++a) phi += g[a];
+    for (int a = 0; a < Q; ++a) phi += ga(a);        // eq:phase_field_variable
 
     // eq:gradient_phi, eq:laplacian_phi (c / (c_s^2 dx) = 3, 2 c^2 / (c_s^2 dx^2) = 6)
     float dx = 0.0f, dy = 0.0f, dz = 0.0f, lap = 0.0f;
+    {
+        const float p0 = pa(0);
 #pragma unroll
-    for (int a = 1; a < Q; ++a) {
-        const float wp = 3.0f * L::w(a) * phin[a];
-        if (L::ex(a)) dx += float(L::ex(a)) * wp;
-        if (L::ey(a)) dy += float(L::ey(a)) * wp;
-        if (L::ez(a)) dz += float(L::ez(a)) * wp;
-        lap += L::w(a) * (phin[a] - phin[0]);
+        for (int a = 1; a < Q; ++a) {
+            const float v = pa(a);
+            const float wp = 3.0f * L::w(a) * v;
+            if (L::ex(a)) dx += float(L::ex(a)) * wp;
+            if (L::ey(a)) dy += float(L::ey(a)) * wp;
+            if (L::ez(a)) dz += float(L::ez(a)) * wp;
+            lap += L::w(a) * (v - p0);
+        }
     }
     lap *= 6.0f;
     if (inlet_node) dx = dy = dz = lap = 0.0f;
@@ -130,13 +123,23 @@ __device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q]
     // chemical potential (sign reading: 4 beta (phi - phi_L)(phi - phi_H)(phi - phi_0))
     const float mu_phi = 4.0f * P.beta * phi * (phi - 1.0f) * (phi - 0.5f) - P.kappa * lap;
 
+    // zeroth, first and second moments of f (eq:normalized_pressure)
     float pstar = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+    float sxx = 0.0f, syy = 0.0f, szz = 0.0f, sxy = 0.0f, sxz = 0.0f, syz = 0.0f;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        pstar += f[a];
-        if (L::ex(a)) jx += float(L::ex(a)) * f[a];
-        if (L::ey(a)) jy += float(L::ey(a)) * f[a];
-        if (L::ez(a)) jz += float(L::ez(a)) * f[a];
+        const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+        const float v = fa(a);
+        pstar += v;
+        if (ex) jx += float(ex) * v;
+        if (ey) jy += float(ey) * v;
+        if (ez) jz += float(ez) * v;
+        if (ex) sxx += v;
+        if (ey) syy += v;
+        if (ez) szz += v;
+        if (ex * ey) sxy += float(ex * ey) * v;
+        if (ex * ez) sxz += float(ex * ez) * v;
+        if (ey * ez) syz += float(ey * ez) * v;
     }
     const float drho = P.rho_H - P.rho_L;                     // eq:density_gradient_phase_field
     const float rx = drho * dx, ry = drho * dy, rz = drho * dz;
@@ -144,46 +147,29 @@ __device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q]
     const float fb = rho - P.rho_ref;                          // eq:gravity_force
     float Fx = mu_phi * dx + cp * rx + fb * P.gx;              // F_s + F_p + F_b
     float Fy = mu_phi * dy + cp * ry + fb * P.gy;
-    float Fz = mu_phi * dz + cp * rz + fb * P.gz;
+    float Fz = (L::D == 2) ? 0.0f : mu_phi * dz + cp * rz + fb * P.gz;
     const float h_rho = 0.5f / rho;
+    const float p3 = pstar * (1.0f / 3.0f);
 
-    // viscous force (eq:viscous_force_wmrt) with the predictor velocity
+    // Viscous force, eq:viscous_force_wmrt, with the predictor velocity u0.
+    // Second moments of M^-1 S M (f - feq(u0)): the non-equilibrium stress
+    // D = Pi(f) - p* c_s^2 I - u0 u0 (the second moment of feq is exactly
+    // p* c_s^2 I + u u on D2Q9 and D3Q19); the deviatoric stress rows relax
+    // at s_nu and the trace at 1, so the relaxed stress is
+    // s_nu D + (1 - s_nu) tr(D) / dim I.
     {
         const float u0x = jx + Fx * h_rho, u0y = jy + Fy * h_rho, u0z = (L::D == 2) ? 0.0f : jz + Fz * h_rho;
-        float dn[Q];
-        f_equilibrium<L>(pstar, u0x, u0y, u0z, dn);
-#pragma unroll
-        for (int a = 0; a < Q; ++a) dn[a] = f[a] - dn[a];
-        float ck[L::NS];
-#pragma unroll
-        for (int k = 0; k < L::NS; ++k) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int a = 0; a < Q; ++a)
-                if (L::m(k, a)) acc += float(L::m(k, a)) * dn[a];
-            ck[k] = (1.0f - s_nu) * acc;
-        }
-        float pxx = 0.0f, pyy = 0.0f, pzz = 0.0f, pxy = 0.0f, pxz = 0.0f, pyz = 0.0f;
-#pragma unroll
-        for (int a = 1; a < Q; ++a) {
-            float md = dn[a];
-#pragma unroll
-            for (int k = 0; k < L::NS; ++k)
-                if (L::m(k, a)) md -= L::rw(k, a) * ck[k];
-            const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-            if (ex) pxx += md;
-            if (ey) pyy += md;
-            if (ez) pzz += md;
-            if (ex * ey) pxy += float(ex * ey) * md;
-            if (ex * ez) pxz += float(ex * ez) * md;
-            if (ey * ez) pyz += float(ey * ez) * md;
-        }
+        const float dxx = sxx - p3 - u0x * u0x, dyy = syy - p3 - u0y * u0y;
+        const float dzz = (L::D == 2) ? 0.0f : szz - p3 - u0z * u0z;
+        const float dxy = sxy - u0x * u0y, dxz = sxz - u0x * u0z, dyz = syz - u0y * u0z;
+        const float iso = (1.0f - s_nu) * (dxx + dyy + dzz) * (1.0f / float(L::D));
+        const float txx = s_nu * dxx + iso, tyy = s_nu * dyy + iso, tzz = s_nu * dzz + iso;
+        const float txy = s_nu * dxy, txz = s_nu * dxz, tyz = s_nu * dyz;
         // nu / c_s^2 = tau
-        Fx -= tau * (pxx * rx + pxy * ry + pxz * rz);
-        Fy -= tau * (pxy * rx + pyy * ry + pyz * rz);
-        Fz -= tau * (pxz * rx + pyz * ry + pzz * rz);
+        Fx -= tau * (txx * rx + txy * ry + txz * rz);
+        Fy -= tau * (txy * rx + tyy * ry + tyz * rz);
+        if (L::D == 3) Fz -= tau * (txz * rx + tyz * ry + tzz * rz);
     }
-    if (L::D == 2) Fz = 0.0f;
 
     // eq:velocity_update
     const float ux = jx + Fx * h_rho, uy = jy + Fy * h_rho, uz = (L::D == 2) ? 0.0f : jz + Fz * h_rho;
@@ -195,50 +181,93 @@ __device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q]
         out[3] = uz;
         out[4] = pstar * rho * (1.0f / 3.0f);
     }
-    if (!collide) return;
+    if constexpr (!collide) {
+        return;
+    } else {
+        const float uu = ux * ux + uy * uy + uz * uz;
+        // Equilibria (eq:equilibrium_function, eq:equilibrium): geq_a = phi
+        // Gamma_a, feq_a = p* w_a + Gamma_a - w_a.  The rest population takes
+        // the remainder so that sum_a geq_a = phi and sum_a feq_a = p* hold to
+        // the rounding of one sum: float32 weights do not add up to exactly 1,
+        // and without this every collision would create or destroy mass.
+        float sg = 0.0f, sf = 0.0f;
+#pragma unroll
+        for (int a = 1; a < Q; ++a) {
+            const float d = gdev<L>(a, ux, uy, uz, uu);
+            sg += phi * (L::w(a) + d);
+            sf += pstar * L::w(a) + d;
+        }
+        const float geq0 = phi - sg, feq0 = pstar - sf;
 
-    float geq[Q], feq[Q];
-    equilibria<L>(phi, pstar, ux, uy, uz, geq, feq);
-
-    // g: eq:forcing_term, eq:equilibrium_with_force, eq:lbe_interface;
-    // n = 0 where |grad phi| < 1e-12
-    {
+        // g forcing: eq:forcing_term, n = 0 where |grad phi| < 1e-12
         const float gn2 = dx * dx + dy * dy + dz * dz;
         const float amp = (gn2 >= 1e-24f) ? (1.0f - 4.0f * (phi - 0.5f) * (phi - 0.5f)) * P.inv_W * rsqrtf(gn2) : 0.0f;
         const float nx = amp * dx, ny = amp * dy, nz = amp * dz;
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const float Fphi = L::w(a) * (float(L::ex(a)) * nx + float(L::ey(a)) * ny + float(L::ez(a)) * nz);
-            g[a] = g[a] - P.omega_phi * (g[a] - geq[a] + 0.5f * Fphi) + Fphi;
-        }
-    }
-    // f: eq:force_term, eq:equilibrium_modified, eq:mrt_collision with
-    // M^-1 S M = I - (1 - s_nu) P:  f* = f - M^-1 S M (f - feq + F/2) + F
-    //                                  = feq + F/2 + (1 - s_nu) P (f - feq + F/2)
-    {
-        const float ir = 3.0f / rho;
-        float dl[Q], Fa[Q];
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            Fa[a] = L::w(a) * ir * (float(L::ex(a)) * Fx + float(L::ey(a)) * Fy + float(L::ez(a)) * Fz);
-            dl[a] = f[a] - feq[a] + 0.5f * Fa[a];
-        }
+
+        // f: eq:force_term, eq:equilibrium_modified, eq:mrt_collision with
+        // M^-1 S M = I - (1 - s_nu) P:
+        //   f* = f - M^-1 S M (f - feq + F/2) + F = feq + F/2 + (1 - s_nu) P (f - feq + F/2).
+        // The stress-row moments of f - feq + F/2 are combinations of the
+        // non-equilibrium stress E = Pi(f) - p* c_s^2 I - u u (F/2 has none).
+        const float exx = sxx - p3 - ux * ux, eyy = syy - p3 - uy * uy;
+        const float ezz = (L::D == 2) ? 0.0f : szz - p3 - uz * uz;
+        const float exy = sxy - ux * uy, exz = sxz - ux * uz, eyz = syz - uy * uz;
         float ck[L::NS];
-#pragma unroll
-        for (int k = 0; k < L::NS; ++k) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int a = 0; a < Q; ++a)
-                if (L::m(k, a)) acc += float(L::m(k, a)) * dl[a];
-            ck[k] = (1.0f - s_nu) * acc;
+        const float r = 1.0f - s_nu;
+        if constexpr (L::D == 2) {
+            ck[0] = r * (exx - eyy);                        // p_xx row of eq:A1
+            ck[1] = r * exy;                                // p_xy row
+        } else {
+            ck[0] = r * exy;                                // rows 5-9 of eq:A2
+            ck[1] = r * eyz;
+            ck[2] = r * exz;
+            ck[3] = r * (2.0f * exx - eyy - ezz);
+            ck[4] = r * (eyy - ezz);
         }
+        const float ir = 3.0f / rho;
+        const float fxr = Fx * ir, fyr = Fy * ir, fzr = Fz * ir;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
+            const float eF = float(L::ex(a)) * fxr + float(L::ey(a)) * fyr + float(L::ez(a)) * fzr;
+            const float en = float(L::ex(a)) * nx + float(L::ey(a)) * ny + float(L::ez(a)) * nz;
+            float geq, feq;
+            if (a == 0) {
+                geq = geq0;
+                feq = feq0;
+            } else {
+                const float d = gdev<L>(a, ux, uy, uz, uu);
+                geq = phi * (L::w(a) + d);
+                feq = pstar * L::w(a) + d;
+            }
+            // g: eq:equilibrium_with_force, eq:lbe_interface
+            const float Fphi = L::w(a) * en;
+            const float gv = ga(a);
+            const float gs = gv - P.omega_phi * (gv - geq + 0.5f * Fphi) + Fphi;
+            // f
+            const float Fa = L::w(a) * eF;
             float proj = 0.0f;
 #pragma unroll
             for (int k = 0; k < L::NS; ++k)
                 if (L::m(k, a)) proj += L::rw(k, a) * ck[k];
-            f[a] = feq[a] + 0.5f * Fa[a] + proj;
+            emit(a, feq + 0.5f * Fa + proj, gs);
+        }
+    }
+}
+
+// Array form of node_update for the kernels that hold a node in registers.
+template <class L, bool collide>
+__device__ __forceinline__ void node_update(const DevParams& P, float (&f)[L::Q], float (&g)[L::Q],
+                                            const float (&phin)[L::Q], bool inlet_node, float* out)
+{
+    float fo[L::Q], go[L::Q];
+    node_update<L, collide>(
+        P, [&](int a) { return f[a]; }, [&](int a) { return g[a]; }, [&](int a) { return phin[a]; },
+        inlet_node, out, [&](int a, float fs, float gs) { fo[a] = fs; go[a] = gs; });
+    if (collide) {
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) {
+            f[a] = fo[a];
+            g[a] = go[a];
         }
     }
 }
@@ -374,8 +403,10 @@ __device__ __forceinline__ float phi_at(const DevParams& P, const float* __restr
     return s;
 }
 
+// Three resident blocks per SM for D3Q19 (24 warps; the stream form of the
+// node update keeps the register count within 85), four for D2Q9.
 template <class L, int TX, int TY>
-__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1))
+__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (L::D == 3) ? 3 : 4)
 k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const float* __restrict__ fA,
              const float* __restrict__ gA, float* __restrict__ fB, float* __restrict__ gB)
 {
@@ -424,40 +455,36 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const float
             fill(m + 1, m + 1 < m1);
             __syncthreads();
             if (own) {
-                float f[Q], g[Q], phin[Q];
                 const float* sbuf = stash + (m & 1) * Q * NT + tid;
                 const int64_t node = (L::D == 3) ? (int64_t(m) * P.ny + y) * P.nx + x : int64_t(m) * P.nx + x;
-#pragma unroll
-                for (int a = 0; a < Q; ++a) {
-                    f[a] = __ldg(fA + a * N + node);
-                    g[a] = sbuf[a * NT];
-                }
-#pragma unroll
-                for (int a = 0; a < Q; ++a) {
+                const int z = (L::D == 3) ? m : 0;
+                const int yc = (L::D == 3) ? y : m;
+                const bool inlet_node = m == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
+                const float* fnode = fA + node;
+                auto fa = [&](int a) { return __ldg(fnode + a * N); };
+                auto ga = [&](int a) { return sbuf[a * NT]; };
+                auto pa = [&](int a) {
                     const int dm = (L::D == 3) ? L::ez(a) : L::ey(a);
                     const int dy = (L::D == 3) ? L::ey(a) : 0;
                     const float* wslot = win + (((m + dm) % 3 + 3) % 3) * EXT;
-                    phin[a] = wslot[(ty + ((L::D == 3) ? 1 : 0) + dy) * EX + tx + 1 + L::ex(a)];
-                }
-                const bool inlet_node = m == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
-                node_update<L, true>(P, f, g, phin, inlet_node, nullptr);
-                const int z = (L::D == 3) ? m : 0;
-                const int yc = (L::D == 3) ? y : m;
-#pragma unroll
-                for (int a = 0; a < Q; ++a) {
+                    return wslot[(ty + ((L::D == 3) ? 1 : 0) + dy) * EX + tx + 1 + L::ex(a)];
+                };
+                // push streaming (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g)
+                auto emit = [&](int a, float fs, float gs) {
                     int kind = 0;
                     const int xx = map_push(x + L::ex(a), P.nx, P.bc[0], P.bc[1], kind);
                     const int yy = map_push(yc + L::ey(a), P.ny, P.bc[2], P.bc[3], kind);
                     const int zz = (L::D == 3) ? map_push(z + L::ez(a), P.nz, P.bc[4], P.bc[5], kind) : 0;
                     if (kind == 0) {
                         const int64_t t = (int64_t(zz) * P.ny + yy) * P.nx + xx;
-                        fB[a * N + t] = f[a];
-                        gB[a * N + t] = g[a];
-                    } else if (kind == 2) {
-                        fB[L::opp(a) * N + node] = f[a];
-                        gB[L::opp(a) * N + node] = g[a];
-                    }
-                }
+                        fB[a * N + t] = fs;
+                        gB[a * N + t] = gs;
+                    } else if (kind == 2) {             // wall: back to this node, opposite slot
+                        fB[L::opp(a) * N + node] = fs;
+                        gB[L::opp(a) * N + node] = gs;
+                    }                                   // open face: leaves the domain
+                };
+                node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, emit);
             }
             __syncthreads();
         }

@@ -22,7 +22,7 @@
 #include <mutex>
 #include <string>
 
-#include "../../include/lbm.h"
+#include "lbm.h"
 #include "lbm_kernels.cuh"
 
 extern template struct lbm::Launch<lbm::D2Q9>;
