@@ -8,6 +8,7 @@ eq:lbe_interface and the moment identities of the equilibria and forcing
 terms.
 """
 import itertools
+import sys
 import os
 
 import numpy as np
@@ -204,3 +205,28 @@ def test_chemical_potential_vanishes_on_tanh_profile(oracle_mod, W):
     # discrete residual ~ 2.5 / W^2 of the double-well scale beta/8; the
     # printed sign would leave about 3 of it
     assert worst * W * W < 3.0
+
+
+def test_prosperetti_reference_curve_limits():
+    """The repaired Prosperetti curve starts at 1; for small viscosity it
+    oscillates at omega_0 = sqrt(sigma k^3 / (rho_H + rho_L)), and its damping
+    is set by the interfacial boundary layer, so it grows like sqrt(nu)."""
+    pytest.importorskip("scipy")
+    from prosperetti import amplitude
+    k, sigma = 2 * np.pi / 256, 1e-2
+    om0 = np.sqrt(sigma * k ** 3 / 2.0)
+    assert abs(amplitude([0.0], k, 1e-3, sigma, 1.0, 1.0)[0] - 1.0) < 1e-9
+    t = np.linspace(0, 4 * 2 * np.pi / om0, 8001)
+
+    def crossings_and_decay(nu):
+        eta = amplitude(t, k, nu, sigma, 1.0, 1.0)
+        zc = [t[i] - eta[i] * (t[i + 1] - t[i]) / (eta[i + 1] - eta[i])
+              for i in range(len(t) - 1) if eta[i] * eta[i + 1] < 0]
+        env = np.abs(eta)
+        peaks = [i for i in range(1, len(t) - 1) if env[i] >= env[i - 1] and env[i] > env[i + 1]]
+        rate = -np.log(env[peaks[-1]] / env[peaks[0]]) / (t[peaks[-1]] - t[peaks[0]])
+        return np.array(zc), rate
+    zc, r1 = crossings_and_decay(1e-6)
+    assert abs(2 * np.mean(np.diff(zc)) * om0 / (2 * np.pi) - 1) < 5e-3
+    _, r4 = crossings_and_decay(4e-6)
+    assert 1.6 < r4 / r1 < 2.4
