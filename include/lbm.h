@@ -55,6 +55,7 @@ typedef enum {
     LBM_ERR_CUDA = -2,     /* a CUDA runtime call failed */
     LBM_ERR_OOM = -3,      /* device allocation failed */
     LBM_ERR_DIVERGED = -4, /* non-finite populations found by lbm_diag */
+    LBM_ERR_TIMEOUT = -5,  /* reserved: a bounded wait on the device gave up */
     LBM_ERR_STATE = -6     /* call out of order (e.g. step before init) */
 } lbm_status;
 

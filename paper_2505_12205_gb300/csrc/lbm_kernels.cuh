@@ -186,18 +186,12 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
     } else {
         const float uu = ux * ux + uy * uy + uz * uz;
         // Equilibria (eq:equilibrium_function, eq:equilibrium): geq_a = phi
-        // Gamma_a, feq_a = p* w_a + Gamma_a - w_a.  The rest population takes
-        // the remainder so that sum_a geq_a = phi and sum_a feq_a = p* hold to
-        // the rounding of one sum: float32 weights do not add up to exactly 1,
-        // and without this every collision would create or destroy mass.
+        // Gamma_a, feq_a = p* w_a + Gamma_a - w_a.  The rest population (a = 0,
+        // emitted last) takes the remainder so that sum_a geq_a = phi and
+        // sum_a feq_a = p* hold to the rounding of one sum: float32 weights do
+        // not add up to exactly 1, and without this every collision would
+        // create or destroy mass.
         float sg = 0.0f, sf = 0.0f;
-#pragma unroll
-        for (int a = 1; a < Q; ++a) {
-            const float d = gdev<L>(a, ux, uy, uz, uu);
-            sg += phi * (L::w(a) + d);
-            sf += pstar * L::w(a) + d;
-        }
-        const float geq0 = phi - sg, feq0 = pstar - sf;
 
         // g forcing: eq:forcing_term, n = 0 where |grad phi| < 1e-12
         const float gn2 = dx * dx + dy * dy + dz * dz;
@@ -226,19 +220,9 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
         }
         const float ir = 3.0f / rho;
         const float fxr = Fx * ir, fyr = Fy * ir, fzr = Fz * ir;
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
+        auto collide_one = [&](int a, float geq, float feq) {
             const float eF = float(L::ex(a)) * fxr + float(L::ey(a)) * fyr + float(L::ez(a)) * fzr;
             const float en = float(L::ex(a)) * nx + float(L::ey(a)) * ny + float(L::ez(a)) * nz;
-            float geq, feq;
-            if (a == 0) {
-                geq = geq0;
-                feq = feq0;
-            } else {
-                const float d = gdev<L>(a, ux, uy, uz, uu);
-                geq = phi * (L::w(a) + d);
-                feq = pstar * L::w(a) + d;
-            }
             // g: eq:equilibrium_with_force, eq:lbe_interface
             const float Fphi = L::w(a) * en;
             const float gv = ga(a);
@@ -250,7 +234,17 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
             for (int k = 0; k < L::NS; ++k)
                 if (L::m(k, a)) proj += L::rw(k, a) * ck[k];
             emit(a, feq + 0.5f * Fa + proj, gs);
+        };
+#pragma unroll
+        for (int a = 1; a < Q; ++a) {
+            const float d = gdev<L>(a, ux, uy, uz, uu);
+            const float geq = phi * (L::w(a) + d);
+            const float feq = pstar * L::w(a) + d;
+            sg += geq;
+            sf += feq;
+            collide_one(a, geq, feq);
         }
+        collide_one(0, phi - sg, pstar - sf);
     }
 }
 
@@ -469,14 +463,23 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const float
                     const float* wslot = win + (((m + dm) % 3 + 3) % 3) * EXT;
                     return wslot[(ty + ((L::D == 3) ? 1 : 0) + dy) * EX + tx + 1 + L::ex(a)];
                 };
-                // push streaming (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g)
+                // push streaming (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g):
+                // the target of each axis step -1, 0, +1 is mapped once per node
+                // (kind 0 inside or wrapped, 1 open face, 2 wall)
+                int kx[3] = {0, 0, 0}, ky[3] = {0, 0, 0}, kz[3] = {0, 0, 0};
+                const int64_t sxy = int64_t(P.nx) * P.ny;
+                int64_t ox[3], oy[3], oz[3];
+#pragma unroll
+                for (int d = -1; d <= 1; ++d) {
+                    ox[d + 1] = map_push(x + d, P.nx, P.bc[0], P.bc[1], kx[d + 1]);
+                    oy[d + 1] = int64_t(map_push(yc + d, P.ny, P.bc[2], P.bc[3], ky[d + 1])) * P.nx;
+                    oz[d + 1] = (L::D == 3) ? int64_t(map_push(z + d, P.nz, P.bc[4], P.bc[5], kz[d + 1])) * sxy : 0;
+                }
                 auto emit = [&](int a, float fs, float gs) {
-                    int kind = 0;
-                    const int xx = map_push(x + L::ex(a), P.nx, P.bc[0], P.bc[1], kind);
-                    const int yy = map_push(yc + L::ey(a), P.ny, P.bc[2], P.bc[3], kind);
-                    const int zz = (L::D == 3) ? map_push(z + L::ez(a), P.nz, P.bc[4], P.bc[5], kind) : 0;
+                    const int ex = L::ex(a) + 1, ey = L::ey(a) + 1, ez = (L::D == 3) ? L::ez(a) + 1 : 1;
+                    const int kind = max(kx[ex], max(ky[ey], kz[ez]));
                     if (kind == 0) {
-                        const int64_t t = (int64_t(zz) * P.ny + yy) * P.nx + xx;
+                        const int64_t t = oz[ez] + oy[ey] + ox[ex];
                         fB[a * N + t] = fs;
                         gB[a * N + t] = gs;
                     } else if (kind == 2) {             // wall: back to this node, opposite slot
@@ -762,7 +765,10 @@ struct Launch {
     static cudaError_t step_fused(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
                                   cudaStream_t s);
     static cudaError_t fused_geom(const DevParams& P, FusedGeom* G, int* nblocks);
+
     // the same launches, with mark() (which records an event) after each stage
+    // the same launches as step_fused, with mark() recording an event after
+    // each stage
     template <class Mark>
     static cudaError_t step_timed(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
                                   cudaStream_t s, Mark mark);
@@ -848,8 +854,8 @@ cudaError_t Launch<L>::step_timed(const DevParams& P, const FusedGeom& G, int nb
     using Cfg = FusedCfg<L, TX, TY>;
     cudaError_t e;
     if ((e = mark()) != cudaSuccess) return e;      // no separate phi pass in the fused step
-    const dim3 block(TX, (L::D == 3) ? TY : 1);
-    k_step_fused<L, TX, TY><<<nblocks, block, Cfg::smem, s>>>(P, G, b.fA, b.gA, b.fB, b.gB);
+    k_step_fused<L, TX, TY><<<nblocks, dim3(TX, (L::D == 3) ? TY : 1), Cfg::smem, s>>>(P, G, b.fA, b.gA, b.fB,
+                                                                                    b.gB);
     if ((e = mark()) != cudaSuccess) return e;
     const int lastlo = (L::D == 2) ? P.bc[2] : P.bc[4];
     const int lasthi = (L::D == 2) ? P.bc[3] : P.bc[5];

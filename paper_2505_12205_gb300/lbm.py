@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
 
 LBM_D2Q9, LBM_D3Q19 = 0, 1
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_INLET, LBM_BC_OUTFLOW = 0, 1, 2, 3
-LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_STATE = 0, -1, -2, -3, -4, -6
+LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_STATE = \
+    0, -1, -2, -3, -4, -5, -6
 
 # every symbol declared in include/lbm.h
 EXPORTS = ["lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_fields", "lbm_get_populations",

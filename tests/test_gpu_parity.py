@@ -95,6 +95,10 @@ STEP_CASES = {
     "d3q19_periodic": (1, (9, 7, 131), [0] * 6),
     "d3q19_walls": (1, (11, 9, 13), [1, 1, 0, 0, 1, 1]),
     "d3q19_jet": (1, (12, 10, 129), [0, 0, 1, 1, 2, 3]),
+    # grids whose x-y planes are whole numbers of 32 x 8 tiles
+    "d3q19_aligned_periodic": (1, (10, 16, 64), [0] * 6),
+    "d3q19_aligned_walls": (1, (9, 8, 32), [1, 1, 1, 1, 1, 1]),
+    "d3q19_aligned_jet": (1, (12, 16, 32), [0, 0, 0, 0, 2, 3]),
 }
 
 
@@ -172,6 +176,22 @@ def test_rt2d_parity_full_size(lib, orc, report):
     o.step(200)
     r_phi, r_u, _ = o.fields()
     report("rt2d_200", phi_l2=rel_l2(g_phi, r_phi), u_l2=rel_l2(g_u, r_u))
+    assert rel_l2(g_phi, r_phi) <= 1e-5
+    assert rel_l2(g_u, r_u) <= 1e-5
+
+
+def test_jet3d_aligned_parity(lib, orc, report):
+    """Jet on a 32 x 32 x 64 grid (whole 32 x 8 tiles), 100 steps."""
+    p, phi, u, ps = C.jet3d(nx=32, ny=32, nz=64, Rn=5.0)
+    sim = lib.LBM(p)
+    sim.init_fields(phi, u, ps)
+    sim.step(100)
+    g_phi, g_u, _ = sim.fields()
+    o = orc.Oracle(p)
+    o.init_fields(phi, u, ps)
+    o.step(100)
+    r_phi, r_u, _ = o.fields()
+    report("jet3d_aligned_100", phi_l2=rel_l2(g_phi, r_phi), u_l2=rel_l2(g_u, r_u))
     assert rel_l2(g_phi, r_phi) <= 1e-5
     assert rel_l2(g_u, r_u) <= 1e-5
 
