@@ -228,6 +228,8 @@ def run_gpu(args):
 
     nx, ny, nz = args.grid if args.grid else (WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"])
     p, phi, u, ps = C.jet3d(nx=nx, ny=ny, nz=nz, Rn=WORKLOAD["Rn"], We=WORKLOAD["We"])
+    p["storage"] = {"fp32": 0, "fp16": 1, "bf16": 2}[args.storage]
+    elem = 4 if args.storage == "fp32" else 2
     N = p["nx"] * p["ny"] * p["nz"]
     stream = torch.cuda.current_stream()
     sim = lbm.LBM(p, stream=stream)
@@ -265,11 +267,12 @@ def run_gpu(args):
     # roofline of the fused collide-stream kernel
     peak, peak_kind = peaks()
     step_ms = ms_step / max(nrec, 1)
-    achieved = BYTES_PER_LU * N / (step_ms * 1e-3) / 1e9
+    bytes_per_lu = 4 * 19 * elem
+    achieved = bytes_per_lu * N / (step_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": ncu_traffic(),
+            "frac": achieved / peak, "traffic": ncu_traffic() if args.storage == "fp32" else None,
             "kernel": "k_step_fused<D3Q19,32,8> (phi + collide + push-stream, one pass)",
-            "algorithmic_bytes_per_lu": BYTES_PER_LU, "peak_source": peak_kind + " hbm_gbs",
+            "algorithmic_bytes_per_lu": bytes_per_lu, "peak_source": peak_kind + " hbm_gbs",
             "kernel_share_of_step": ms_step / max(ms_phi + ms_step + ms_face, 1e-9)}
 
     # ---------------- end to end through the C ABI with host buffers
@@ -302,15 +305,16 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
+            "dtype": "f32" if args.storage == "fp32" else "f32 arithmetic, %s storage" % args.storage,
+            "data": "synthetic",
             "config": {"workload": WORKLOAD["name"] if not args.grid else
                        "jet3d_D3Q19_%dx%dx%d_fp32 (reduced grid)" % tuple(args.grid), "lattice": "D3Q19",
                        "grid": [p["nx"], p["ny"], p["nz"]], "nodes_per_gpu": N,
-                       "We": WORKLOAD["We"], "storage": "fp32",
+                       "We": WORKLOAD["We"], "storage": args.storage,
                        "l2": "inputs larger than L2: %.1f GB of populations per GPU vs 129 MB L2"
-                             % (4 * 19 * 4 * N / 1e9),
+                             % (4 * 19 * elem * N / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single"},
-            "hbm_gbs_algorithmic": value / ws * 1e6 * BYTES_PER_LU / 1e9 if ws == 1 else None,
+            "hbm_gbs_algorithmic": value / ws * 1e6 * bytes_per_lu / 1e9 if ws == 1 else None,
             "roofline": roof,
             "e2e": e2e,
             "gpu_launches": 3 * args.steps,
@@ -330,6 +334,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="population storage format (arithmetic is float32)")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
                     help="reduced grid of the same jet workload (profiling captures)")
     args = ap.parse_args()

@@ -65,8 +65,10 @@ typedef enum {
  *  visc_model   0: dynamic viscosity linear in phi (eq:dynamic_viscosity),
  *                  tau = mu(phi) / (rho(phi) c_s^2), mu_X = rho_X tau_X c_s^2;
  *               1: relaxation time linear in phi (eq:relaxation_time)
- *  storage      population storage precision: 0 = float32 (the only value
- *               accepted by this version)
+ *  storage      population storage format (arithmetic is float32 always):
+ *               0 = float32; 1 = float16 and 2 = bfloat16, both storing
+ *               each population normalised by its weight: f as
+ *               (f_a / w_a) * storage_scale, g as g_a / w_a - 1/2
  *  rho_L, rho_H densities (eq:density_interpolation)
  *  tau_L, tau_H relaxation times, nu = tau c_s^2 (eq:kinematic_viscosity)
  *  sigma, W     surface tension and interface width xi
@@ -93,6 +95,9 @@ typedef struct {
     double inlet_u;
     double inlet_center[2];
     double inlet_radius;
+    double storage_scale;   /* power-of-two scale of f in 16-bit storage;
+                               0 = 2048 (f_a / w_a from ~3e-8 to ~30 in
+                               float16 normal range) */
 } lbm_params;
 
 /* FP64 diagnostics of the current state (lbm_diag). */
@@ -134,7 +139,9 @@ int lbm_step(lbm_ctx* ctx, int64_t nsteps);
 int lbm_get_fields(lbm_ctx* ctx, float* phi, float* u, float* p, int on_device);
 
 /* Raw state (checkpoint): the post-streaming populations f and g, each
- * [Q][N] float32.  lbm_set_populations restores it exactly. */
+ * [Q][N] float32.  With float32 storage lbm_set_populations restores it
+ * exactly; with 16-bit storage the values are decoded to float32 and
+ * encoded again on restore (exact up to that rounding).  Synchronises. */
 int lbm_get_populations(lbm_ctx* ctx, float* f, float* g, int on_device);
 int lbm_set_populations(lbm_ctx* ctx, const float* f, const float* g, int on_device);
 

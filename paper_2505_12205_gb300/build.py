@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
-UNITS = ["lbm_d2q9.cu", "lbm_d3q19.cu", "lbm_api.cu", "lbm_noalloc.cu"]
+UNITS = ["lbm_d3q19.cu", "lbm_d3q19_f16.cu", "lbm_d3q19_bf16.cu", "lbm_d2q9.cu", "lbm_api.cu",
+         "lbm_noalloc.cu"]
 HEADERS = ["lbm_lattice.cuh", "lbm_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]

@@ -12,14 +12,35 @@
 #include "lbm.h"
 #include "lbm_kernels.cuh"
 
-extern template struct lbm::Launch<lbm::D2Q9>;
-extern template struct lbm::Launch<lbm::D3Q19>;
+extern template struct lbm::Launch<lbm::D2Q9, lbm::StoreF32>;
+extern template struct lbm::Launch<lbm::D2Q9, lbm::StoreF16>;
+extern template struct lbm::Launch<lbm::D2Q9, lbm::StoreBF16>;
+extern template struct lbm::Launch<lbm::D3Q19, lbm::StoreF32>;
+extern template struct lbm::Launch<lbm::D3Q19, lbm::StoreF16>;
+extern template struct lbm::Launch<lbm::D3Q19, lbm::StoreBF16>;
 
 using lbm::D2Q9;
 using lbm::D3Q19;
 using lbm::DevParams;
 using lbm::DiagPartial;
 using lbm::Launch;
+using lbm::StoreBF16;
+using lbm::StoreF16;
+using lbm::StoreF32;
+
+// Calls fn with a default-constructed Launch<lattice, storage> of the context.
+template <class Fn>
+static cudaError_t with_launch(int D, int storage, Fn fn)
+{
+    if (D == 2) {
+        if (storage == 1) return fn(Launch<D2Q9, StoreF16>{});
+        if (storage == 2) return fn(Launch<D2Q9, StoreBF16>{});
+        return fn(Launch<D2Q9, StoreF32>{});
+    }
+    if (storage == 1) return fn(Launch<D3Q19, StoreF16>{});
+    if (storage == 2) return fn(Launch<D3Q19, StoreBF16>{});
+    return fn(Launch<D3Q19, StoreF32>{});
+}
 
 struct lbm_ctx {
     lbm_params p;
@@ -35,6 +56,8 @@ struct lbm_ctx {
     DiagPartial* diag_part = nullptr;
     DiagPartial* diag_res = nullptr;
     int diag_nparts = 0;
+    float* staging = nullptr;       // float32 planes for checkpoints of 16-bit states
+    size_t elem = 4;                // bytes per stored population value
     bool initialised = false;
     // kernel timing: 4 events per recorded step (before phi, after phi,
     // after the collide-stream kernel, after the face kernels)
@@ -74,7 +97,8 @@ static int validate(const lbm_params* p, std::string& why)
     if (!(p->rho_L > 0 && p->rho_H > 0 && p->tau_L > 0 && p->tau_H > 0)) { why = "rho_L, rho_H, tau_L, tau_H must be > 0"; return -1; }
     if (!(p->W > 0 && p->mobility > 0 && p->sigma >= 0)) { why = "W, mobility must be > 0 and sigma >= 0"; return -1; }
     if (p->visc_model != 0 && p->visc_model != 1) { why = "visc_model must be 0 or 1"; return -1; }
-    if (p->storage != 0) { why = "storage must be 0 (float32)"; return -1; }
+    if (p->storage < 0 || p->storage > 2) { why = "storage must be 0 (float32), 1 (float16) or 2 (bfloat16)"; return -1; }
+    if (!(p->storage_scale >= 0)) { why = "storage_scale must be >= 0"; return -1; }
     const int D = p->lattice == LBM_D2Q9 ? 2 : 3, L = D - 1;
     const int n[3] = {p->nx, p->ny, p->nz};
     for (int d = 0; d < D; ++d) {
@@ -111,6 +135,9 @@ static DevParams make_dev(const lbm_params* p, int64_t N)
     d.gx = float(p->force[0]); d.gy = float(p->force[1]);
     d.gz = p->lattice == LBM_D2Q9 ? 0.0f : float(p->force[2]);
     d.rho_ref = float(p->rho_ref);
+    const double sc = p->storage_scale > 0 ? p->storage_scale : 2048.0;
+    d.fscale = float(sc);
+    d.inv_fscale = float(1.0 / sc);
     return d;
 }
 
@@ -126,18 +153,19 @@ static cudaError_t next_event(lbm_ctx* c, cudaEvent_t* ev)
     return cudaEventRecord(*ev, c->stream);
 }
 
-template <class L>
 static cudaError_t dispatch_step(lbm_ctx* c)
 {
-    cudaError_t e;
-    if (c->timing) {
-        cudaEvent_t ev;
-        if ((e = next_event(c, &ev)) != cudaSuccess) return e;
-        e = Launch<L>::step_timed(c->dp, c->geom, c->fused_blocks, c->b, c->stream,
+    cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+        using Ln = decltype(l);
+        if (c->timing) {
+            cudaEvent_t ev;
+            cudaError_t r = next_event(c, &ev);
+            if (r != cudaSuccess) return r;
+            return Ln::step_timed(c->dp, c->geom, c->fused_blocks, c->b, c->stream,
                                   [&]() { return next_event(c, &ev); });
-    } else {
-        e = Launch<L>::step_fused(c->dp, c->geom, c->fused_blocks, c->b, c->stream);
-    }
+        }
+        return Ln::step_fused(c->dp, c->geom, c->fused_blocks, c->b, c->stream);
+    });
     std::swap(c->b.fA, c->b.fB);
     std::swap(c->b.gA, c->b.gB);
     return e;
@@ -175,10 +203,11 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
     cudaGetDevice(&c->device);
     c->dp = make_dev(p, c->N);
 
-    const size_t plane = size_t(c->N) * c->Q * sizeof(float);
-    float** bufs[4] = {&c->b.fA, &c->b.gA, &c->b.fB, &c->b.gB};
-    for (float** b : bufs) {
-        e = cudaMalloc(reinterpret_cast<void**>(b), plane);
+    c->elem = p->storage == 0 ? 4 : 2;
+    const size_t plane = size_t(c->N) * c->Q * c->elem;
+    void** bufs[4] = {&c->b.fA, &c->b.gA, &c->b.fB, &c->b.gB};
+    for (void** b : bufs) {
+        e = cudaMalloc(b, plane);
         if (e != cudaSuccess) {
             int r = cuda_fail(nullptr, e, "cudaMalloc(populations)");
             lbm_destroy(c);
@@ -196,8 +225,7 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
         return r;
     }
     c->diag_res = c->diag_part + c->diag_nparts;
-    e = c->D == 2 ? Launch<D2Q9>::fused_geom(c->dp, &c->geom, &c->fused_blocks)
-                  : Launch<D3Q19>::fused_geom(c->dp, &c->geom, &c->fused_blocks);
+    e = with_launch(c->D, p->storage, [&](auto l) { return decltype(l)::fused_geom(c->dp, &c->geom, &c->fused_blocks); });
     if (e != cudaSuccess) {
         int r = cuda_fail(nullptr, e, "fused step set-up");
         lbm_destroy(c);
@@ -207,11 +235,11 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
     c->dp.u_in = c->face + nface;
     const int L = c->D - 1;
     if (p->bc[2 * L] == LBM_BC_INLET) {
-        e = c->D == 2 ? Launch<D2Q9>::inlet_profile(c->dp, p->inlet_center[0], 0.0, p->inlet_radius, p->W,
-                                                     p->inlet_u, c->face, c->face + nface, c->stream)
-                      : Launch<D3Q19>::inlet_profile(c->dp, p->inlet_center[0], p->inlet_center[1],
-                                                      p->inlet_radius, p->W, p->inlet_u, c->face,
-                                                      c->face + nface, c->stream);
+        e = c->D == 2 ? Launch<D2Q9, StoreF32>::inlet_profile(c->dp, p->inlet_center[0], 0.0, p->inlet_radius,
+                                                               p->W, p->inlet_u, c->face, c->face + nface, c->stream)
+                      : Launch<D3Q19, StoreF32>::inlet_profile(c->dp, p->inlet_center[0], p->inlet_center[1],
+                                                                p->inlet_radius, p->W, p->inlet_u, c->face,
+                                                                c->face + nface, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) {
             int r = cuda_fail(nullptr, e, "inlet profile");
@@ -229,7 +257,7 @@ int lbm_destroy(lbm_ctx* c)
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     cudaFree(c->b.fA); cudaFree(c->b.gA); cudaFree(c->b.fB); cudaFree(c->b.gB);
-    cudaFree(c->b.phi); cudaFree(c->face); cudaFree(c->diag_part);
+    cudaFree(c->b.phi); cudaFree(c->face); cudaFree(c->diag_part); cudaFree(c->staging);
     delete c;
     return LBM_OK;
 }
@@ -286,15 +314,16 @@ int lbm_init_fields(lbm_ctx* c, const float* phi, const float* u, const float* p
     if (!phi) return fail(c, LBM_ERR_ARG, "phi is NULL");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t nb = size_t(c->N) * sizeof(float);
-    // stage the fields in the B planes (Q >= D + 2 planes of N floats)
-    float* s_phi = c->b.fB;
-    float* s_u = c->b.fB + c->N;
-    float* s_p = c->b.fB + c->N * (1 + c->D);
+    // stage the fields in the f buffer B (Q * elem >= 4 (D + 2) bytes per node)
+    float* s_phi = static_cast<float*>(c->b.fB);
+    float* s_u = s_phi + c->N;
+    float* s_p = s_phi + c->N * (1 + c->D);
     LBM_CUDA(c, cudaMemcpyAsync(s_phi, phi, nb, kind, c->stream));
     if (u) LBM_CUDA(c, cudaMemcpyAsync(s_u, u, nb * c->D, kind, c->stream));
     if (pstar) LBM_CUDA(c, cudaMemcpyAsync(s_p, pstar, nb, kind, c->stream));
-    cudaError_t e = c->D == 2 ? Launch<D2Q9>::init(c->dp, s_phi, u ? s_u : nullptr, pstar ? s_p : nullptr, c->b.fA, c->b.gA, c->stream)
-                              : Launch<D3Q19>::init(c->dp, s_phi, u ? s_u : nullptr, pstar ? s_p : nullptr, c->b.fA, c->b.gA, c->stream);
+    cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+        return decltype(l)::init(c->dp, s_phi, u ? s_u : nullptr, pstar ? s_p : nullptr, c->b.fA, c->b.gA, c->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = true;
@@ -307,7 +336,7 @@ int lbm_step(lbm_ctx* c, int64_t nsteps)
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps < 0");
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_fields/lbm_set_populations");
     for (int64_t s = 0; s < nsteps; ++s) {
-        cudaError_t e = c->D == 2 ? dispatch_step<D2Q9>(c) : dispatch_step<D3Q19>(c);
+        cudaError_t e = dispatch_step(c);
         if (e != cudaSuccess) return cuda_fail(c, e, "step kernels");
     }
     return LBM_OK;
@@ -317,12 +346,12 @@ int lbm_get_fields(lbm_ctx* c, float* phi, float* u, float* p, int on_device)
 {
     if (!c) return LBM_ERR_ARG;
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
-    // outputs are computed into the B planes, then copied out
-    float* o_phi = c->b.fB;
-    float* o_u = c->b.fB + c->N;
-    float* o_p = c->b.fB + c->N * (1 + c->D);
-    cudaError_t e = c->D == 2 ? Launch<D2Q9>::fields(c->dp, c->b, o_phi, o_u, o_p, c->stream)
-                              : Launch<D3Q19>::fields(c->dp, c->b, o_phi, o_u, o_p, c->stream);
+    // outputs are computed into the f buffer B, then copied out
+    float* o_phi = static_cast<float*>(c->b.fB);
+    float* o_u = o_phi + c->N;
+    float* o_p = o_phi + c->N * (1 + c->D);
+    cudaError_t e = with_launch(c->D, c->p.storage,
+                                [&](auto l) { return decltype(l)::fields(c->dp, c->b, o_phi, o_u, o_p, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "fields kernel");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const size_t nb = size_t(c->N) * sizeof(float);
@@ -333,15 +362,37 @@ int lbm_get_fields(lbm_ctx* c, float* phi, float* u, float* p, int on_device)
     return LBM_OK;
 }
 
+// float32 staging planes (2 Q N) for checkpoints of a 16-bit state
+static int ensure_staging(lbm_ctx* c)
+{
+    if (c->staging) return LBM_OK;
+    LBM_CUDA(c, cudaMalloc(reinterpret_cast<void**>(&c->staging), 2 * size_t(c->N) * c->Q * sizeof(float)));
+    return LBM_OK;
+}
+
 int lbm_get_populations(lbm_ctx* c, float* f, float* g, int on_device)
 {
     if (!c) return LBM_ERR_ARG;
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const size_t nb = size_t(c->N) * c->Q * sizeof(float);
-    if (f) LBM_CUDA(c, cudaMemcpyAsync(f, c->b.fA, nb, kind, c->stream));
-    if (g) LBM_CUDA(c, cudaMemcpyAsync(g, c->b.gA, nb, kind, c->stream));
-    if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    const void* sf = c->b.fA;
+    const void* sg = c->b.gA;
+    if (c->p.storage != 0) {
+        int r = ensure_staging(c);
+        if (r != LBM_OK) return r;
+        float* fo = c->staging;
+        float* go = c->staging + size_t(c->N) * c->Q;
+        cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+            return decltype(l)::unpack(c->dp, c->b.fA, c->b.gA, fo, go, c->stream);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e, "unpack kernel");
+        sf = fo;
+        sg = go;
+    }
+    if (f) LBM_CUDA(c, cudaMemcpyAsync(f, sf, nb, kind, c->stream));
+    if (g) LBM_CUDA(c, cudaMemcpyAsync(g, sg, nb, kind, c->stream));
+    if (!on_device || c->p.storage != 0) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
 
@@ -351,9 +402,22 @@ int lbm_set_populations(lbm_ctx* c, const float* f, const float* g, int on_devic
     if (!f || !g) return fail(c, LBM_ERR_ARG, "f and g are required");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t nb = size_t(c->N) * c->Q * sizeof(float);
-    LBM_CUDA(c, cudaMemcpyAsync(c->b.fA, f, nb, kind, c->stream));
-    LBM_CUDA(c, cudaMemcpyAsync(c->b.gA, g, nb, kind, c->stream));
-    if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->p.storage == 0) {
+        LBM_CUDA(c, cudaMemcpyAsync(c->b.fA, f, nb, kind, c->stream));
+        LBM_CUDA(c, cudaMemcpyAsync(c->b.gA, g, nb, kind, c->stream));
+    } else {
+        int r = ensure_staging(c);
+        if (r != LBM_OK) return r;
+        float* fi = c->staging;
+        float* gi = c->staging + size_t(c->N) * c->Q;
+        LBM_CUDA(c, cudaMemcpyAsync(fi, f, nb, kind, c->stream));
+        LBM_CUDA(c, cudaMemcpyAsync(gi, g, nb, kind, c->stream));
+        cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+            return decltype(l)::pack(c->dp, fi, gi, c->b.fA, c->b.gA, c->stream);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
+    }
+    if (!on_device || c->p.storage != 0) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = true;
     return LBM_OK;
 }
@@ -362,8 +426,9 @@ int lbm_diag(lbm_ctx* c, double phase_eps, lbm_diag_out* out)
 {
     if (!c || !out) return LBM_ERR_ARG;
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
-    cudaError_t e = c->D == 2 ? Launch<D2Q9>::diag(c->dp, c->b, phase_eps, c->diag_part, c->diag_nparts, c->diag_res, c->stream)
-                              : Launch<D3Q19>::diag(c->dp, c->b, phase_eps, c->diag_part, c->diag_nparts, c->diag_res, c->stream);
+    cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+        return decltype(l)::diag(c->dp, c->b, phase_eps, c->diag_part, c->diag_nparts, c->diag_res, c->stream);
+    });
     if (e != cudaSuccess) return cuda_fail(c, e, "diag kernels");
     DiagPartial r;
     LBM_CUDA(c, cudaMemcpyAsync(&r, c->diag_res, sizeof r, cudaMemcpyDeviceToHost, c->stream));
@@ -388,8 +453,8 @@ int lbm_collide_cells(const lbm_params* p, int64_t n, const float* f, const floa
     if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) return fail(nullptr, LBM_ERR_ARG, "bad lattice");
     DevParams d = make_dev(p, 1);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = p->lattice == LBM_D2Q9 ? Launch<D2Q9>::collide_cells(d, n, f, g, phin, fs, gs, out, s)
-                                           : Launch<D3Q19>::collide_cells(d, n, f, g, phin, fs, gs, out, s);
+    cudaError_t e = p->lattice == LBM_D2Q9 ? Launch<D2Q9, StoreF32>::collide_cells(d, n, f, g, phin, fs, gs, out, s)
+                                           : Launch<D3Q19, StoreF32>::collide_cells(d, n, f, g, phin, fs, gs, out, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "collide cells");
     return LBM_OK;

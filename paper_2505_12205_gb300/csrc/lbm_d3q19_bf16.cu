@@ -1,0 +1,3 @@
+// Kernels of the D3Q19 lattice with bfloat16 storage (explicit instantiation).
+#include "lbm_kernels.cuh"
+template struct lbm::Launch<lbm::D3Q19, lbm::StoreBF16>;

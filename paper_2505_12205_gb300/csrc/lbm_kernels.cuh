@@ -17,6 +17,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "lbm_lattice.cuh"
@@ -36,9 +38,41 @@ struct DevParams {
     float inv_W;           // 1 / xi
     float omega_phi;       // 1 / (tau_phi + 1/2), tau_phi = M / c_s^2
     float gx, gy, gz, rho_ref;
+    float fscale, inv_fscale;   // power-of-two scale of f in 16-bit storage
     // inlet plane profile (face arrays, precomputed in double on the device)
     const float* phi_in;
     const float* u_in;
+};
+
+// ---------------------------------------------------------- storage formats
+//
+// Arithmetic is float32 throughout; the populations may be stored in 16 bits
+// to halve the bytes a step moves.  16-bit formats store each population
+// normalised by its weight: f as (f_a / w_a) * fscale (fscale a power of two,
+// so f_a / w_a = p* + O(u) keeps its relative precision over a wide range),
+// and g as g_a / w_a - 1/2 (in [-1/2, 1/2] up to O(u) overshoot).
+struct StoreF32 {
+    using T = float;
+    __device__ static float f(T v, float, const DevParams&) { return v; }
+    __device__ static float g(T v, float) { return v; }
+    __device__ static T ef(float v, float, const DevParams&) { return v; }
+    __device__ static T eg(float v, float) { return v; }
+};
+
+struct StoreF16 {
+    using T = __half;
+    __device__ static float f(T v, float wa, const DevParams& P) { return __half2float(v) * (wa * P.inv_fscale); }
+    __device__ static float g(T v, float wa) { return wa * (__half2float(v) + 0.5f); }
+    __device__ static T ef(float v, float wa, const DevParams& P) { return __float2half_rn(v * (P.fscale / wa)); }
+    __device__ static T eg(float v, float wa) { return __float2half_rn(v * (1.0f / wa) - 0.5f); }
+};
+
+struct StoreBF16 {
+    using T = __nv_bfloat16;
+    __device__ static float f(T v, float wa, const DevParams& P) { return __bfloat162float(v) * (wa * P.inv_fscale); }
+    __device__ static float g(T v, float wa) { return wa * (__bfloat162float(v) + 0.5f); }
+    __device__ static T ef(float v, float wa, const DevParams& P) { return __float2bfloat16_rn(v * (P.fscale / wa)); }
+    __device__ static T eg(float v, float wa) { return __float2bfloat16_rn(v * (1.0f / wa) - 0.5f); }
 };
 
 // ------------------------------------------------------------ node physics
@@ -303,15 +337,15 @@ __device__ __forceinline__ int map_push(int v, int n, int bclo, int bchi, int& k
 
 // ---------------------------------------------------------------- kernels
 
-template <class L>
+template <class L, class S>
 __global__ void __launch_bounds__(128) k_phi(const __grid_constant__ DevParams P,
-                                             const float* __restrict__ g, float* __restrict__ phi)
+                                             const typename S::T* __restrict__ g, float* __restrict__ phi)
 {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     float s = 0.0f;
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) s += __ldg(g + a * P.N + i);
+    for (int a = 0; a < L::Q; ++a) s += S::g(__ldg(g + a * P.N + i), L::w(a));
     phi[i] = s;
 }
 
@@ -367,8 +401,8 @@ struct FusedCfg {
 // phi at the (possibly out-of-range) node (xx, yy, mm) of the march
 // coordinate mm, with the ghost rules of the faces; stores the node's g into
 // stash (NT-strided) when stash is not null.
-template <class L>
-__device__ __forceinline__ float phi_at(const DevParams& P, const float* __restrict__ gA, int xx, int yy, int mm,
+template <class L, class S>
+__device__ __forceinline__ float phi_at(const DevParams& P, const typename S::T* __restrict__ gA, int xx, int yy, int mm,
                                         float* stash, int stride)
 {
     bool inlet = false;
@@ -390,7 +424,7 @@ __device__ __forceinline__ float phi_at(const DevParams& P, const float* __restr
     float s = 0.0f;
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-        const float v = __ldg(gA + a * N + node);
+        const float v = S::g(__ldg(gA + a * N + node), L::w(a));
         if (stash) stash[a * stride] = v;
         s += v;
     }
@@ -399,10 +433,10 @@ __device__ __forceinline__ float phi_at(const DevParams& P, const float* __restr
 
 // Three resident blocks per SM for D3Q19 (24 warps; the stream form of the
 // node update keeps the register count within 85), four for D2Q9.
-template <class L, int TX, int TY>
+template <class L, class S, int TX, int TY>
 __global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (L::D == 3) ? 3 : 4)
-k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const float* __restrict__ fA,
-             const float* __restrict__ gA, float* __restrict__ fB, float* __restrict__ gB)
+k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typename S::T* __restrict__ fA,
+             const typename S::T* __restrict__ gA, typename S::T* __restrict__ fB, typename S::T* __restrict__ gB)
 {
     using Cfg = FusedCfg<L, TX, TY>;
     constexpr int Q = L::Q, EX = Cfg::EX, EXT = Cfg::EXT, NT = Cfg::NT;
@@ -429,7 +463,7 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const float
             float* wslot = win + ((mm % 3 + 3) % 3) * EXT;
             float* sbuf = stash + (mm & 1) * Q * NT;
             if (own) wslot[(ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 1] =
-                phi_at<L>(P, gA, x, y, mm, keep ? sbuf + tid : nullptr, NT);
+                phi_at<L, S>(P, gA, x, y, mm, keep ? sbuf + tid : nullptr, NT);
             for (int q = tid; q < EXT; q += NT) {
                 const int px = q % EX, py = q / EX;
                 const int xx = x0 - 1 + px;
@@ -438,7 +472,7 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const float
                                       ((L::D == 2) || (py >= 1 && py <= TY && yy < P.ny));
                 // positions beyond the one-node ring of the grid are never read
                 const bool needed = xx <= P.nx && ((L::D == 2) || yy <= P.ny);
-                if (!interior) wslot[q] = needed ? phi_at<L>(P, gA, xx, yy, mm, nullptr, 0) : 0.0f;
+                if (!interior) wslot[q] = needed ? phi_at<L, S>(P, gA, xx, yy, mm, nullptr, 0) : 0.0f;
             }
         };
 
@@ -454,8 +488,8 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const float
                 const int z = (L::D == 3) ? m : 0;
                 const int yc = (L::D == 3) ? y : m;
                 const bool inlet_node = m == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
-                const float* fnode = fA + node;
-                auto fa = [&](int a) { return __ldg(fnode + a * N); };
+                const typename S::T* fnode = fA + node;
+                auto fa = [&](int a) { return S::f(__ldg(fnode + a * N), L::w(a), P); };
                 auto ga = [&](int a) { return sbuf[a * NT]; };
                 auto pa = [&](int a) {
                     const int dm = (L::D == 3) ? L::ez(a) : L::ey(a);
@@ -478,13 +512,14 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const float
                 auto emit = [&](int a, float fs, float gs) {
                     const int ex = L::ex(a) + 1, ey = L::ey(a) + 1, ez = (L::D == 3) ? L::ez(a) + 1 : 1;
                     const int kind = max(kx[ex], max(ky[ey], kz[ez]));
+                    const float wa = L::w(a);           // w of a and of its opposite
                     if (kind == 0) {
                         const int64_t t = oz[ez] + oy[ey] + ox[ex];
-                        fB[a * N + t] = fs;
-                        gB[a * N + t] = gs;
+                        fB[a * N + t] = S::ef(fs, wa, P);
+                        gB[a * N + t] = S::eg(gs, wa);
                     } else if (kind == 2) {             // wall: back to this node, opposite slot
-                        fB[L::opp(a) * N + node] = fs;
-                        gB[L::opp(a) * N + node] = gs;
+                        fB[L::opp(a) * N + node] = S::ef(fs, wa, P);
+                        gB[L::opp(a) * N + node] = S::eg(gs, wa);
                     }                                   // open face: leaves the domain
                 };
                 node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, emit);
@@ -499,8 +534,8 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const float
 // shift is omitted at the inlet, p* cancels, the tangential excess momentum
 // is shared by the two unknowns that carry each tangential component, the
 // phase excess by the unknowns with a tangential component).
-template <class L>
-__global__ void k_inlet(const __grid_constant__ DevParams P, float* __restrict__ fB, float* __restrict__ gB)
+template <class L, class S>
+__global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __restrict__ fB, typename S::T* __restrict__ gB)
 {
     constexpr int Q = L::Q;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -515,8 +550,8 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, float* __restrict__
     float f[Q], g[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        f[a] = fB[a * N + node];
-        g[a] = gB[a * N + node];
+        f[a] = S::f(fB[a * N + node], L::w(a), P);
+        g[a] = S::g(gB[a * N + node], L::w(a));
     }
     float Mx = 0.0f, My = 0.0f, theta = 0.0f;
     int ndiag = 0;
@@ -543,19 +578,20 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, float* __restrict__
         const int ab = L::opp(a);
         const float da = gdev<L>(a, ux, uy, uz, uu), db = gdev<L>(ab, ux, uy, uz, uu);
         const float eM = float(t0) * Mx + float(t1) * My;
-        fB[a * N + node] = f[ab] + (da - db) - 0.5f * eM;      // eq:velocity_boundary_distribution
+        fB[a * N + node] = S::ef(f[ab] + (da - db) - 0.5f * eM, L::w(a), P);   // eq:velocity_boundary_distribution
         const float corr = (t0 != 0 || t1 != 0) ? th_n : 0.0f;
         // eq:unknown_distribution_*: g_a = geq_a - (g_abar - geq_abar) - corr, w_a = w_abar
-        gB[a * N + node] = phin * (2.0f * L::w(a) + da + db) - g[ab] - corr;
+        gB[a * N + node] = S::eg(phin * (2.0f * L::w(a) + da + db) - g[ab] - corr, L::w(a));
     }
 }
 
 // Convective outlet on the high face of the last axis (eq:implicit_convective,
 // eq:convective_f/g): chi(N, t+1) = (chi(N, t) + lambda chi(N-1, t+1)) / (1 + lambda),
 // lambda = clamp(sum_a f_a e_a.n at layer N-1 after streaming, 0, 1).
-template <class L>
-__global__ void k_outlet(const __grid_constant__ DevParams P, const float* __restrict__ fA,
-                         const float* __restrict__ gA, float* __restrict__ fB, float* __restrict__ gB)
+template <class L, class S>
+__global__ void k_outlet(const __grid_constant__ DevParams P, const typename S::T* __restrict__ fA,
+                         const typename S::T* __restrict__ gA, typename S::T* __restrict__ fB,
+                         typename S::T* __restrict__ gB)
 {
     constexpr int Q = L::Q;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -568,14 +604,17 @@ __global__ void k_outlet(const __grid_constant__ DevParams P, const float* __res
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
-        if (en) U += float(en) * fB[a * N + iM];
+        if (en) U += float(en) * S::f(fB[a * N + iM], L::w(a), P);
     }
     const float lam = fminf(fmaxf(U, 0.0f), 1.0f);
     const float inv = 1.0f / (1.0f + lam);
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        fB[a * N + iN] = (fA[a * N + iN] + lam * fB[a * N + iM]) * inv;
-        gB[a * N + iN] = (gA[a * N + iN] + lam * gB[a * N + iM]) * inv;
+        const float wa = L::w(a);
+        const float fo = S::f(fA[a * N + iN], wa, P), fm = S::f(fB[a * N + iM], wa, P);
+        const float go = S::g(gA[a * N + iN], wa), gm = S::g(gB[a * N + iM], wa);
+        fB[a * N + iN] = S::ef((fo + lam * fm) * inv, wa, P);
+        gB[a * N + iN] = S::eg((go + lam * gm) * inv, wa);
     }
 }
 
@@ -600,10 +639,10 @@ __global__ void k_inlet_profile(int nface, int nx, double cx, double cy, double 
 
 // Equilibrium initialisation from float32 fields (eq:equilibrium,
 // eq:equilibrium_function).
-template <class L>
+template <class L, class S>
 __global__ void k_init(const __grid_constant__ DevParams P, const float* __restrict__ phi,
-                       const float* __restrict__ u, const float* __restrict__ pstar, float* __restrict__ f,
-                       float* __restrict__ g)
+                       const float* __restrict__ u, const float* __restrict__ pstar, typename S::T* __restrict__ f,
+                       typename S::T* __restrict__ g)
 {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
@@ -614,15 +653,16 @@ __global__ void k_init(const __grid_constant__ DevParams P, const float* __restr
     equilibria<L>(ph, ps, ux, uy, uz, geq, feq);
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-        g[a * P.N + i] = geq[a];
-        f[a * P.N + i] = feq[a];
+        g[a * P.N + i] = S::eg(geq[a], L::w(a));
+        f[a * P.N + i] = S::ef(feq[a], L::w(a), P);
     }
 }
 
 // Macroscopic fields of the state in A (same device code as the step).
-template <class L>
+template <class L, class S>
 __global__ void __launch_bounds__(128) k_fields(const __grid_constant__ DevParams P,
-                                                const float* __restrict__ fA, const float* __restrict__ gA,
+                                                const typename S::T* __restrict__ fA,
+                                                const typename S::T* __restrict__ gA,
                                                 const float* __restrict__ phi, float* __restrict__ ophi,
                                                 float* __restrict__ ou, float* __restrict__ op)
 {
@@ -635,8 +675,8 @@ __global__ void __launch_bounds__(128) k_fields(const __grid_constant__ DevParam
     float f[Q], g[Q], phin[Q], out[5];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        f[a] = fA[a * N + node];
-        g[a] = gA[a * N + node];
+        f[a] = S::f(fA[a * N + node], L::w(a), P);
+        g[a] = S::g(gA[a * N + node], L::w(a));
     }
     gather_phi<L>(P, phi, x, y, z, phin);
     const bool inlet_node = ((L::D == 3) ? z : y) == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
@@ -658,9 +698,10 @@ struct DiagPartial {
     int pad;
 };
 
-template <class L>
+template <class L, class S>
 __global__ void __launch_bounds__(256) k_diag(const __grid_constant__ DevParams P,
-                                              const float* __restrict__ fA, const float* __restrict__ gA,
+                                              const typename S::T* __restrict__ fA,
+                                              const typename S::T* __restrict__ gA,
                                               const float* __restrict__ phi, double eps,
                                               DiagPartial* __restrict__ part)
 {
@@ -680,8 +721,8 @@ __global__ void __launch_bounds__(256) k_diag(const __grid_constant__ DevParams 
         float f[Q], g[Q], phin[Q], out[5];
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            f[a] = fA[a * N + node];
-            g[a] = gA[a * N + node];
+            f[a] = S::f(fA[a * N + node], L::w(a), P);
+            g[a] = S::g(gA[a * N + node], L::w(a));
             if (!isfinite(f[a]) || !isfinite(g[a])) bad = 1;
         }
         gather_phi<L>(P, phi, x, y, z, phin);
@@ -755,29 +796,33 @@ __global__ void k_collide_cells(const __grid_constant__ DevParams P, int64_t n, 
 
 // ------------------------------------------------------ host-side launchers
 
+// Device buffers of a context; the population planes hold S::T values.
 struct Buffers {
-    float *fA, *gA, *fB, *gB, *phi;
+    void *fA, *gA, *fB, *gB;
+    float* phi;
 };
 
-template <class L>
+template <class L, class S>
 struct Launch {
+    using T = typename S::T;
     // fused single-pass step (k_step_fused + face kernels); geometry from fused_geom
     static cudaError_t step_fused(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
                                   cudaStream_t s);
     static cudaError_t fused_geom(const DevParams& P, FusedGeom* G, int* nblocks);
-
-    // the same launches, with mark() (which records an event) after each stage
     // the same launches as step_fused, with mark() recording an event after
     // each stage
     template <class Mark>
     static cudaError_t step_timed(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
                                   cudaStream_t s, Mark mark);
-    static cudaError_t init(const DevParams& P, const float* phi, const float* u, const float* pstar,
-                            float* f, float* g, cudaStream_t s);
+    static cudaError_t init(const DevParams& P, const float* phi, const float* u, const float* pstar, void* f,
+                            void* g, cudaStream_t s);
     static cudaError_t fields(const DevParams& P, const Buffers& b, float* ophi, float* ou, float* op,
                               cudaStream_t s);
     static cudaError_t diag(const DevParams& P, const Buffers& b, double eps, DiagPartial* part, int nparts,
                             DiagPartial* res, cudaStream_t s);
+    // populations of the state <-> float32 planes [Q][N] (checkpoints)
+    static cudaError_t unpack(const DevParams& P, const void* f, const void* g, float* fo, float* go, cudaStream_t s);
+    static cudaError_t pack(const DevParams& P, const float* fi, const float* gi, void* f, void* g, cudaStream_t s);
     static cudaError_t inlet_profile(const DevParams& P, double cx, double cy, double R, double W, double uj,
                                      float* phi_in, float* u_in, cudaStream_t s);
     static cudaError_t collide_cells(const DevParams& P, int64_t n, const float* f, const float* g,
@@ -789,12 +834,12 @@ template <class L> struct FusedTile;
 template <> struct FusedTile<D2Q9> { static constexpr int TX = 128, TY = 1; };
 template <> struct FusedTile<D3Q19> { static constexpr int TX = 32, TY = 8; };
 
-template <class L>
-cudaError_t Launch<L>::fused_geom(const DevParams& P, FusedGeom* G, int* nblocks)
+template <class L, class S>
+cudaError_t Launch<L, S>::fused_geom(const DevParams& P, FusedGeom* G, int* nblocks)
 {
     constexpr int TX = FusedTile<L>::TX, TY = FusedTile<L>::TY;
     using Cfg = FusedCfg<L, TX, TY>;
-    auto kern = k_step_fused<L, TX, TY>;
+    auto kern = k_step_fused<L, S, TX, TY>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -821,7 +866,6 @@ cudaError_t Launch<L>::fused_geom(const DevParams& P, FusedGeom* G, int* nblocks
         const double eff = (double(items) / double(rounds * slots)) * (double(nm) / work);
         if (eff > best_eff + 1e-9) { best_eff = eff; best = nseg; }
     }
-    G->nseg = best;
     G->seglen = (nm + best - 1) / best;
     G->nseg = (nm + G->seglen - 1) / G->seglen;
     G->items = G->ntiles * G->nseg;
@@ -829,83 +873,125 @@ cudaError_t Launch<L>::fused_geom(const DevParams& P, FusedGeom* G, int* nblocks
     return cudaSuccess;
 }
 
-template <class L>
-cudaError_t Launch<L>::step_fused(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
-                                  cudaStream_t s)
+template <class L, class S>
+cudaError_t Launch<L, S>::step_fused(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
+                                     cudaStream_t s)
 {
-    constexpr int TX = FusedTile<L>::TX, TY = FusedTile<L>::TY;
-    using Cfg = FusedCfg<L, TX, TY>;
-    const dim3 block(TX, (L::D == 3) ? TY : 1);
-    k_step_fused<L, TX, TY><<<nblocks, block, Cfg::smem, s>>>(P, G, b.fA, b.gA, b.fB, b.gB);
-    const int lastlo = (L::D == 2) ? P.bc[2] : P.bc[4];
-    const int lasthi = (L::D == 2) ? P.bc[3] : P.bc[5];
-    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
-    if (lastlo == BC_INLET) k_inlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fB, b.gB);
-    if (lasthi == BC_OUTFLOW) k_outlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fA, b.gA, b.fB, b.gB);
-    return cudaGetLastError();
+    return step_timed(P, G, nblocks, b, s, []() { return cudaSuccess; });
 }
 
-template <class L>
+template <class L, class S>
 template <class Mark>
-cudaError_t Launch<L>::step_timed(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
-                                  cudaStream_t s, Mark mark)
+cudaError_t Launch<L, S>::step_timed(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
+                                     cudaStream_t s, Mark mark)
 {
     constexpr int TX = FusedTile<L>::TX, TY = FusedTile<L>::TY;
     using Cfg = FusedCfg<L, TX, TY>;
+    const T* fA = static_cast<const T*>(b.fA);
+    const T* gA = static_cast<const T*>(b.gA);
+    T* fB = static_cast<T*>(b.fB);
+    T* gB = static_cast<T*>(b.gB);
     cudaError_t e;
     if ((e = mark()) != cudaSuccess) return e;      // no separate phi pass in the fused step
-    k_step_fused<L, TX, TY><<<nblocks, dim3(TX, (L::D == 3) ? TY : 1), Cfg::smem, s>>>(P, G, b.fA, b.gA, b.fB,
-                                                                                    b.gB);
+    k_step_fused<L, S, TX, TY><<<nblocks, dim3(TX, (L::D == 3) ? TY : 1), Cfg::smem, s>>>(P, G, fA, gA, fB, gB);
     if ((e = mark()) != cudaSuccess) return e;
     const int lastlo = (L::D == 2) ? P.bc[2] : P.bc[4];
     const int lasthi = (L::D == 2) ? P.bc[3] : P.bc[5];
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
-    if (lastlo == BC_INLET) k_inlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fB, b.gB);
-    if (lasthi == BC_OUTFLOW) k_outlet<L><<<(nface + 127) / 128, 128, 0, s>>>(P, b.fA, b.gA, b.fB, b.gB);
+    if (lastlo == BC_INLET) k_inlet<L, S><<<(nface + 127) / 128, 128, 0, s>>>(P, fB, gB);
+    if (lasthi == BC_OUTFLOW) k_outlet<L, S><<<(nface + 127) / 128, 128, 0, s>>>(P, fA, gA, fB, gB);
     if ((e = mark()) != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
-template <class L>
-cudaError_t Launch<L>::init(const DevParams& P, const float* phi, const float* u, const float* pstar, float* f,
-                            float* g, cudaStream_t s)
+template <class L, class S>
+cudaError_t Launch<L, S>::init(const DevParams& P, const float* phi, const float* u, const float* pstar, void* f,
+                               void* g, cudaStream_t s)
 {
-    k_init<L><<<unsigned((P.N + 255) / 256), 256, 0, s>>>(P, phi, u, pstar, f, g);
+    k_init<L, S><<<unsigned((P.N + 255) / 256), 256, 0, s>>>(P, phi, u, pstar, static_cast<T*>(f),
+                                                             static_cast<T*>(g));
     return cudaGetLastError();
 }
 
-template <class L>
-cudaError_t Launch<L>::fields(const DevParams& P, const Buffers& b, float* ophi, float* ou, float* op,
-                              cudaStream_t s)
+template <class L, class S>
+cudaError_t Launch<L, S>::fields(const DevParams& P, const Buffers& b, float* ophi, float* ou, float* op,
+                                 cudaStream_t s)
 {
-    k_phi<L><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, b.gA, b.phi);
+    const T* fA = static_cast<const T*>(b.fA);
+    const T* gA = static_cast<const T*>(b.gA);
+    k_phi<L, S><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.phi);
     dim3 grid((P.nx + 127) / 128, P.ny, (L::D == 3) ? P.nz : 1);
-    k_fields<L><<<grid, 128, 0, s>>>(P, b.fA, b.gA, b.phi, ophi, ou, op);
+    k_fields<L, S><<<grid, 128, 0, s>>>(P, fA, gA, b.phi, ophi, ou, op);
     return cudaGetLastError();
 }
 
-template <class L>
-cudaError_t Launch<L>::diag(const DevParams& P, const Buffers& b, double eps, DiagPartial* part, int nparts,
-                            DiagPartial* res, cudaStream_t s)
+template <class L, class S>
+cudaError_t Launch<L, S>::diag(const DevParams& P, const Buffers& b, double eps, DiagPartial* part, int nparts,
+                               DiagPartial* res, cudaStream_t s)
 {
-    k_phi<L><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, b.gA, b.phi);
-    k_diag<L><<<nparts, 256, 0, s>>>(P, b.fA, b.gA, b.phi, eps, part);
+    const T* fA = static_cast<const T*>(b.fA);
+    const T* gA = static_cast<const T*>(b.gA);
+    k_phi<L, S><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.phi);
+    k_diag<L, S><<<nparts, 256, 0, s>>>(P, fA, gA, b.phi, eps, part);
     k_diag_final<L><<<1, 32, 0, s>>>(part, nparts, res);
     return cudaGetLastError();
 }
 
-template <class L>
-cudaError_t Launch<L>::inlet_profile(const DevParams& P, double cx, double cy, double R, double W, double uj,
-                                     float* phi_in, float* u_in, cudaStream_t s)
+template <class L, class S>
+__global__ void k_unpack(const __grid_constant__ DevParams P, const typename S::T* __restrict__ f,
+                         const typename S::T* __restrict__ g, float* __restrict__ fo, float* __restrict__ go)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+        fo[a * P.N + i] = S::f(f[a * P.N + i], L::w(a), P);
+        go[a * P.N + i] = S::g(g[a * P.N + i], L::w(a));
+    }
+}
+
+template <class L, class S>
+__global__ void k_pack(const __grid_constant__ DevParams P, const float* __restrict__ fi,
+                       const float* __restrict__ gi, typename S::T* __restrict__ f, typename S::T* __restrict__ g)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+#pragma unroll
+    for (int a = 0; a < L::Q; ++a) {
+        f[a * P.N + i] = S::ef(fi[a * P.N + i], L::w(a), P);
+        g[a * P.N + i] = S::eg(gi[a * P.N + i], L::w(a));
+    }
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::unpack(const DevParams& P, const void* f, const void* g, float* fo, float* go,
+                                 cudaStream_t s)
+{
+    k_unpack<L, S><<<unsigned((P.N + 255) / 256), 256, 0, s>>>(P, static_cast<const T*>(f),
+                                                               static_cast<const T*>(g), fo, go);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::pack(const DevParams& P, const float* fi, const float* gi, void* f, void* g,
+                               cudaStream_t s)
+{
+    k_pack<L, S><<<unsigned((P.N + 255) / 256), 256, 0, s>>>(P, fi, gi, static_cast<T*>(f), static_cast<T*>(g));
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::inlet_profile(const DevParams& P, double cx, double cy, double R, double W, double uj,
+                                        float* phi_in, float* u_in, cudaStream_t s)
 {
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
     k_inlet_profile<L><<<(nface + 127) / 128, 128, 0, s>>>(nface, P.nx, cx, cy, R, W, uj, phi_in, u_in);
     return cudaGetLastError();
 }
 
-template <class L>
-cudaError_t Launch<L>::collide_cells(const DevParams& P, int64_t n, const float* f, const float* g,
-                                     const float* phin, float* fs, float* gs, float* out, cudaStream_t s)
+template <class L, class S>
+cudaError_t Launch<L, S>::collide_cells(const DevParams& P, int64_t n, const float* f, const float* g,
+                                        const float* phin, float* fs, float* gs, float* out, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     k_collide_cells<L><<<unsigned((n + 127) / 128), 128, 0, s>>>(P, n, f, g, phin, fs, gs, out);

@@ -25,8 +25,8 @@
 #include "lbm.h"
 #include "lbm_kernels.cuh"
 
-extern template struct lbm::Launch<lbm::D2Q9>;
-extern template struct lbm::Launch<lbm::D3Q19>;
+extern template struct lbm::Launch<lbm::D2Q9, lbm::StoreF32>;
+extern template struct lbm::Launch<lbm::D3Q19, lbm::StoreF32>;
 
 namespace lbm {
 int api_validate(const lbm_params* p, std::string& why);
@@ -89,6 +89,7 @@ extern "C" int lbm_diag_noalloc(const lbm_params* p, const float* f, const float
     if (!p || !f || !g || !out) return fail(LBM_ERR_ARG, "lbm_diag_noalloc: NULL argument");
     std::string why;
     if (lbm::api_validate(p, why) != 0) return fail(LBM_ERR_ARG, "lbm_diag_noalloc: " + why);
+    if (p->storage != 0) return fail(LBM_ERR_ARG, "lbm_diag_noalloc: populations must be float32 (storage 0)");
     const int64_t N = int64_t(p->nx) * p->ny * p->nz;
     const int D = p->lattice == LBM_D2Q9 ? 2 : 3;
     const int64_t nface = D == 2 ? p->nx : int64_t(p->nx) * p->ny;
@@ -118,16 +119,16 @@ extern "C" int lbm_diag_noalloc(const lbm_params* p, const float* f, const float
     cudaError_t e = cudaSuccess;
     const int L = D - 1;
     if (p->bc[2 * L] == LBM_BC_INLET) {
-        e = D == 2 ? lbm::Launch<lbm::D2Q9>::inlet_profile(dp, p->inlet_center[0], 0.0, p->inlet_radius, p->W,
+        e = D == 2 ? lbm::Launch<lbm::D2Q9, lbm::StoreF32>::inlet_profile(dp, p->inlet_center[0], 0.0, p->inlet_radius, p->W,
                                                           p->inlet_u, base + kMaxNodes,
                                                           base + kMaxNodes + kMaxFace, s)
-                   : lbm::Launch<lbm::D3Q19>::inlet_profile(dp, p->inlet_center[0], p->inlet_center[1],
+                   : lbm::Launch<lbm::D3Q19, lbm::StoreF32>::inlet_profile(dp, p->inlet_center[0], p->inlet_center[1],
                                                            p->inlet_radius, p->W, p->inlet_u, base + kMaxNodes,
                                                            base + kMaxNodes + kMaxFace, s);
     }
     if (e == cudaSuccess)
-        e = D == 2 ? lbm::Launch<lbm::D2Q9>::diag(dp, b, phase_eps, part, kParts, res, s)
-                   : lbm::Launch<lbm::D3Q19>::diag(dp, b, phase_eps, part, kParts, res, s);
+        e = D == 2 ? lbm::Launch<lbm::D2Q9, lbm::StoreF32>::diag(dp, b, phase_eps, part, kParts, res, s)
+                   : lbm::Launch<lbm::D3Q19, lbm::StoreF32>::diag(dp, b, phase_eps, part, kParts, res, s);
     lbm::DiagPartial h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, res, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

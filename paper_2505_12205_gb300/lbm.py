@@ -44,6 +44,7 @@ class LbmParams(ctypes.Structure):
         ("inlet_u", ctypes.c_double),
         ("inlet_center", ctypes.c_double * 2),
         ("inlet_radius", ctypes.c_double),
+        ("storage_scale", ctypes.c_double),
     ]
 
 
@@ -116,6 +117,7 @@ def make_params(p: dict) -> LbmParams:
     c = list(p.get("inlet_center", (0.0, 0.0))) + [0.0, 0.0]
     s.inlet_center[0], s.inlet_center[1] = float(c[0]), float(c[1])
     s.inlet_radius = float(p.get("inlet_radius", 0.0))
+    s.storage_scale = float(p.get("storage_scale", 0.0))
     return s
 
 

@@ -32,8 +32,8 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_params_struct_layout(lib):
-    # natural alignment of the C struct: 12 int32 then 15 doubles
-    assert ctypes.sizeof(lib.LbmParams) == 12 * 4 + 15 * 8
+    # natural alignment of the C struct: 12 int32 then 16 doubles
+    assert ctypes.sizeof(lib.LbmParams) == 12 * 4 + 16 * 8
     assert lib.LbmParams.rho_L.offset == 48
     assert ctypes.sizeof(lib.LbmDiagOut) == 4 * 8 + 2 * 8 + 2 * 4
 
@@ -50,11 +50,14 @@ def test_no_gpu_means_an_error_not_a_fallback(lib):
 
 def test_ptxas_reports_at_most_token_spills(lib):
     """The D3Q19 step is built for three resident blocks per SM (at most 85
-    registers); ptxas may spill a few bytes for that, never more than 64."""
-    logs = [os.path.join(ROOT, "paper_2505_12205_gb300", "_build", n)
-            for n in ("lbm_d2q9.ptxas.log", "lbm_d3q19.ptxas.log")]
+    registers); ptxas may spill a little for that (most with the 16-bit
+    conversions), never more than 128 bytes a thread."""
+    build_dir = os.path.join(ROOT, "paper_2505_12205_gb300", "_build")
+    logs = [os.path.join(build_dir, n) for n in os.listdir(build_dir) if n.endswith(".ptxas.log")
+            and "api" not in n and "noalloc" not in n]
+    assert len(logs) == 4
     for log in logs:
         txt = open(log).read()
         assert "sm_103a" in txt
         spills = re.findall(r"(\d+) bytes spill stores", txt)
-        assert spills and all(int(s) <= 64 for s in spills)
+        assert spills and all(int(s) <= 128 for s in spills)
