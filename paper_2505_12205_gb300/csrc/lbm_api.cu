@@ -94,6 +94,7 @@ static int validate(const lbm_params* p, std::string& why)
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) { why = "grid sizes must be >= 1"; return -1; }
     if (p->lattice == LBM_D2Q9 && p->nz != 1) { why = "D2Q9 needs nz == 1"; return -1; }
     if (p->nx > 65535 * 128 || p->ny > 65535 || p->nz > 65535) { why = "grid too large for the launch shape"; return -1; }
+    if (int64_t(p->nx) * p->ny * p->nz > int64_t(INT32_MAX)) { why = "grid too large: node indices are 32-bit"; return -1; }
     if (!(p->rho_L > 0 && p->rho_H > 0 && p->tau_L > 0 && p->tau_H > 0)) { why = "rho_L, rho_H, tau_L, tau_H must be > 0"; return -1; }
     if (!(p->W > 0 && p->mobility > 0 && p->sigma >= 0)) { why = "W, mobility must be > 0 and sigma >= 0"; return -1; }
     if (p->visc_model != 0 && p->visc_model != 1) { why = "visc_model must be 0 or 1"; return -1; }
@@ -153,6 +154,12 @@ static cudaError_t next_event(lbm_ctx* c, cudaEvent_t* ev)
     return cudaEventRecord(*ev, c->stream);
 }
 
+static cudaError_t mark_step(void* ctx)
+{
+    cudaEvent_t ev;
+    return next_event(static_cast<lbm_ctx*>(ctx), &ev);
+}
+
 static cudaError_t dispatch_step(lbm_ctx* c)
 {
     cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
@@ -161,8 +168,7 @@ static cudaError_t dispatch_step(lbm_ctx* c)
             cudaEvent_t ev;
             cudaError_t r = next_event(c, &ev);
             if (r != cudaSuccess) return r;
-            return Ln::step_timed(c->dp, c->geom, c->fused_blocks, c->b, c->stream,
-                                  [&]() { return next_event(c, &ev); });
+            return Ln::step_timed(c->dp, c->geom, c->fused_blocks, c->b, c->stream, mark_step, c);
         }
         return Ln::step_fused(c->dp, c->geom, c->fused_blocks, c->b, c->stream);
     });

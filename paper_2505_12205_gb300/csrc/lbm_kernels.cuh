@@ -111,12 +111,57 @@ __device__ __forceinline__ void equilibria(float phi, float pstar, float ux, flo
     feq[0] = pstar - sf;
 }
 
+// Weight class of a direction: |e_a|^2 (0 rest, 1 axis, 2 diagonal); the
+// weights of D2Q9 and D3Q19 are equal within a class.
+template <class L>
+__host__ __device__ constexpr int wclass(int a)
+{
+    return L::ex(a) * L::ex(a) + L::ey(a) * L::ey(a) + L::ez(a) * L::ez(a);
+}
+
+// Directions whose component along axis d (0 x, 1 y, 2 z) equals sign.
+template <class L>
+__host__ __device__ constexpr uint32_t dirmask(int d, int sign)
+{
+    uint32_t m = 0;
+    for (int a = 0; a < L::Q; ++a) {
+        const int e = d == 0 ? L::ex(a) : d == 1 ? L::ey(a) : L::ez(a);
+        if (e == sign) m |= 1u << a;
+    }
+    return m;
+}
+
+template <class L>
+__host__ __device__ constexpr bool rest_is_stress_free()
+{
+    for (int k = 0; k < L::NS; ++k)
+        if (L::m(k, 0) != 0) return false;
+    return true;
+}
+
+// e_a . v without multiplications by the zero or unit components (a product
+// with 0 cannot be folded away in IEEE arithmetic; accumulators start at -0,
+// the identity of addition).
+template <class L>
+__device__ __forceinline__ float edot(int a, float vx, float vy, float vz)
+{
+    float s = -0.0f;
+    if (L::ex(a)) s = L::ex(a) > 0 ? s + vx : s - vx;
+    if (L::ey(a)) s = L::ey(a) > 0 ? s + vy : s - vy;
+    if (L::ez(a)) s = L::ez(a) > 0 ? s + vz : s - vz;
+    return s;
+}
+
 // Macroscopic update and collision of one node, written as a stream over
-// the populations so that no per-population array has to live in registers:
-//   fa(a)   -> f_a,  ga(a) -> g_a   (post-streaming populations; ga is read
-//                                    twice, for phi and for the collision)
-//   pa(a)   -> phi(x + e_a)          (stencil values, pa(0) = phi(x))
+// the populations so that no per-population output array has to live in
+// registers:
+//   fa(a)   -> f_a,  ga(a) -> g_a   (post-streaming populations)
+//   pa(a)   -> phi(x + e_a)          (stencil values; pa(0) = phi(x), the
+//                                     node's own sum_a g_a)
 //   emit(a, f*_a, g*_a)              (post-collision populations, when collide)
+// The directions are taken in opposite pairs (a, abar): sums and differences
+// of a pair give the stencil and the moments, and the equilibria of a pair
+// share their even part.
 // inlet_node: the node lies on the inlet face, where derivatives of phi are
 // not evaluated (the inlet is single phase in the paper's treatment), so the
 // interfacial forces vanish there.  out (may be null): phi, u_x, u_y, u_z, p.
@@ -125,55 +170,71 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
                                             float* out, EM emit)
 {
     constexpr int Q = L::Q;
-    float phi = 0.0f;
-#pragma unroll
-    for (int a = 0; a < Q; ++a) phi += ga(a);        // eq:phase_field_variable
+    constexpr float W1 = L::w(1);                       // axis weight
+    constexpr float W2 = L::w(Q - 1);                   // diagonal weight
+    static_assert(wclass<L>(1) == 1 && wclass<L>(Q - 1) == 2, "direction order");
+    static_assert(rest_is_stress_free<L>(), "the rest population carries no stress moment");
 
-    // eq:gradient_phi, eq:laplacian_phi (c / (c_s^2 dx) = 3, 2 c^2 / (c_s^2 dx^2) = 6)
-    float dx = 0.0f, dy = 0.0f, dz = 0.0f, lap = 0.0f;
-    {
-        const float p0 = pa(0);
+    const float phi = pa(0);                            // eq:phase_field_variable
+
+    // eq:gradient_phi, eq:laplacian_phi over opposite pairs, per weight class
+    // (c / (c_s^2 dx) = 3, 2 c^2 / (c_s^2 dx^2) = 6)
+    float gxs[3] = {-0.0f, -0.0f, -0.0f}, gys[3] = {-0.0f, -0.0f, -0.0f}, gzs[3] = {-0.0f, -0.0f, -0.0f};
+    float lps[3] = {-0.0f, -0.0f, -0.0f};
 #pragma unroll
-        for (int a = 1; a < Q; ++a) {
-            const float v = pa(a);
-            const float wp = 3.0f * L::w(a) * v;
-            if (L::ex(a)) dx += float(L::ex(a)) * wp;
-            if (L::ey(a)) dy += float(L::ey(a)) * wp;
-            if (L::ez(a)) dz += float(L::ez(a)) * wp;
-            lap += L::w(a) * (v - p0);
-        }
+    for (int a = 1; a < Q; ++a) {
+        if (L::opp(a) < a) continue;
+        const int c = wclass<L>(a);
+        const float va = pa(a), vb = pa(L::opp(a));
+        const float dp = va - vb;
+        lps[c] += fmaf(-2.0f, phi, va + vb);            // (phi_a - phi) + (phi_abar - phi)
+        if (L::ex(a)) gxs[c] = L::ex(a) > 0 ? gxs[c] + dp : gxs[c] - dp;
+        if (L::ey(a)) gys[c] = L::ey(a) > 0 ? gys[c] + dp : gys[c] - dp;
+        if (L::ez(a)) gzs[c] = L::ez(a) > 0 ? gzs[c] + dp : gzs[c] - dp;
     }
-    lap *= 6.0f;
+    float dx = fmaf(3.0f * W2, gxs[2], (3.0f * W1) * gxs[1]);
+    float dy = fmaf(3.0f * W2, gys[2], (3.0f * W1) * gys[1]);
+    float dz = (L::D == 2) ? 0.0f : fmaf(3.0f * W2, gzs[2], (3.0f * W1) * gzs[1]);
+    float lap = fmaf(6.0f * W2, lps[2], (6.0f * W1) * lps[1]);
     if (inlet_node) dx = dy = dz = lap = 0.0f;
 
     // phi clamped inside the material properties only
     const float ph = fminf(fmaxf(phi, 0.0f), 1.0f);
     const float rho = P.rho_L + ph * (P.rho_H - P.rho_L);      // eq:density_interpolation
+    const float inv_rho = 1.0f / rho;
     float tau;
     if (P.visc_model == 1) tau = P.tau_L + ph * (P.tau_H - P.tau_L);   // eq:relaxation_time
-    else tau = (P.mu_L + ph * (P.mu_H - P.mu_L)) / (rho * (1.0f / 3.0f));  // eq:dynamic_viscosity
+    else tau = (P.mu_L + ph * (P.mu_H - P.mu_L)) * (3.0f * inv_rho);  // eq:dynamic_viscosity, nu = c_s^2 tau
     const float s_nu = 1.0f / (tau + 0.5f);
 
     // chemical potential (sign reading: 4 beta (phi - phi_L)(phi - phi_H)(phi - phi_0))
     const float mu_phi = 4.0f * P.beta * phi * (phi - 1.0f) * (phi - 0.5f) - P.kappa * lap;
 
-    // zeroth, first and second moments of f (eq:normalized_pressure)
-    float pstar = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
-    float sxx = 0.0f, syy = 0.0f, szz = 0.0f, sxy = 0.0f, sxz = 0.0f, syz = 0.0f;
+    // zeroth, first and second moments of f (eq:normalized_pressure) from
+    // the pair sums s = f_a + f_abar and differences d = f_a - f_abar
+    float pstar, jx = -0.0f, jy = -0.0f, jz = -0.0f;
+    float sxx = -0.0f, syy = -0.0f, szz = -0.0f, sxy = -0.0f, sxz = -0.0f, syz = -0.0f;
+    {
+        float fv[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) {
-        const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-        const float v = fa(a);
-        pstar += v;
-        if (ex) jx += float(ex) * v;
-        if (ey) jy += float(ey) * v;
-        if (ez) jz += float(ez) * v;
-        if (ex) sxx += v;
-        if (ey) syy += v;
-        if (ez) szz += v;
-        if (ex * ey) sxy += float(ex * ey) * v;
-        if (ex * ez) sxz += float(ex * ez) * v;
-        if (ey * ez) syz += float(ey * ez) * v;
+        for (int a = 0; a < Q; ++a) fv[a] = fa(a);
+        pstar = fv[0];
+#pragma unroll
+        for (int a = 1; a < Q; ++a) {
+            if (L::opp(a) < a) continue;
+            const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+            const float s = fv[a] + fv[L::opp(a)], d = fv[a] - fv[L::opp(a)];
+            pstar += s;
+            if (ex) jx = ex > 0 ? jx + d : jx - d;
+            if (ey) jy = ey > 0 ? jy + d : jy - d;
+            if (ez) jz = ez > 0 ? jz + d : jz - d;
+            if (ex) sxx += s;
+            if (ey) syy += s;
+            if (ez) szz += s;
+            if (ex * ey) sxy = ex * ey > 0 ? sxy + s : sxy - s;
+            if (ex * ez) sxz = ex * ez > 0 ? sxz + s : sxz - s;
+            if (ey * ez) syz = ey * ez > 0 ? syz + s : syz - s;
+        }
     }
     const float drho = P.rho_H - P.rho_L;                     // eq:density_gradient_phase_field
     const float rx = drho * dx, ry = drho * dy, rz = drho * dz;
@@ -182,7 +243,7 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
     float Fx = mu_phi * dx + cp * rx + fb * P.gx;              // F_s + F_p + F_b
     float Fy = mu_phi * dy + cp * ry + fb * P.gy;
     float Fz = (L::D == 2) ? 0.0f : mu_phi * dz + cp * rz + fb * P.gz;
-    const float h_rho = 0.5f / rho;
+    const float h_rho = 0.5f * inv_rho;
     const float p3 = pstar * (1.0f / 3.0f);
 
     // Viscous force, eq:viscous_force_wmrt, with the predictor velocity u0.
@@ -195,14 +256,21 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
         const float u0x = jx + Fx * h_rho, u0y = jy + Fy * h_rho, u0z = (L::D == 2) ? 0.0f : jz + Fz * h_rho;
         const float dxx = sxx - p3 - u0x * u0x, dyy = syy - p3 - u0y * u0y;
         const float dzz = (L::D == 2) ? 0.0f : szz - p3 - u0z * u0z;
-        const float dxy = sxy - u0x * u0y, dxz = sxz - u0x * u0z, dyz = syz - u0y * u0z;
+        const float dxy = sxy - u0x * u0y;
         const float iso = (1.0f - s_nu) * (dxx + dyy + dzz) * (1.0f / float(L::D));
-        const float txx = s_nu * dxx + iso, tyy = s_nu * dyy + iso, tzz = s_nu * dzz + iso;
-        const float txy = s_nu * dxy, txz = s_nu * dxz, tyz = s_nu * dyz;
+        const float txx = s_nu * dxx + iso, tyy = s_nu * dyy + iso;
+        const float txy = s_nu * dxy;
         // nu / c_s^2 = tau
-        Fx -= tau * (txx * rx + txy * ry + txz * rz);
-        Fy -= tau * (txy * rx + tyy * ry + tyz * rz);
-        if (L::D == 3) Fz -= tau * (txz * rx + tyz * ry + tzz * rz);
+        if constexpr (L::D == 2) {
+            Fx -= tau * (txx * rx + txy * ry);
+            Fy -= tau * (txy * rx + tyy * ry);
+        } else {
+            const float dxz = sxz - u0x * u0z, dyz = syz - u0y * u0z;
+            const float tzz = s_nu * dzz + iso, txz = s_nu * dxz, tyz = s_nu * dyz;
+            Fx -= tau * (txx * rx + txy * ry + txz * rz);
+            Fy -= tau * (txy * rx + tyy * ry + tyz * rz);
+            Fz -= tau * (txz * rx + tyz * ry + tzz * rz);
+        }
     }
 
     // eq:velocity_update
@@ -219,13 +287,6 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
         return;
     } else {
         const float uu = ux * ux + uy * uy + uz * uz;
-        // Equilibria (eq:equilibrium_function, eq:equilibrium): geq_a = phi
-        // Gamma_a, feq_a = p* w_a + Gamma_a - w_a.  The rest population (a = 0,
-        // emitted last) takes the remainder so that sum_a geq_a = phi and
-        // sum_a feq_a = p* hold to the rounding of one sum: float32 weights do
-        // not add up to exactly 1, and without this every collision would
-        // create or destroy mass.
-        float sg = 0.0f, sf = 0.0f;
 
         // g forcing: eq:forcing_term, n = 0 where |grad phi| < 1e-12
         const float gn2 = dx * dx + dy * dy + dz * dz;
@@ -252,33 +313,58 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
             ck[3] = r * (2.0f * exx - eyy - ezz);
             ck[4] = r * (eyy - ezz);
         }
-        const float ir = 3.0f / rho;
-        const float fxr = Fx * ir, fyr = Fy * ir, fzr = Fz * ir;
-        auto collide_one = [&](int a, float geq, float feq) {
-            const float eF = float(L::ex(a)) * fxr + float(L::ey(a)) * fyr + float(L::ez(a)) * fzr;
-            const float en = float(L::ex(a)) * nx + float(L::ey(a)) * ny + float(L::ez(a)) * nz;
-            // g: eq:equilibrium_with_force, eq:lbe_interface
-            const float Fphi = L::w(a) * en;
-            const float gv = ga(a);
-            const float gs = gv - P.omega_phi * (gv - geq + 0.5f * Fphi) + Fphi;
-            // f
-            const float Fa = L::w(a) * eF;
-            float proj = 0.0f;
-#pragma unroll
-            for (int k = 0; k < L::NS; ++k)
-                if (L::m(k, a)) proj += L::rw(k, a) * ck[k];
-            emit(a, feq + 0.5f * Fa + proj, gs);
-        };
+
+        // g: eq:equilibrium_with_force, eq:lbe_interface,
+        //   g* = g - w_phi (g - geq + F^phi / 2) + F^phi
+        //      = (1 - w_phi) g + w_phi geq + (1 - w_phi / 2) F^phi,  F^phi_a = w_a e_a . n
+        const float om = P.omega_phi, om1 = 1.0f - om, kph = 1.0f - 0.5f * om;
+        // Equilibria (eq:equilibrium_function, eq:equilibrium) with
+        // Gamma_a - w_a = w_a (3 e.u + 4.5 (e.u)^2 - 1.5 u.u), whose even part
+        // is shared by a and abar: geq_a = phi w_a + phi (Gamma_a - w_a),
+        // feq_a = p* w_a + (Gamma_a - w_a).  The rest population (emitted
+        // last) takes the remainder so that sum_a geq_a = phi and
+        // sum_a feq_a = p* hold to the rounding of one sum: float32 weights do
+        // not add up to exactly 1, and without this every collision would
+        // create or destroy mass.
+        const float phw1 = phi * W1, phw2 = phi * W2, pw1 = pstar * W1, pw2 = pstar * W2;
+        const float uw1 = (-1.5f * W1) * uu, uw2 = (-1.5f * W2) * uu;
+        const float kw1 = kph * W1, kw2 = kph * W2;
+        const float fr = 1.5f * inv_rho;                    // F_a / 2 = 1.5 w_a e_a . F / rho
+        const float frx = Fx * fr, fry = Fy * fr, frz = Fz * fr;
+        float sg = -0.0f, sf = -0.0f;
 #pragma unroll
         for (int a = 1; a < Q; ++a) {
-            const float d = gdev<L>(a, ux, uy, uz, uu);
-            const float geq = phi * (L::w(a) + d);
-            const float feq = pstar * L::w(a) + d;
-            sg += geq;
-            sf += feq;
-            collide_one(a, geq, feq);
+            if (L::opp(a) < a) continue;
+            const int b = L::opp(a);
+            const bool diag = wclass<L>(a) == 2;
+            const float W = diag ? W2 : W1;
+            const float eu = edot<L>(a, ux, uy, uz);
+            const float even = fmaf((4.5f * W) * eu, eu, diag ? uw2 : uw1);
+            const float odd = (3.0f * W) * eu;
+            const float da = even + odd, db = even - odd;
+            const float fph = edot<L>(a, nx, ny, nz) * (diag ? kw2 : kw1);
+            const float hf = edot<L>(a, frx, fry, frz) * W;
+            float proj = -0.0f;
+#pragma unroll
+            for (int k = 0; k < L::NS; ++k)
+                if (L::m(k, a)) proj = fmaf(L::rw(k, a), ck[k], proj);
+            const float phw = diag ? phw2 : phw1, pw = diag ? pw2 : pw1;
+            {
+                const float geq = fmaf(phi, da, phw);
+                const float feq = pw + da;
+                sg += geq;
+                sf += feq;
+                emit(a, feq + (proj + hf), fmaf(om1, ga(a), fmaf(om, geq, fph)));
+            }
+            {
+                const float geq = fmaf(phi, db, phw);
+                const float feq = pw + db;
+                sg += geq;
+                sf += feq;
+                emit(b, feq + (proj - hf), fmaf(om1, ga(b), fmaf(om, geq, -fph)));
+            }
         }
-        collide_one(0, phi - sg, pstar - sf);
+        emit(0, pstar - sf, fmaf(om1, ga(0), om * (phi - sg)));
     }
 }
 
@@ -457,30 +543,45 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typen
         const int x = x0 + tx, y = y0 + ty;
         const bool own = x < P.nx && ((L::D == 2) || y < P.ny);
 
-        // phi of plane mm over the extended tile into window slot (mm mod 3);
-        // the interior g of that plane goes to stash buffer (mm mod 2)
-        auto fill = [&](int mm, bool keep) {
-            float* wslot = win + ((mm % 3 + 3) % 3) * EXT;
+        // phi of plane mm over the extended tile into window slot wslot; the
+        // interior g of that plane goes to stash buffer (mm mod 2).  The
+        // one-node ring around the tile's nodes inside the grid (wx x wy of
+        // them) is enumerated on its own, on the first threads, so that only
+        // a few warps take the halo path.
+        const int wx = min(TX, P.nx - x0), wy = (L::D == 3) ? min(TY, P.ny - y0) : 1;
+        const int nh = (L::D == 3) ? 2 * (wx + 2) + 2 * wy : 2;
+        auto fill = [&](int mm, float* wslot, bool keep) {
             float* sbuf = stash + (mm & 1) * Q * NT;
             if (own) wslot[(ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 1] =
                 phi_at<L, S>(P, gA, x, y, mm, keep ? sbuf + tid : nullptr, NT);
-            for (int q = tid; q < EXT; q += NT) {
-                const int px = q % EX, py = q / EX;
-                const int xx = x0 - 1 + px;
-                const int yy = (L::D == 3) ? y0 - 1 + py : 0;
-                const bool interior = px >= 1 && px <= TX && xx < P.nx &&
-                                      ((L::D == 2) || (py >= 1 && py <= TY && yy < P.ny));
-                // positions beyond the one-node ring of the grid are never read
-                const bool needed = xx <= P.nx && ((L::D == 2) || yy <= P.ny);
-                if (!interior) wslot[q] = needed ? phi_at<L, S>(P, gA, xx, yy, mm, nullptr, 0) : 0.0f;
+            for (int h = tid; h < nh; h += NT) {
+                int px, py;
+                if (L::D == 2) {
+                    px = h ? wx + 1 : 0;
+                    py = 0;
+                } else if (h < wx + 2) {
+                    px = h;
+                    py = 0;
+                } else if (h < 2 * (wx + 2)) {
+                    px = h - (wx + 2);
+                    py = wy + 1;
+                } else {
+                    px = ((h - 2 * (wx + 2)) & 1) ? wx + 1 : 0;
+                    py = 1 + ((h - 2 * (wx + 2)) >> 1);
+                }
+                wslot[py * EX + px] = phi_at<L, S>(P, gA, x0 - 1 + px, (L::D == 3) ? y0 - 1 + py : 0, mm, nullptr, 0);
             }
         };
 
+        // window slots of planes m - 1, m, m + 1, rotated after each plane
+        float* wlo = win;
+        float* wmid = win + EXT;
+        float* whi = win + 2 * EXT;
         __syncthreads();
-        fill(m0 - 1, false);
-        fill(m0, true);
+        fill(m0 - 1, wlo, false);
+        fill(m0, wmid, true);
         for (int m = m0; m < m1; ++m) {
-            fill(m + 1, m + 1 < m1);
+            fill(m + 1, whi, m + 1 < m1);
             __syncthreads();
             if (own) {
                 const float* sbuf = stash + (m & 1) * Q * NT + tid;
@@ -491,40 +592,70 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typen
                 const typename S::T* fnode = fA + node;
                 auto fa = [&](int a) { return S::f(__ldg(fnode + a * N), L::w(a), P); };
                 auto ga = [&](int a) { return sbuf[a * NT]; };
+                const int ctr = (ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 1;
                 auto pa = [&](int a) {
                     const int dm = (L::D == 3) ? L::ez(a) : L::ey(a);
                     const int dy = (L::D == 3) ? L::ey(a) : 0;
-                    const float* wslot = win + (((m + dm) % 3 + 3) % 3) * EXT;
-                    return wslot[(ty + ((L::D == 3) ? 1 : 0) + dy) * EX + tx + 1 + L::ex(a)];
+                    const float* wslot = dm < 0 ? wlo : (dm > 0 ? whi : wmid);
+                    return wslot[ctr + dy * EX + L::ex(a)];
                 };
                 // push streaming (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g):
-                // the target of each axis step -1, 0, +1 is mapped once per node
-                // (kind 0 inside or wrapped, 1 open face, 2 wall)
-                int kx[3] = {0, 0, 0}, ky[3] = {0, 0, 0}, kz[3] = {0, 0, 0};
-                const int64_t sxy = int64_t(P.nx) * P.ny;
-                int64_t ox[3], oy[3], oz[3];
+                // per axis the node offsets of the steps -1 and +1 (wrapped on
+                // periodic faces), and the directions whose target lies behind a
+                // wall (bounced back into the opposite slot of this node) or
+                // beyond an open face (they leave the domain)
+                uint32_t wallm = 0, openm = 0;
+                int o[3][2];
+                {
+                    const int pos[3] = {x, yc, z};
+                    const int len[3] = {P.nx, (L::D == 3) ? P.ny : nm, (L::D == 3) ? P.nz : 1};
+                    int stride = 1;
 #pragma unroll
-                for (int d = -1; d <= 1; ++d) {
-                    ox[d + 1] = map_push(x + d, P.nx, P.bc[0], P.bc[1], kx[d + 1]);
-                    oy[d + 1] = int64_t(map_push(yc + d, P.ny, P.bc[2], P.bc[3], ky[d + 1])) * P.nx;
-                    oz[d + 1] = (L::D == 3) ? int64_t(map_push(z + d, P.nz, P.bc[4], P.bc[5], kz[d + 1])) * sxy : 0;
+                    for (int d = 0; d < L::D; ++d) {
+                        o[d][0] = -stride;
+                        o[d][1] = stride;
+                        const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
+                        if (pos[d] == 0) {
+                            if (lo == BC_PERIODIC) o[d][0] = (len[d] - 1) * stride;
+                            else if (lo == BC_WALL) wallm |= dirmask<L>(d, -1);
+                            else openm |= dirmask<L>(d, -1);
+                        }
+                        if (pos[d] == len[d] - 1) {
+                            if (hi == BC_PERIODIC) o[d][1] = -(len[d] - 1) * stride;
+                            else if (hi == BC_WALL) wallm |= dirmask<L>(d, 1);
+                            else openm |= dirmask<L>(d, 1);
+                        }
+                        stride *= len[d];
+                    }
                 }
+                const uint32_t offm = wallm | openm;
+                const int inode = int(node);
                 auto emit = [&](int a, float fs, float gs) {
-                    const int ex = L::ex(a) + 1, ey = L::ey(a) + 1, ez = (L::D == 3) ? L::ez(a) + 1 : 1;
-                    const int kind = max(kx[ex], max(ky[ey], kz[ez]));
                     const float wa = L::w(a);           // w of a and of its opposite
-                    if (kind == 0) {
-                        const int64_t t = oz[ez] + oy[ey] + ox[ex];
+                    const uint32_t bit = 1u << a;
+                    if (!(offm & bit)) {
+                        int t = inode;
+                        if (L::ex(a)) t += o[0][L::ex(a) > 0];
+                        if (L::D == 3) {
+                            if (L::ey(a)) t += o[1][L::ey(a) > 0];
+                            if (L::ez(a)) t += o[2][L::ez(a) > 0];
+                        } else {
+                            if (L::ey(a)) t += o[1][L::ey(a) > 0];
+                        }
                         fB[a * N + t] = S::ef(fs, wa, P);
                         gB[a * N + t] = S::eg(gs, wa);
-                    } else if (kind == 2) {             // wall: back to this node, opposite slot
-                        fB[L::opp(a) * N + node] = S::ef(fs, wa, P);
-                        gB[L::opp(a) * N + node] = S::eg(gs, wa);
+                    } else if (wallm & bit) {           // wall: back to this node, opposite slot
+                        fB[L::opp(a) * N + inode] = S::ef(fs, wa, P);
+                        gB[L::opp(a) * N + inode] = S::eg(gs, wa);
                     }                                   // open face: leaves the domain
                 };
                 node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, emit);
             }
             __syncthreads();
+            float* t = wlo;
+            wlo = wmid;
+            wmid = whi;
+            whi = t;
         }
     }
 }
@@ -809,11 +940,11 @@ struct Launch {
     static cudaError_t step_fused(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
                                   cudaStream_t s);
     static cudaError_t fused_geom(const DevParams& P, FusedGeom* G, int* nblocks);
-    // the same launches as step_fused, with mark() recording an event after
-    // each stage
-    template <class Mark>
+    // the same launches as step_fused, with mark(mctx) recording an event
+    // after each stage
+    using MarkFn = cudaError_t (*)(void*);
     static cudaError_t step_timed(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
-                                  cudaStream_t s, Mark mark);
+                                  cudaStream_t s, MarkFn mark, void* mctx);
     static cudaError_t init(const DevParams& P, const float* phi, const float* u, const float* pstar, void* f,
                             void* g, cudaStream_t s);
     static cudaError_t fields(const DevParams& P, const Buffers& b, float* ophi, float* ou, float* op,
@@ -877,14 +1008,14 @@ template <class L, class S>
 cudaError_t Launch<L, S>::step_fused(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
                                      cudaStream_t s)
 {
-    return step_timed(P, G, nblocks, b, s, []() { return cudaSuccess; });
+    return step_timed(P, G, nblocks, b, s, nullptr, nullptr);
 }
 
 template <class L, class S>
-template <class Mark>
 cudaError_t Launch<L, S>::step_timed(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
-                                     cudaStream_t s, Mark mark)
+                                     cudaStream_t s, MarkFn markfn, void* mctx)
 {
+    auto mark = [&]() { return markfn ? markfn(mctx) : cudaSuccess; };
     constexpr int TX = FusedTile<L>::TX, TY = FusedTile<L>::TY;
     using Cfg = FusedCfg<L, TX, TY>;
     const T* fA = static_cast<const T*>(b.fA);
