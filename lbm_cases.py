@@ -24,7 +24,9 @@ workload sizes used by the benchmark:
   * liquid jet (Sec. 6): circular plug inlet on the z = 0 face, convective
     outlet on the top z face, periodic sides, gravity along the jet;
   * two-phase Poiseuille (Sec. 5.3), flat interface, single-phase shear wave
-    and capillary wave set-ups for the physics checks.
+    and capillary wave set-ups for the physics checks;
+  * batched sweep: many drop and capillary-wave cases of random size and
+    material parameters, advanced together.
 """
 from __future__ import annotations
 
@@ -260,6 +262,46 @@ def capillary_wave2d(L=32, height=None, amp=None, sigma=1e-2, rho_ratio=1.0, nu=
     y0 = ny / 2.0 + amp * np.cos(2.0 * np.pi * x / L)
     phi = tanh_profile(y0 - y, W).astype(np.float32)[None]       # heavy below
     return p, phi, _zeros_u(2, (1, ny, L)), None
+
+
+# ---------------------------------------------------- batched sweep cases
+
+def sweep_case(kind, L, rho_ratio, sigma, R=None, W=5.0, mobility=0.02, tau=0.5):
+    """One case of a parameter sweep on an L x L D2Q9 grid with equal
+    kinematic viscosity in both phases (tau_L = tau_H, tau linear in phi, so
+    tau is the same everywhere):
+      kind 0: stationary drop of radius R, centred, periodic box (Sec. 5.2);
+      kind 1: capillary wave (Sec. 5.1), heavy fluid below, interface
+              y = L/2 + 0.01 L cos(2 pi x / L), walls top and bottom,
+              periodic x."""
+    p = base_params(D2Q9, L, L, 1, rho_H=1.0, rho_L=1.0 / rho_ratio, tau_H=tau, tau_L=tau,
+                    sigma=sigma, W=W, mobility=mobility, visc_model=1)
+    y, x = np.meshgrid(np.arange(L, dtype=np.float64), np.arange(L, dtype=np.float64),
+                       indexing="ij")
+    if kind == 0:
+        c = (L - 1) / 2.0
+        phi = tanh_profile(R - np.sqrt((x - c) ** 2 + (y - c) ** 2), W)
+    else:
+        p["bc"] = [PERIODIC, PERIODIC, WALL, WALL, PERIODIC, PERIODIC]
+        y0 = L / 2.0 + 0.01 * L * np.cos(2.0 * np.pi * x / L)
+        phi = tanh_profile(y0 - y, W)
+    return p, phi.astype(np.float32)[None], _zeros_u(2, (1, L, L)), None
+
+
+def sweep_cases(n=512, L_min=64, L_max=512, seed_offset=4):
+    """The seeded sweep of n cases: L ~ U{L_min..L_max}, kind ~ Bernoulli(1/2)
+    (drop / capillary wave), drop radius R ~ U[8, 0.3 L], density ratio
+    log-uniform in [10, 1000], sigma log-uniform in [1e-5, 1e-3]."""
+    r = rng(seed_offset)
+    out = []
+    for _ in range(n):
+        L = int(r.integers(L_min, L_max + 1))
+        kind = int(r.integers(0, 2))
+        R = float(r.uniform(8.0, max(8.0, 0.3 * L)))
+        rho_ratio = float(np.exp(r.uniform(np.log(10.0), np.log(1000.0))))
+        sigma = float(np.exp(r.uniform(np.log(1e-5), np.log(1e-3))))
+        out.append(sweep_case(kind, L, rho_ratio, sigma, R=R))
+    return out
 
 
 # ------------------------------------------------- random states (1 step)
