@@ -20,6 +20,12 @@ the FP64 oracle on a slab of the same workload on the host cores.
 `--impl reference` times the FP64 CPU oracle (the baseline of this project)
 on a bounded slab of the same workload instead.
 
+`--workload sweep` measures the batched sweep instead: 512 seeded 2D cases
+(drops and capillary waves, L x L with L uniform in 64..512, about 51 M nodes,
+float16 storage by default) advanced together by the batch API, reported as
+cases per hour of 5000 steps, beside the same cases stepped one context per
+case (one launch per case and step) on the same GPU.
+
 Multi-GPU (torchrun): independent replicas, one per GPU (weak scaling); the
 only collectives are the timing barrier and the max over ranks.
 """
@@ -327,6 +333,151 @@ def run_gpu(args):
     return 0
 
 
+SWEEP = dict(name="sweep512_D2Q9_L64-512_drop+capillary-wave", ncases=512, steps_per_case=5000)
+
+
+def run_sweep(args):
+    """Cases per hour of the batched sweep vs one context per case."""
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2505_12205_gb300 import build, lbm
+    build.build()
+    storage = {"fp32": 0, "fp16": 1, "bf16": 2}[args.storage or "fp16"]
+    if storage == 2:
+        raise SystemExit("the batched sweep stores float32 or float16")
+    elem = 4 if storage == 0 else 2
+    cases = C.sweep_cases(n=SWEEP["ncases"], seed_offset=4 + rank)
+    for c in cases:
+        c[0]["storage"] = storage
+    nodes = sum(c[0]["nx"] * c[0]["ny"] for c in cases)
+    ncases = len(cases)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import oracle
+        oracle.build()
+        p, phi, u, ps = C.sweep_case(0, 256, 100.0, 1e-4, R=60.0)
+        o = oracle.Oracle(p)
+        o.init_fields(phi, u, ps)
+        o.step(1)
+        t0, n = time.perf_counter(), 0
+        while time.perf_counter() - t0 < 10.0 and n < 2000:
+            o.step(1)
+            n += 1
+        el = time.perf_counter() - t0
+        o.close()
+        mlups_cpu = 256 * 256 * n / el / 1e6
+        cph_cpu = ncases * 3600.0 / (nodes * SWEEP["steps_per_case"] / (mlups_cpu * 1e6))
+        cpu = {"value": cph_cpu, "unit": "cases/h", "cores": oracle.threads(), "kind": "oracle",
+               "sample": "one 256x256 drop case of the sweep, %d steps, %.1f s (%.2f MLUPS), scaled to the "
+                         "sweep's %d nodes x %d steps" % (n, el, mlups_cpu, nodes, SWEEP["steps_per_case"])}
+
+    stream = torch.cuda.current_stream()
+    batch = lbm.Batch([c[0] for c in cases], stream=stream)
+    for i, (p, phi, u, ps) in enumerate(cases):
+        batch.init_fields(i, phi, u, ps)
+    plan = batch.tune(trial_steps=3)
+    batch.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    ms_step = ms / args.steps
+    cph = ws * ncases * 3600.0 / (ms_step * 1e-3 * SWEEP["steps_per_case"])
+    finite = all(batch.diag(i)["finite"] == 1 for i in range(0, ncases, 37))
+
+    # the same cases, one context each, stepped in turn (one launch per case and step)
+    sims = []
+    for p, phi, u, ps in cases:
+        s = lbm.LBM(p, stream=stream)
+        s.init_fields(phi, u, ps)
+        sims.append(s)
+    for s in sims:
+        s.step(1)
+    torch.cuda.synchronize()
+    kp = max(2, args.steps // 10)
+    e0.record(stream)
+    for _ in range(kp):
+        for s in sims:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = max_over_ranks(e0.elapsed_time(e1)) / kp
+    for s in sims:
+        s.close()
+    cph_plain = ws * ncases * 3600.0 / (ms_plain * 1e-3 * SWEEP["steps_per_case"])
+
+    # end to end through the C ABI with host buffers: fields of every case in,
+    # the steps, fields of every case out
+    hostf = [(torch.from_numpy(phi).pin_memory(), torch.from_numpy(u).pin_memory()) for _, phi, u, _ in cases]
+    outs = [(torch.empty(c[0]["nx"] * c[0]["ny"], dtype=torch.float32).pin_memory(),
+             torch.empty(2 * c[0]["nx"] * c[0]["ny"], dtype=torch.float32).pin_memory()) for c in cases]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, (ph, uu) in enumerate(hostf):
+        lbm.lbm_batch_init_fields(batch._h, i, ph, uu, None)
+    batch.step(args.steps)
+    for i, (oph, ou) in enumerate(outs):
+        lbm.lbm_batch_get_fields(batch._h, i, oph, ou, None)
+    te2e = max_over_ranks(time.perf_counter() - t0)
+    h2d = sum((a.numel() + b.numel()) * 4 for a, b in hostf)
+    d2h = sum((a.numel() + b.numel()) * 4 for a, b in outs)
+    batch.close()
+
+    bytes_per_lu = 4 * 9 * elem
+    peak, peak_kind = peaks()
+    achieved = bytes_per_lu * nodes / (ms_step * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": "cases_per_hour", "value": cph, "unit": "cases/h", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 arithmetic, %s storage" % ("fp16" if storage else "fp32"),
+            "data": "synthetic",
+            "config": {"workload": SWEEP["name"], "cases": ncases, "nodes": nodes,
+                       "steps_per_case": SWEEP["steps_per_case"], "storage": "fp16" if storage else "fp32",
+                       "l2": "inputs larger than L2: %.2f GB of populations vs 129 MB L2"
+                             % (4 * 9 * elem * nodes / 1e9),
+                       "plan": plan, "parallelism": "replicas" if ws > 1 else "single"},
+            "mlups": nodes * ws / (ms_step * 1e-3) / 1e6,
+            "plain": {"value": cph_plain, "unit": "cases/h", "ms_per_step_all_cases": ms_plain,
+                      "note": "one context per case, every case stepped in turn (one launch per case and step)"},
+            "speedup_vs_plain": cph / cph_plain,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_step_batch<D2Q9> (all classes of one step, concurrent)",
+                         "algorithmic_bytes_per_lu": bytes_per_lu, "peak_source": peak_kind + " hbm_gbs"},
+            "e2e": {"value": ws * ncases * 3600.0 / (te2e / args.steps * SWEEP["steps_per_case"]),
+                    "unit": "cases/h", "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "note": "fields of every case in from pinned host, %d steps, fields back" % args.steps},
+            "fields_finite": finite,
+            "gpu_launches": plan["nclasses"] * args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,8 +485,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"],
-                    help="population storage format (arithmetic is float32)")
+    ap.add_argument("--storage", default=None, choices=["fp32", "fp16", "bf16"],
+                    help="population storage format (arithmetic is float32); default fp32 for the "
+                         "jet, fp16 for the sweep")
+    ap.add_argument("--workload", default="jet", choices=["jet", "sweep"])
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
                     help="reduced grid of the same jet workload (profiling captures)")
     args = ap.parse_args()
@@ -343,6 +496,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
+    if args.storage is None:
+        args.storage = "fp32"
     return run_gpu(args)
 
 

@@ -204,6 +204,84 @@ int lbm_destroy(lbm_ctx* ctx);
 int lbm_collide_cells(const lbm_params* p, int64_t n, const float* f, const float* g,
                       const float* phin, float* fs, float* gs, float* out, void* stream);
 
+/* ---------------------------------------------------------- batched sweeps
+ *
+ * A batch holds many independent cases of one lattice and one storage format
+ * (float32 or float16), each with its own grid and physical parameters, and
+ * advances all of them together: one time step of the batch is one time step
+ * (the fused update of Algorithms 1-3) of every case.  Faces must be periodic
+ * or walls (no inlet or outlet).  The cases are grouped into size classes by
+ * nx; each class runs one persistent kernel per step over a device work list
+ * of (case, tile segment) items, taken from a per-launch counter so that
+ * items of unequal size balance themselves, and the classes run concurrently
+ * on their own streams.  The steps are recorded once into CUDA graphs and
+ * replayed.  A plan gives, per class, the tile width, the planes per work
+ * item and the persistent blocks per SM; lbm_batch_tune measures candidate
+ * plans on the batch itself and keeps the fastest.  Each case computes
+ * exactly what a context of its own (lbm_create with the same parameters)
+ * computes, bit for bit.
+ *
+ * The batch runs on `stream`; with stream == NULL it owns a blocking stream
+ * (the legacy default stream cannot be recorded into a graph).  Calls that
+ * return data synchronise that stream. */
+typedef struct lbm_batch lbm_batch;   /* opaque; owns all device memory */
+
+#define LBM_BATCH_MAX_CLASSES 8
+
+typedef struct {
+    int32_t nclasses;                           /* size classes in use */
+    int32_t nx_max[LBM_BATCH_MAX_CLASSES];      /* class k holds cases with nx_max[k-1] < nx <= nx_max[k] */
+    int32_t ncases[LBM_BATCH_MAX_CLASSES];      /* cases in the class */
+    int32_t tile_x[LBM_BATCH_MAX_CLASSES];      /* tile width: 32, 64 or 128 (D2Q9), 32 (D3Q19, 32 x 8) */
+    int32_t seglen[LBM_BATCH_MAX_CLASSES];      /* planes of the march axis per work item (>= 1) */
+    int32_t blocks_per_sm[LBM_BATCH_MAX_CLASSES]; /* persistent blocks per SM (1 .. occupancy) */
+    double ms_per_step[LBM_BATCH_MAX_CLASSES];  /* last measurement of lbm_batch_tune (0 if none) */
+} lbm_batch_plan;
+
+/* Create a batch of ncases cases from params[0 .. ncases-1] (each validated
+ * like lbm_create; all with the same lattice and storage, storage 0 or 1,
+ * faces periodic or wall).  Allocates the populations of every case (two
+ * buffers per set).  Returns LBM_ERR_ARG, LBM_ERR_CUDA or LBM_ERR_OOM on
+ * failure (*out = NULL; text from lbm_batch_last_error(NULL)). */
+int lbm_batch_create(const lbm_params* params, int32_t ncases, void* stream, lbm_batch** out);
+
+/* Equilibrium initialisation of case c from its fields, as lbm_init_fields
+ * (phi [nz][ny][nx]; u D planes or NULL; pstar or NULL). */
+int lbm_batch_init_fields(lbm_batch* b, int32_t c, const float* phi, const float* u, const float* pstar,
+                          int32_t on_device);
+
+/* Advance every case by nsteps time steps (enqueued; returns at once).
+ * LBM_ERR_STATE if a case has not been initialised. */
+int lbm_batch_step(lbm_batch* b, int64_t nsteps);
+
+/* Macroscopic fields of case c, as lbm_get_fields. */
+int lbm_batch_get_fields(lbm_batch* b, int32_t c, float* phi, float* u, float* p, int32_t on_device);
+
+/* FP64 diagnostics of case c, as lbm_diag. */
+int lbm_batch_diag(lbm_batch* b, int32_t c, double phase_eps, lbm_diag_out* out);
+
+/* Read or replace the plan.  set: each class's fields tile_x, seglen and
+ * blocks_per_sm are checked (LBM_ERR_ARG when out of range); nclasses,
+ * nx_max and ncases must equal those of the batch. */
+int lbm_batch_get_plan(const lbm_batch* b, lbm_batch_plan* plan);
+int lbm_batch_set_plan(lbm_batch* b, const lbm_batch_plan* plan);
+
+/* Autotuner: for every class, time each candidate (tile width, planes per
+ * item, blocks per SM) over trial_steps launches of that class alone (one
+ * step from the current state, repeated: the state is not advanced), keep
+ * the fastest, and return the resulting plan (may be NULL).  Synchronises. */
+int lbm_batch_tune(lbm_batch* b, int32_t trial_steps, lbm_batch_plan* plan);
+
+/* Wait for the batch's queued work. */
+int lbm_batch_sync(lbm_batch* b);
+
+/* Last error text of b (never NULL); with b == NULL, that of the last failed
+ * lbm_batch_create on this thread. */
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* Free all device memory of b (after synchronising its stream). */
+int lbm_batch_destroy(lbm_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

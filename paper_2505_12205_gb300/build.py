@@ -1,7 +1,8 @@
 """In-tree build of the CUDA library ``_build/liblbm.so`` for sm_103a.
 
-The three translation units (one per lattice plus the C ABI) are compiled in
-parallel with nvcc and linked into a shared library with a static CUDA
+The translation units (kernels per lattice and storage format, batched-step
+kernels, the C ABI of contexts and of batches, the allocation-free
+diagnostics) are compiled in parallel with nvcc and linked into a shared library with a static CUDA
 runtime.  A content hash of the sources and flags decides whether a rebuild
 is needed.
 """
@@ -18,8 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
-UNITS = ["lbm_d3q19.cu", "lbm_d3q19_f16.cu", "lbm_d3q19_bf16.cu", "lbm_d2q9.cu", "lbm_api.cu",
-         "lbm_noalloc.cu"]
+UNITS = ["lbm_d3q19.cu", "lbm_d3q19_f16.cu", "lbm_d3q19_bf16.cu", "lbm_d2q9.cu", "lbm_batch_d2q9.cu",
+         "lbm_batch_d3q19.cu", "lbm_api.cu", "lbm_batch.cu", "lbm_noalloc.cu"]
 HEADERS = ["lbm_lattice.cuh", "lbm_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]

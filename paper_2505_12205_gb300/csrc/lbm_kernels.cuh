@@ -59,20 +59,23 @@ struct StoreF32 {
     __device__ static T eg(float v, float) { return v; }
 };
 
+// The conversions use explicitly rounded operations (no contraction into a
+// neighbouring multiply-add), so that every kernel that stores or loads a
+// population rounds it the same way.
 struct StoreF16 {
     using T = __half;
-    __device__ static float f(T v, float wa, const DevParams& P) { return __half2float(v) * (wa * P.inv_fscale); }
-    __device__ static float g(T v, float wa) { return wa * (__half2float(v) + 0.5f); }
-    __device__ static T ef(float v, float wa, const DevParams& P) { return __float2half_rn(v * (P.fscale / wa)); }
-    __device__ static T eg(float v, float wa) { return __float2half_rn(v * (1.0f / wa) - 0.5f); }
+    __device__ static float f(T v, float wa, const DevParams& P) { return __fmul_rn(__half2float(v), wa * P.inv_fscale); }
+    __device__ static float g(T v, float wa) { return __fmul_rn(wa, __fadd_rn(__half2float(v), 0.5f)); }
+    __device__ static T ef(float v, float wa, const DevParams& P) { return __float2half_rn(__fmul_rn(v, P.fscale / wa)); }
+    __device__ static T eg(float v, float wa) { return __float2half_rn(__fmaf_rn(v, 1.0f / wa, -0.5f)); }
 };
 
 struct StoreBF16 {
     using T = __nv_bfloat16;
-    __device__ static float f(T v, float wa, const DevParams& P) { return __bfloat162float(v) * (wa * P.inv_fscale); }
-    __device__ static float g(T v, float wa) { return wa * (__bfloat162float(v) + 0.5f); }
-    __device__ static T ef(float v, float wa, const DevParams& P) { return __float2bfloat16_rn(v * (P.fscale / wa)); }
-    __device__ static T eg(float v, float wa) { return __float2bfloat16_rn(v * (1.0f / wa) - 0.5f); }
+    __device__ static float f(T v, float wa, const DevParams& P) { return __fmul_rn(__bfloat162float(v), wa * P.inv_fscale); }
+    __device__ static float g(T v, float wa) { return __fmul_rn(wa, __fadd_rn(__bfloat162float(v), 0.5f)); }
+    __device__ static T ef(float v, float wa, const DevParams& P) { return __float2bfloat16_rn(__fmul_rn(v, P.fscale / wa)); }
+    __device__ static T eg(float v, float wa) { return __float2bfloat16_rn(__fmaf_rn(v, 1.0f / wa, -0.5f)); }
 };
 
 // ------------------------------------------------------------ node physics
@@ -517,146 +520,208 @@ __device__ __forceinline__ float phi_at(const DevParams& P, const typename S::T*
     return s;
 }
 
-// Three resident blocks per SM for D3Q19 (24 warps; the stream form of the
-// node update keeps the register count within 85), four for D2Q9.
+// One work item of the fused step: the tile (x0, y0) over the planes
+// [m0, m1) of the march axis.  smem: the phi window [3][EY][EX] followed by
+// the stash [2][Q][NT]; every thread of the block calls this.
 template <class L, class S, int TX, int TY>
-__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (L::D == 3) ? 3 : 4)
-k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typename S::T* __restrict__ fA,
-             const typename S::T* __restrict__ gA, typename S::T* __restrict__ fB, typename S::T* __restrict__ gB)
+__device__ __forceinline__ void fused_item(const DevParams& P, const typename S::T* __restrict__ fA,
+                                           const typename S::T* __restrict__ gA, typename S::T* __restrict__ fB,
+                                           typename S::T* __restrict__ gB, int x0, int y0, int m0, int m1,
+                                           float* smem)
 {
     using Cfg = FusedCfg<L, TX, TY>;
     constexpr int Q = L::Q, EX = Cfg::EX, EXT = Cfg::EXT, NT = Cfg::NT;
-    extern __shared__ float smem[];
     float* win = smem;                    // [3][EY][EX]
     float* stash = smem + 3 * EXT;        // [2][Q][NT]
     const int tid = threadIdx.x + ((L::D == 3) ? threadIdx.y * TX : 0);
     const int tx = threadIdx.x, ty = (L::D == 3) ? threadIdx.y : 0;
     const int nm = (L::D == 3) ? P.nz : P.ny;       // length of the march axis
     const int64_t N = P.N;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool own = x < P.nx && ((L::D == 2) || y < P.ny);
 
+    // phi of plane mm over the extended tile into window slot wslot; the
+    // interior g of that plane goes to stash buffer (mm mod 2).  The
+    // one-node ring around the tile's nodes inside the grid (wx x wy of
+    // them) is enumerated on its own, on the first threads, so that only
+    // a few warps take the halo path.
+    const int wx = min(TX, P.nx - x0), wy = (L::D == 3) ? min(TY, P.ny - y0) : 1;
+    const int nh = (L::D == 3) ? 2 * (wx + 2) + 2 * wy : 2;
+    auto fill = [&](int mm, float* wslot, bool keep) {
+        float* sbuf = stash + (mm & 1) * Q * NT;
+        if (own) wslot[(ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 1] =
+            phi_at<L, S>(P, gA, x, y, mm, keep ? sbuf + tid : nullptr, NT);
+        for (int h = tid; h < nh; h += NT) {
+            int px, py;
+            if (L::D == 2) {
+                px = h ? wx + 1 : 0;
+                py = 0;
+            } else if (h < wx + 2) {
+                px = h;
+                py = 0;
+            } else if (h < 2 * (wx + 2)) {
+                px = h - (wx + 2);
+                py = wy + 1;
+            } else {
+                px = ((h - 2 * (wx + 2)) & 1) ? wx + 1 : 0;
+                py = 1 + ((h - 2 * (wx + 2)) >> 1);
+            }
+            wslot[py * EX + px] = phi_at<L, S>(P, gA, x0 - 1 + px, (L::D == 3) ? y0 - 1 + py : 0, mm, nullptr, 0);
+        }
+    };
+
+    // window slots of planes m - 1, m, m + 1, rotated after each plane
+    float* wlo = win;
+    float* wmid = win + EXT;
+    float* whi = win + 2 * EXT;
+    __syncthreads();
+    fill(m0 - 1, wlo, false);
+    fill(m0, wmid, true);
+    for (int m = m0; m < m1; ++m) {
+        fill(m + 1, whi, m + 1 < m1);
+        __syncthreads();
+        if (own) {
+            const float* sbuf = stash + (m & 1) * Q * NT + tid;
+            const int64_t node = (L::D == 3) ? (int64_t(m) * P.ny + y) * P.nx + x : int64_t(m) * P.nx + x;
+            const int z = (L::D == 3) ? m : 0;
+            const int yc = (L::D == 3) ? y : m;
+            const bool inlet_node = m == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
+            const typename S::T* fnode = fA + node;
+            auto fa = [&](int a) { return S::f(__ldg(fnode + a * N), L::w(a), P); };
+            auto ga = [&](int a) { return sbuf[a * NT]; };
+            const int ctr = (ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 1;
+            auto pa = [&](int a) {
+                const int dm = (L::D == 3) ? L::ez(a) : L::ey(a);
+                const int dy = (L::D == 3) ? L::ey(a) : 0;
+                const float* wslot = dm < 0 ? wlo : (dm > 0 ? whi : wmid);
+                return wslot[ctr + dy * EX + L::ex(a)];
+            };
+            // push streaming (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g):
+            // per axis the node offsets of the steps -1 and +1 (wrapped on
+            // periodic faces), and the directions whose target lies behind a
+            // wall (bounced back into the opposite slot of this node) or
+            // beyond an open face (they leave the domain)
+            uint32_t wallm = 0, openm = 0;
+            int o[3][2];
+            {
+                const int pos[3] = {x, yc, z};
+                const int len[3] = {P.nx, (L::D == 3) ? P.ny : nm, (L::D == 3) ? P.nz : 1};
+                int stride = 1;
+#pragma unroll
+                for (int d = 0; d < L::D; ++d) {
+                    o[d][0] = -stride;
+                    o[d][1] = stride;
+                    const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
+                    if (pos[d] == 0) {
+                        if (lo == BC_PERIODIC) o[d][0] = (len[d] - 1) * stride;
+                        else if (lo == BC_WALL) wallm |= dirmask<L>(d, -1);
+                        else openm |= dirmask<L>(d, -1);
+                    }
+                    if (pos[d] == len[d] - 1) {
+                        if (hi == BC_PERIODIC) o[d][1] = -(len[d] - 1) * stride;
+                        else if (hi == BC_WALL) wallm |= dirmask<L>(d, 1);
+                        else openm |= dirmask<L>(d, 1);
+                    }
+                    stride *= len[d];
+                }
+            }
+            const uint32_t offm = wallm | openm;
+            const int inode = int(node);
+            auto emit = [&](int a, float fs, float gs) {
+                const float wa = L::w(a);           // w of a and of its opposite
+                const uint32_t bit = 1u << a;
+                if (!(offm & bit)) {
+                    int t = inode;
+                    if (L::ex(a)) t += o[0][L::ex(a) > 0];
+                    if (L::D == 3) {
+                        if (L::ey(a)) t += o[1][L::ey(a) > 0];
+                        if (L::ez(a)) t += o[2][L::ez(a) > 0];
+                    } else {
+                        if (L::ey(a)) t += o[1][L::ey(a) > 0];
+                    }
+                    fB[a * N + t] = S::ef(fs, wa, P);
+                    gB[a * N + t] = S::eg(gs, wa);
+                } else if (wallm & bit) {           // wall: back to this node, opposite slot
+                    fB[L::opp(a) * N + inode] = S::ef(fs, wa, P);
+                    gB[L::opp(a) * N + inode] = S::eg(gs, wa);
+                }                                   // open face: leaves the domain
+            };
+            node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, emit);
+        }
+        __syncthreads();
+        float* t = wlo;
+        wlo = wmid;
+        wmid = whi;
+        whi = t;
+    }
+}
+
+// Three resident blocks per SM for D3Q19 (24 warps; the pair-form node update
+// keeps the register count within 85), four for D2Q9.
+template <class L, class S, int TX, int TY>
+__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (L::D == 3) ? 3 : 4)
+k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typename S::T* __restrict__ fA,
+             const typename S::T* __restrict__ gA, typename S::T* __restrict__ fB, typename S::T* __restrict__ gB)
+{
+    extern __shared__ float smem[];
+    const int nm = (L::D == 3) ? P.nz : P.ny;
     for (int item = blockIdx.x; item < G.items; item += gridDim.x) {
         const int tile = item % G.ntiles, seg = item / G.ntiles;
         const int x0 = (tile % G.tiles_x) * TX;
         const int y0 = (L::D == 3) ? (tile / G.tiles_x) * TY : 0;
         const int m0 = seg * G.seglen;
-        const int m1 = min(m0 + G.seglen, nm);
-        const int x = x0 + tx, y = y0 + ty;
-        const bool own = x < P.nx && ((L::D == 2) || y < P.ny);
+        fused_item<L, S, TX, TY>(P, fA, gA, fB, gB, x0, y0, m0, min(m0 + G.seglen, nm), smem);
+    }
+}
 
-        // phi of plane mm over the extended tile into window slot wslot; the
-        // interior g of that plane goes to stash buffer (mm mod 2).  The
-        // one-node ring around the tile's nodes inside the grid (wx x wy of
-        // them) is enumerated on its own, on the first threads, so that only
-        // a few warps take the halo path.
-        const int wx = min(TX, P.nx - x0), wy = (L::D == 3) ? min(TY, P.ny - y0) : 1;
-        const int nh = (L::D == 3) ? 2 * (wx + 2) + 2 * wy : 2;
-        auto fill = [&](int mm, float* wslot, bool keep) {
-            float* sbuf = stash + (mm & 1) * Q * NT;
-            if (own) wslot[(ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 1] =
-                phi_at<L, S>(P, gA, x, y, mm, keep ? sbuf + tid : nullptr, NT);
-            for (int h = tid; h < nh; h += NT) {
-                int px, py;
-                if (L::D == 2) {
-                    px = h ? wx + 1 : 0;
-                    py = 0;
-                } else if (h < wx + 2) {
-                    px = h;
-                    py = 0;
-                } else if (h < 2 * (wx + 2)) {
-                    px = h - (wx + 2);
-                    py = wy + 1;
-                } else {
-                    px = ((h - 2 * (wx + 2)) & 1) ? wx + 1 : 0;
-                    py = 1 + ((h - 2 * (wx + 2)) >> 1);
-                }
-                wslot[py * EX + px] = phi_at<L, S>(P, gA, x0 - 1 + px, (L::D == 3) ? y0 - 1 + py : 0, mm, nullptr, 0);
-            }
-        };
+// ---------------------------------------------------------- batched sweeps
+//
+// Many independent cases of one lattice and storage format advance together:
+// one launch per size class and step, over the class's work list of items
+// (case, tile segment).  Blocks are persistent and take items from a counter
+// (zeroed before each launch), so that items of unequal size balance
+// themselves.  Each case keeps its own population planes, pop[a * N_c + node]
+// from element offset off of the batch arrays, and its own parameters, which
+// the block copies into shared memory per item.  Per node the arithmetic is
+// that of k_step_fused, so each case evolves exactly as it would alone.
+struct BatchCase {
+    DevParams P;       // parameters of the case (P.N = its nodes)
+    int64_t off;       // first element of the case's planes in the batch arrays
+    FusedGeom G;       // its tiles and segments for the class's tile shape
+    int pad;
+};
 
-        // window slots of planes m - 1, m, m + 1, rotated after each plane
-        float* wlo = win;
-        float* wmid = win + EXT;
-        float* whi = win + 2 * EXT;
+template <class L, class S, int TX, int TY>
+__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (L::D == 3) ? 3 : 4)
+k_step_batch(const BatchCase* __restrict__ cases, const int2* __restrict__ items, int nitems,
+             int* __restrict__ counter, const typename S::T* __restrict__ fA, const typename S::T* __restrict__ gA,
+             typename S::T* __restrict__ fB, typename S::T* __restrict__ gB)
+{
+    constexpr int NT = TX * ((L::D == 3) ? TY : 1);
+    static_assert(sizeof(BatchCase) % sizeof(int) == 0, "case descriptors are copied as words");
+    extern __shared__ float smem[];
+    __shared__ BatchCase sc;
+    __shared__ int s_item;
+    const int tid = threadIdx.x + ((L::D == 3) ? threadIdx.y * TX : 0);
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
-        fill(m0 - 1, wlo, false);
-        fill(m0, wmid, true);
-        for (int m = m0; m < m1; ++m) {
-            fill(m + 1, whi, m + 1 < m1);
-            __syncthreads();
-            if (own) {
-                const float* sbuf = stash + (m & 1) * Q * NT + tid;
-                const int64_t node = (L::D == 3) ? (int64_t(m) * P.ny + y) * P.nx + x : int64_t(m) * P.nx + x;
-                const int z = (L::D == 3) ? m : 0;
-                const int yc = (L::D == 3) ? y : m;
-                const bool inlet_node = m == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
-                const typename S::T* fnode = fA + node;
-                auto fa = [&](int a) { return S::f(__ldg(fnode + a * N), L::w(a), P); };
-                auto ga = [&](int a) { return sbuf[a * NT]; };
-                const int ctr = (ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 1;
-                auto pa = [&](int a) {
-                    const int dm = (L::D == 3) ? L::ez(a) : L::ey(a);
-                    const int dy = (L::D == 3) ? L::ey(a) : 0;
-                    const float* wslot = dm < 0 ? wlo : (dm > 0 ? whi : wmid);
-                    return wslot[ctr + dy * EX + L::ex(a)];
-                };
-                // push streaming (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g):
-                // per axis the node offsets of the steps -1 and +1 (wrapped on
-                // periodic faces), and the directions whose target lies behind a
-                // wall (bounced back into the opposite slot of this node) or
-                // beyond an open face (they leave the domain)
-                uint32_t wallm = 0, openm = 0;
-                int o[3][2];
-                {
-                    const int pos[3] = {x, yc, z};
-                    const int len[3] = {P.nx, (L::D == 3) ? P.ny : nm, (L::D == 3) ? P.nz : 1};
-                    int stride = 1;
-#pragma unroll
-                    for (int d = 0; d < L::D; ++d) {
-                        o[d][0] = -stride;
-                        o[d][1] = stride;
-                        const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
-                        if (pos[d] == 0) {
-                            if (lo == BC_PERIODIC) o[d][0] = (len[d] - 1) * stride;
-                            else if (lo == BC_WALL) wallm |= dirmask<L>(d, -1);
-                            else openm |= dirmask<L>(d, -1);
-                        }
-                        if (pos[d] == len[d] - 1) {
-                            if (hi == BC_PERIODIC) o[d][1] = -(len[d] - 1) * stride;
-                            else if (hi == BC_WALL) wallm |= dirmask<L>(d, 1);
-                            else openm |= dirmask<L>(d, 1);
-                        }
-                        stride *= len[d];
-                    }
-                }
-                const uint32_t offm = wallm | openm;
-                const int inode = int(node);
-                auto emit = [&](int a, float fs, float gs) {
-                    const float wa = L::w(a);           // w of a and of its opposite
-                    const uint32_t bit = 1u << a;
-                    if (!(offm & bit)) {
-                        int t = inode;
-                        if (L::ex(a)) t += o[0][L::ex(a) > 0];
-                        if (L::D == 3) {
-                            if (L::ey(a)) t += o[1][L::ey(a) > 0];
-                            if (L::ez(a)) t += o[2][L::ez(a) > 0];
-                        } else {
-                            if (L::ey(a)) t += o[1][L::ey(a) > 0];
-                        }
-                        fB[a * N + t] = S::ef(fs, wa, P);
-                        gB[a * N + t] = S::eg(gs, wa);
-                    } else if (wallm & bit) {           // wall: back to this node, opposite slot
-                        fB[L::opp(a) * N + inode] = S::ef(fs, wa, P);
-                        gB[L::opp(a) * N + inode] = S::eg(gs, wa);
-                    }                                   // open face: leaves the domain
-                };
-                node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, emit);
-            }
-            __syncthreads();
-            float* t = wlo;
-            wlo = wmid;
-            wmid = whi;
-            whi = t;
-        }
+        const int item = s_item;
+        if (item >= nitems) break;                  // the same for every thread
+        const int2 it = items[item];
+        const int* src = reinterpret_cast<const int*>(cases + it.x);
+        int* dst = reinterpret_cast<int*>(&sc);
+        for (int k = tid; k < int(sizeof(BatchCase) / sizeof(int)); k += NT) dst[k] = src[k];
+        __syncthreads();
+        const int nm = (L::D == 3) ? sc.P.nz : sc.P.ny;
+        const int tile = it.y % sc.G.ntiles, seg = it.y / sc.G.ntiles;
+        const int x0 = (tile % sc.G.tiles_x) * TX;
+        const int y0 = (L::D == 3) ? (tile / sc.G.tiles_x) * TY : 0;
+        const int m0 = seg * sc.G.seglen;
+        const int64_t off = sc.off;
+        fused_item<L, S, TX, TY>(sc.P, fA + off, gA + off, fB + off, gB + off, x0, y0, m0,
+                                 min(m0 + sc.G.seglen, nm), smem);
+        __syncthreads();                            // sc and s_item are rewritten next
     }
 }
 
@@ -1126,6 +1191,41 @@ cudaError_t Launch<L, S>::collide_cells(const DevParams& P, int64_t n, const flo
 {
     if (n <= 0) return cudaSuccess;
     k_collide_cells<L><<<unsigned((n + 127) / 128), 128, 0, s>>>(P, n, f, g, phin, fs, gs, out);
+    return cudaGetLastError();
+}
+
+// Launcher of the batched step for one tile shape.
+template <class L, class S, int TX, int TY>
+struct BatchLaunch {
+    using T = typename S::T;
+    static constexpr int NT = TX * ((L::D == 3) ? TY : 1);
+    // sets the kernel's shared-memory limit; *per_sm = resident blocks per SM
+    static cudaError_t setup(int* per_sm);
+    static cudaError_t step(const BatchCase* cases, const int2* items, int nitems, int* counter, int nblocks,
+                            const void* fA, const void* gA, void* fB, void* gB, cudaStream_t s);
+};
+
+template <class L, class S, int TX, int TY>
+cudaError_t BatchLaunch<L, S, TX, TY>::setup(int* per_sm)
+{
+    using Cfg = FusedCfg<L, TX, TY>;
+    auto kern = k_step_batch<L, S, TX, TY>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, NT, Cfg::smem);
+}
+
+template <class L, class S, int TX, int TY>
+cudaError_t BatchLaunch<L, S, TX, TY>::step(const BatchCase* cases, const int2* items, int nitems, int* counter,
+                                            int nblocks, const void* fA, const void* gA, void* fB, void* gB,
+                                            cudaStream_t s)
+{
+    using Cfg = FusedCfg<L, TX, TY>;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_step_batch<L, S, TX, TY><<<nblocks, dim3(TX, (L::D == 3) ? TY : 1), Cfg::smem, s>>>(
+        cases, items, nitems, counter, static_cast<const T*>(fA), static_cast<const T*>(gA), static_cast<T*>(fB),
+        static_cast<T*>(gB));
     return cudaGetLastError();
 }
 

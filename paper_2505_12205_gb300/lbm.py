@@ -27,7 +27,11 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOU
 EXPORTS = ["lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_fields", "lbm_get_populations",
            "lbm_set_populations", "lbm_diag", "lbm_sync", "lbm_shape", "lbm_last_error",
            "lbm_destroy", "lbm_collide_cells", "lbm_set_timing", "lbm_get_timing",
-           "lbm_diag_noalloc"]
+           "lbm_diag_noalloc", "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step",
+           "lbm_batch_get_fields", "lbm_batch_diag", "lbm_batch_get_plan", "lbm_batch_set_plan",
+           "lbm_batch_tune", "lbm_batch_sync", "lbm_batch_last_error", "lbm_batch_destroy"]
+
+LBM_BATCH_MAX_CLASSES = 8
 
 
 class LbmParams(ctypes.Structure):
@@ -54,6 +58,18 @@ class LbmDiagOut(ctypes.Structure):
         ("sum_p_out", ctypes.c_double), ("max_speed", ctypes.c_double),
         ("n_in", ctypes.c_int64), ("n_out", ctypes.c_int64),
         ("finite", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class LbmBatchPlan(ctypes.Structure):
+    _fields_ = [
+        ("nclasses", ctypes.c_int32),
+        ("nx_max", ctypes.c_int32 * LBM_BATCH_MAX_CLASSES),
+        ("ncases", ctypes.c_int32 * LBM_BATCH_MAX_CLASSES),
+        ("tile_x", ctypes.c_int32 * LBM_BATCH_MAX_CLASSES),
+        ("seglen", ctypes.c_int32 * LBM_BATCH_MAX_CLASSES),
+        ("blocks_per_sm", ctypes.c_int32 * LBM_BATCH_MAX_CLASSES),
+        ("ms_per_step", ctypes.c_double * LBM_BATCH_MAX_CLASSES),
     ]
 
 
@@ -92,8 +108,21 @@ def load(path: str = LIB_PATH):
     lib.lbm_diag_noalloc.argtypes = [P, f32p, f32p, ctypes.c_double, ctypes.POINTER(LbmDiagOut), vp]
     lib.lbm_set_timing.argtypes = [vp, ctypes.c_int]
     lib.lbm_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    BP = ctypes.POINTER(LbmBatchPlan)
+    lib.lbm_batch_create.argtypes = [P, ctypes.c_int32, vp, ctypes.POINTER(vp)]
+    lib.lbm_batch_init_fields.argtypes = [vp, ctypes.c_int32, f32p, f32p, f32p, ctypes.c_int32]
+    lib.lbm_batch_step.argtypes = [vp, i64]
+    lib.lbm_batch_get_fields.argtypes = [vp, ctypes.c_int32, f32p, f32p, f32p, ctypes.c_int32]
+    lib.lbm_batch_diag.argtypes = [vp, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(LbmDiagOut)]
+    lib.lbm_batch_get_plan.argtypes = [vp, BP]
+    lib.lbm_batch_set_plan.argtypes = [vp, BP]
+    lib.lbm_batch_tune.argtypes = [vp, ctypes.c_int32, BP]
+    lib.lbm_batch_sync.argtypes = [vp]
+    lib.lbm_batch_last_error.argtypes = [vp]
+    lib.lbm_batch_destroy.argtypes = [vp]
     for name in EXPORTS:
-        getattr(lib, name).restype = ctypes.c_int if name != "lbm_last_error" else ctypes.c_char_p
+        text = name in ("lbm_last_error", "lbm_batch_last_error")
+        getattr(lib, name).restype = ctypes.c_char_p if text else ctypes.c_int
     _lib = lib
     return lib
 
@@ -343,3 +372,154 @@ class LBM:
 
     def timing(self):
         return lbm_get_timing(self._h)
+
+
+# ------------------------------------------------------------ batched sweeps
+
+def _bcheck(lib, code, b=None):
+    if code != LBM_OK:
+        msg = lib.lbm_batch_last_error(b)
+        raise LbmError(code, msg.decode() if msg else "")
+
+
+def lbm_batch_create(params_list, stream=None):
+    lib = load()
+    arr = (LbmParams * len(params_list))(*[make_params(p) for p in params_list])
+    h = ctypes.c_void_p()
+    _bcheck(lib, lib.lbm_batch_create(arr, len(params_list), ctypes.c_void_p(_stream_handle(stream)),
+                                      ctypes.byref(h)))
+    return h
+
+
+def lbm_batch_init_fields(b, c: int, phi, u=None, pstar=None):
+    lib = load()
+    a, k1 = _ptr(phi)
+    v, k2 = _ptr(u)
+    w, k3 = _ptr(pstar)
+    _bcheck(lib, lib.lbm_batch_init_fields(b, int(c), a, v, w, _one_kind(k1, k2, k3)), b)
+
+
+def lbm_batch_step(b, nsteps: int):
+    lib = load()
+    _bcheck(lib, lib.lbm_batch_step(b, int(nsteps)), b)
+
+
+def lbm_batch_get_fields(b, c: int, phi=None, u=None, p=None):
+    lib = load()
+    a, k1 = _ptr(phi)
+    v, k2 = _ptr(u)
+    w, k3 = _ptr(p)
+    _bcheck(lib, lib.lbm_batch_get_fields(b, int(c), a, v, w, _one_kind(k1, k2, k3)), b)
+
+
+def lbm_batch_diag(b, c: int, phase_eps: float = 1e-3) -> dict:
+    lib = load()
+    out = LbmDiagOut()
+    code = lib.lbm_batch_diag(b, int(c), float(phase_eps), ctypes.byref(out))
+    if code not in (LBM_OK, LBM_ERR_DIVERGED):
+        _bcheck(lib, code, b)
+    return {k: getattr(out, k) for k, _ in LbmDiagOut._fields_ if k != "reserved"}
+
+
+def _plan_dict(pl: LbmBatchPlan) -> dict:
+    n = pl.nclasses
+    d = {"nclasses": n}
+    for k in ("nx_max", "ncases", "tile_x", "seglen", "blocks_per_sm", "ms_per_step"):
+        d[k] = list(getattr(pl, k))[:n]
+    return d
+
+
+def lbm_batch_get_plan(b) -> dict:
+    lib = load()
+    pl = LbmBatchPlan()
+    _bcheck(lib, lib.lbm_batch_get_plan(b, ctypes.byref(pl)), b)
+    return _plan_dict(pl)
+
+
+def lbm_batch_set_plan(b, plan: dict):
+    lib = load()
+    pl = LbmBatchPlan()
+    pl.nclasses = int(plan["nclasses"])
+    for k in ("nx_max", "ncases", "tile_x", "seglen", "blocks_per_sm"):
+        for i, v in enumerate(plan[k]):
+            getattr(pl, k)[i] = int(v)
+    _bcheck(lib, lib.lbm_batch_set_plan(b, ctypes.byref(pl)), b)
+
+
+def lbm_batch_tune(b, trial_steps: int = 5) -> dict:
+    lib = load()
+    pl = LbmBatchPlan()
+    _bcheck(lib, lib.lbm_batch_tune(b, int(trial_steps), ctypes.byref(pl)), b)
+    return _plan_dict(pl)
+
+
+def lbm_batch_sync(b):
+    lib = load()
+    _bcheck(lib, lib.lbm_batch_sync(b), b)
+
+
+def lbm_batch_last_error(b=None) -> str:
+    msg = load().lbm_batch_last_error(b)
+    return msg.decode() if msg else ""
+
+
+def lbm_batch_destroy(b):
+    lib = load()
+    _bcheck(lib, lib.lbm_batch_destroy(b))
+
+
+class Batch:
+    """Many independent cases advanced together (see include/lbm.h)."""
+
+    def __init__(self, params_list, stream=None):
+        self.params = [dict(p) for p in params_list]
+        self.D = 2 if not self.params or int(self.params[0]["lattice"]) == LBM_D2Q9 else 3
+        self.shapes = [(int(p.get("nz", 1)), int(p["ny"]), int(p["nx"])) for p in self.params]
+        self._h = lbm_batch_create(self.params, stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.params)
+
+    def init_fields(self, c, phi, u=None, pstar=None):
+        if not _is_torch(phi):
+            phi = np.ascontiguousarray(phi, np.float32)
+            u = None if u is None else np.ascontiguousarray(u, np.float32)
+            pstar = None if pstar is None else np.ascontiguousarray(pstar, np.float32)
+        lbm_batch_init_fields(self._h, c, phi, u, pstar)
+
+    def step(self, n: int = 1):
+        lbm_batch_step(self._h, n)
+
+    def sync(self):
+        lbm_batch_sync(self._h)
+
+    def fields(self, c):
+        sh = self.shapes[c]
+        phi = np.empty(sh, np.float32)
+        u = np.empty((self.D,) + sh, np.float32)
+        p = np.empty(sh, np.float32)
+        lbm_batch_get_fields(self._h, c, phi, u, p)
+        return phi, u, p
+
+    def diag(self, c, phase_eps: float = 1e-3) -> dict:
+        return lbm_batch_diag(self._h, c, phase_eps)
+
+    def plan(self) -> dict:
+        return lbm_batch_get_plan(self._h)
+
+    def set_plan(self, plan: dict):
+        lbm_batch_set_plan(self._h, plan)
+
+    def tune(self, trial_steps: int = 5) -> dict:
+        return lbm_batch_tune(self._h, trial_steps)

@@ -53,11 +53,36 @@ def test_ptxas_reports_at_most_token_spills(lib):
     registers); ptxas may spill a little for that (most with the 16-bit
     conversions), never more than 128 bytes a thread."""
     build_dir = os.path.join(ROOT, "paper_2505_12205_gb300", "_build")
-    logs = [os.path.join(build_dir, n) for n in os.listdir(build_dir) if n.endswith(".ptxas.log")
-            and "api" not in n and "noalloc" not in n]
-    assert len(logs) == 4
+    kernel_units = ["lbm_d3q19", "lbm_d3q19_f16", "lbm_d3q19_bf16", "lbm_d2q9", "lbm_batch_d2q9", "lbm_batch_d3q19"]
+    logs = [os.path.join(build_dir, n + ".ptxas.log") for n in kernel_units]
     for log in logs:
         txt = open(log).read()
         assert "sm_103a" in txt
         spills = re.findall(r"(\d+) bytes spill stores", txt)
         assert spills and all(int(s) <= 128 for s in spills)
+
+
+def test_batch_plan_struct_layout(lib):
+    import ctypes
+    # int32 nclasses, five int32[8] arrays, padding to 8, double[8]
+    assert ctypes.sizeof(lib.LbmBatchPlan) == 4 + 5 * 8 * 4 + 4 + 8 * 8
+    assert lib.LbmBatchPlan.ms_per_step.offset == 168
+
+
+def test_batch_rejects_invalid_cases_before_touching_a_device(lib):
+    import lbm_cases as C
+    good = C.base_params(0, 16, 16, 1)
+    cases = []
+    p = dict(good); p["bc"] = [0, 0, 2, 3, 0, 0]; cases.append(p)           # inlet/outlet
+    p = dict(good); p["lattice"] = 1; p["nz"] = 4; cases.append(p)          # lattice differs from case 0
+    p = dict(good); p["storage"] = 2; cases.append(p)                       # bfloat16
+    p = dict(good); p["tau_H"] = -1.0; cases.append(p)                      # invalid physics
+    for bad in cases:
+        lst = [good, bad] if bad.get("lattice") == 1 else [bad]
+        with pytest.raises(lib.LbmError) as e:
+            lib.Batch(lst)
+        assert e.value.code == lib.LBM_ERR_ARG, bad
+        assert lib.lbm_batch_last_error() != ""
+    with pytest.raises(lib.LbmError) as e:
+        lib.Batch([])
+    assert e.value.code == lib.LBM_ERR_ARG
