@@ -56,7 +56,7 @@ struct lbm_ctx {
     DiagPartial* diag_part = nullptr;
     DiagPartial* diag_res = nullptr;
     int diag_nparts = 0;
-    float* staging = nullptr;       // float32 planes for checkpoints of 16-bit states
+    float* staging = nullptr;       // float32 population-major planes for checkpoints
     size_t elem = 4;                // bytes per stored population value
     bool initialised = false;
     // kernel timing: 4 events per recorded step (before phi, after phi,
@@ -94,7 +94,13 @@ static int validate(const lbm_params* p, std::string& why)
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) { why = "grid sizes must be >= 1"; return -1; }
     if (p->lattice == LBM_D2Q9 && p->nz != 1) { why = "D2Q9 needs nz == 1"; return -1; }
     if (p->nx > 65535 * 128 || p->ny > 65535 || p->nz > 65535) { why = "grid too large for the launch shape"; return -1; }
-    if (int64_t(p->nx) * p->ny * p->nz > int64_t(INT32_MAX)) { why = "grid too large: node indices are 32-bit"; return -1; }
+    {
+        const int64_t nxp = (int64_t(p->nx) + 31) / 32 * 32, Q = p->lattice == LBM_D2Q9 ? 9 : 19;
+        if (Q * nxp * p->ny * p->nz > int64_t(UINT32_MAX)) {
+            why = "grid too large: population element indices are 32-bit (Q * nodes with rows padded to 32 < 2^32)";
+            return -1;
+        }
+    }
     if (!(p->rho_L > 0 && p->rho_H > 0 && p->tau_L > 0 && p->tau_H > 0)) { why = "rho_L, rho_H, tau_L, tau_H must be > 0"; return -1; }
     if (!(p->W > 0 && p->mobility > 0 && p->sigma >= 0)) { why = "W, mobility must be > 0 and sigma >= 0"; return -1; }
     if (p->visc_model != 0 && p->visc_model != 1) { why = "visc_model must be 0 or 1"; return -1; }
@@ -122,6 +128,8 @@ static DevParams make_dev(const lbm_params* p, int64_t N)
     DevParams d;
     std::memset(&d, 0, sizeof d);
     d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
+    d.nxp = (p->nx + 31) / 32 * 32;
+    d.Np = int64_t(d.nxp) * p->ny * p->nz;
     for (int i = 0; i < 6; ++i) d.bc[i] = p->bc[i];
     if (p->lattice == LBM_D2Q9) d.bc[4] = d.bc[5] = LBM_BC_PERIODIC;
     d.visc_model = p->visc_model;
@@ -210,7 +218,7 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
     c->dp = make_dev(p, c->N);
 
     c->elem = p->storage == 0 ? 4 : 2;
-    const size_t plane = size_t(c->N) * c->Q * c->elem;
+    const size_t plane = size_t(c->dp.Np) * c->Q * c->elem;
     void** bufs[4] = {&c->b.fA, &c->b.gA, &c->b.fB, &c->b.gB};
     for (void** b : bufs) {
         e = cudaMalloc(b, plane);
@@ -368,7 +376,8 @@ int lbm_get_fields(lbm_ctx* c, float* phi, float* u, float* p, int on_device)
     return LBM_OK;
 }
 
-// float32 staging planes (2 Q N) for checkpoints of a 16-bit state
+// float32 staging planes (2 Q N) for checkpoints: the external layout is
+// population-major planes, the state is blocked
 static int ensure_staging(lbm_ctx* c)
 {
     if (c->staging) return LBM_OK;
@@ -382,23 +391,18 @@ int lbm_get_populations(lbm_ctx* c, float* f, float* g, int on_device)
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const size_t nb = size_t(c->N) * c->Q * sizeof(float);
-    const void* sf = c->b.fA;
-    const void* sg = c->b.gA;
-    if (c->p.storage != 0) {
-        int r = ensure_staging(c);
-        if (r != LBM_OK) return r;
-        float* fo = c->staging;
-        float* go = c->staging + size_t(c->N) * c->Q;
-        cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
-            return decltype(l)::unpack(c->dp, c->b.fA, c->b.gA, fo, go, c->stream);
-        });
-        if (e != cudaSuccess) return cuda_fail(c, e, "unpack kernel");
-        sf = fo;
-        sg = go;
-    }
-    if (f) LBM_CUDA(c, cudaMemcpyAsync(f, sf, nb, kind, c->stream));
-    if (g) LBM_CUDA(c, cudaMemcpyAsync(g, sg, nb, kind, c->stream));
-    if (!on_device || c->p.storage != 0) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    // the state is blocked (and maybe 16-bit): unpack into float32 planes first
+    int r = ensure_staging(c);
+    if (r != LBM_OK) return r;
+    float* fo = c->staging;
+    float* go = c->staging + size_t(c->N) * c->Q;
+    cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+        return decltype(l)::unpack(c->dp, c->b.fA, c->b.gA, fo, go, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "unpack kernel");
+    if (f) LBM_CUDA(c, cudaMemcpyAsync(f, fo, nb, kind, c->stream));
+    if (g) LBM_CUDA(c, cudaMemcpyAsync(g, go, nb, kind, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
 
@@ -408,22 +412,17 @@ int lbm_set_populations(lbm_ctx* c, const float* f, const float* g, int on_devic
     if (!f || !g) return fail(c, LBM_ERR_ARG, "f and g are required");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t nb = size_t(c->N) * c->Q * sizeof(float);
-    if (c->p.storage == 0) {
-        LBM_CUDA(c, cudaMemcpyAsync(c->b.fA, f, nb, kind, c->stream));
-        LBM_CUDA(c, cudaMemcpyAsync(c->b.gA, g, nb, kind, c->stream));
-    } else {
-        int r = ensure_staging(c);
-        if (r != LBM_OK) return r;
-        float* fi = c->staging;
-        float* gi = c->staging + size_t(c->N) * c->Q;
-        LBM_CUDA(c, cudaMemcpyAsync(fi, f, nb, kind, c->stream));
-        LBM_CUDA(c, cudaMemcpyAsync(gi, g, nb, kind, c->stream));
-        cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
-            return decltype(l)::pack(c->dp, fi, gi, c->b.fA, c->b.gA, c->stream);
-        });
-        if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
-    }
-    if (!on_device || c->p.storage != 0) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    int r = ensure_staging(c);
+    if (r != LBM_OK) return r;
+    float* fi = c->staging;
+    float* gi = c->staging + size_t(c->N) * c->Q;
+    LBM_CUDA(c, cudaMemcpyAsync(fi, f, nb, kind, c->stream));
+    LBM_CUDA(c, cudaMemcpyAsync(gi, g, nb, kind, c->stream));
+    cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+        return decltype(l)::pack(c->dp, fi, gi, c->b.fA, c->b.gA, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = true;
     return LBM_OK;
 }

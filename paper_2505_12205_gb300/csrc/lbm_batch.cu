@@ -82,7 +82,7 @@ struct lbm_batch {
     int ncases = 0;
     std::vector<lbm_params> params;
     std::vector<DevParams> dp;
-    std::vector<int64_t> node_off;         // first node of each case in the batch
+    std::vector<int64_t> node_off;         // first (padded) node of each case in the batch
     std::vector<char> initialised;
     int64_t total_nodes = 0, max_nodes = 0;
     void *fA = nullptr, *gA = nullptr, *fB = nullptr, *gB = nullptr;   // A = current state
@@ -307,7 +307,7 @@ int lbm_batch_create(const lbm_params* params, int32_t ncases, void* stream, lbm
         if ((b->total_nodes * b->Q * int64_t(b->elem)) % 256 != 0)
             return give_up(bfail(b, LBM_ERR_ARG, "internal: case offset not 256-byte aligned"));
         b->dp.push_back(lbm::api_make_dev(params + c, n));
-        b->total_nodes += n;
+        b->total_nodes += b->dp.back().Np;        // blocked layout: rows padded to 32 nodes
         b->max_nodes = std::max(b->max_nodes, n);
     }
     cudaGetDevice(&b->device);

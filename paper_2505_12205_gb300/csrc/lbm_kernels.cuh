@@ -1,8 +1,7 @@
 // sm_103a kernels of the phase-field WMRT lattice Boltzmann step.
 //
-// State: post-streaming populations f, g in population-major planes
-// pop[a * N + node], node = (z * ny + y) * nx + x, double-buffered (A = current
-// state, B = next state).  One time step (Algorithms 1-3 of the paper, fused):
+// State: post-streaming populations f, g in 32-node blocks (see "layout"
+// below), double-buffered (A = current state, B = next state).  One time step (Algorithms 1-3 of the paper, fused):
 //   k_step_fused  per node: phi = sum_a g_a (eq:phase_field_variable) on the
 //                 tile and its halo, isotropic stencils of phi
 //                 (eq:gradient_phi, eq:laplacian_phi), material properties,
@@ -30,9 +29,11 @@ enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTFLOW = 3 };
 // Parameters as the kernels use them (float32 arithmetic), passed by value.
 struct DevParams {
     int nx, ny, nz;
+    int nxp;               // nx rounded up to a multiple of 32 (row pitch of the state)
     int bc[6];
     int visc_model;
     int64_t N;             // nodes
+    int64_t Np;            // nodes with the padded rows, nxp * ny * nz
     float rho_L, rho_H, tau_L, tau_H, mu_L, mu_H;
     float beta, kappa;     // eq:beta_kappa_relation
     float inv_W;           // 1 / xi
@@ -43,6 +44,46 @@ struct DevParams {
     const float* phi_in;
     const float* u_in;
 };
+
+// ------------------------------------------------------------------ layout
+//
+// The populations of a set are stored in blocks of 32 nodes along x.  Node
+// (x, y, z) has the padded index n = (z ny + y) nxp + x (z = 0 and y the row
+// in 2D), and population a of node n is element
+//     (n / 32) 32 Q + 32 a + n mod 32
+// of the set's array.  A warp of 32 consecutive x reads or writes one
+// population of a block as one contiguous row (128 B at float32), the Q rows
+// of a block are contiguous (2.4 KB for D3Q19 at float32), so that a tile's
+// accesses stay within few DRAM pages, and population a of a node is an
+// immediate offset 32 a from population 0.  Element indices are 32-bit
+// (Q Np < 2^32 is checked on the host).
+__device__ __forceinline__ uint32_t pnode(const DevParams& P, int x, int y, int z)
+{
+    return (uint32_t(z) * uint32_t(P.ny) + uint32_t(y)) * uint32_t(P.nxp) + uint32_t(x);
+}
+
+// element of population 0 of padded node n (population a: + 32 a)
+template <class L>
+__device__ __forceinline__ uint32_t pel(uint32_t n)
+{
+    return (n >> 5) * (32u * L::Q) + (n & 31u);
+}
+
+// Element of population 0 of node (x, y, z) and the stride between the
+// populations of a node: the blocked layout of a state, or (PLANAR) the
+// population-major planes pop[a N + node] of the external interface.
+template <class L, bool PLANAR>
+__device__ __forceinline__ int64_t pop_base(const DevParams& P, int64_t node, int x, int y, int z)
+{
+    if constexpr (PLANAR) return node;
+    else return int64_t(pel<L>(pnode(P, x, y, z)));
+}
+template <bool PLANAR>
+__device__ __forceinline__ int64_t pop_stride(const DevParams& P)
+{
+    if constexpr (PLANAR) return P.N;
+    else return 32;
+}
 
 // ---------------------------------------------------------- storage formats
 //
@@ -426,15 +467,18 @@ __device__ __forceinline__ int map_push(int v, int n, int bclo, int bchi, int& k
 
 // ---------------------------------------------------------------- kernels
 
-template <class L, class S>
+// phi = sum_a g_a of every node into phi[node] (unpadded node order).
+template <class L, class S, bool PLANAR>
 __global__ void __launch_bounds__(128) k_phi(const __grid_constant__ DevParams P,
                                              const typename S::T* __restrict__ g, float* __restrict__ phi)
 {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
+    const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
+    const int64_t b = pop_base<L, PLANAR>(P, i, x, y, z), st = pop_stride<PLANAR>(P);
     float s = 0.0f;
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) s += S::g(__ldg(g + a * P.N + i), L::w(a));
+    for (int a = 0; a < L::Q; ++a) s += S::g(__ldg(g + b + a * st), L::w(a));
     phi[i] = s;
 }
 
@@ -496,24 +540,22 @@ __device__ __forceinline__ float phi_at(const DevParams& P, const typename S::T*
 {
     bool inlet = false;
     const int x = map_phi(xx, P.nx, P.bc[0], P.bc[1], inlet);
-    int y, m;
-    int64_t node;
+    uint32_t n;
     if (L::D == 3) {
-        y = map_phi(yy, P.ny, P.bc[2], P.bc[3], inlet);
-        m = map_phi(mm, P.nz, P.bc[4], P.bc[5], inlet);
+        const int y = map_phi(yy, P.ny, P.bc[2], P.bc[3], inlet);
+        const int m = map_phi(mm, P.nz, P.bc[4], P.bc[5], inlet);
         if (inlet) return P.phi_in[y * P.nx + x];
-        node = (int64_t(m) * P.ny + y) * P.nx + x;
+        n = pnode(P, x, y, m);
     } else {
-        m = map_phi(mm, P.ny, P.bc[2], P.bc[3], inlet);
+        const int m = map_phi(mm, P.ny, P.bc[2], P.bc[3], inlet);
         if (inlet) return P.phi_in[x];
-        node = int64_t(m) * P.nx + x;
+        n = pnode(P, x, m, 0);
     }
-    (void)y;
-    const int64_t N = P.N;
+    const typename S::T* gb = gA + pel<L>(n);
     float s = 0.0f;
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-        const float v = S::g(__ldg(gA + a * N + node), L::w(a));
+        const float v = S::g(__ldg(gb + 32 * a), L::w(a));
         if (stash) stash[a * stride] = v;
         s += v;
     }
@@ -536,7 +578,6 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
     const int tid = threadIdx.x + ((L::D == 3) ? threadIdx.y * TX : 0);
     const int tx = threadIdx.x, ty = (L::D == 3) ? threadIdx.y : 0;
     const int nm = (L::D == 3) ? P.nz : P.ny;       // length of the march axis
-    const int64_t N = P.N;
     const int x = x0 + tx, y = y0 + ty;
     const bool own = x < P.nx && ((L::D == 2) || y < P.ny);
 
@@ -582,12 +623,13 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
         __syncthreads();
         if (own) {
             const float* sbuf = stash + (m & 1) * Q * NT + tid;
-            const int64_t node = (L::D == 3) ? (int64_t(m) * P.ny + y) * P.nx + x : int64_t(m) * P.nx + x;
             const int z = (L::D == 3) ? m : 0;
             const int yc = (L::D == 3) ? y : m;
             const bool inlet_node = m == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
-            const typename S::T* fnode = fA + node;
-            auto fa = [&](int a) { return S::f(__ldg(fnode + a * N), L::w(a), P); };
+            const uint32_t n0 = pnode(P, x, yc, z);
+            const uint32_t e0 = pel<L>(n0);
+            const typename S::T* fblk = fA + e0;
+            auto fa = [&](int a) { return S::f(__ldg(fblk + 32 * a), L::w(a), P); };
             auto ga = [&](int a) { return sbuf[a * NT]; };
             const int ctr = (ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 1;
             auto pa = [&](int a) {
@@ -597,53 +639,54 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
                 return wslot[ctr + dy * EX + L::ex(a)];
             };
             // push streaming (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g):
-            // per axis the node offsets of the steps -1 and +1 (wrapped on
-            // periodic faces), and the directions whose target lies behind a
-            // wall (bounced back into the opposite slot of this node) or
-            // beyond an open face (they leave the domain)
+            // per axis the element offsets of the steps -1 and +1 (wrapped on
+            // periodic faces; a step along y or z moves whole 32-node blocks,
+            // so its offset is the node step times Q), and the directions
+            // whose target lies behind a wall (bounced back into the opposite
+            // slot of this node) or beyond an open face (they leave the domain)
             uint32_t wallm = 0, openm = 0;
-            int o[3][2];
+            uint32_t o[3][2];
             {
                 const int pos[3] = {x, yc, z};
                 const int len[3] = {P.nx, (L::D == 3) ? P.ny : nm, (L::D == 3) ? P.nz : 1};
-                int stride = 1;
+                const uint32_t nstep[3] = {1u, uint32_t(P.nxp), uint32_t(P.nxp) * uint32_t(P.ny)};
 #pragma unroll
                 for (int d = 0; d < L::D; ++d) {
-                    o[d][0] = -stride;
-                    o[d][1] = stride;
+                    int sm = -1, sp = 1;                // node steps in units of the axis
                     const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
                     if (pos[d] == 0) {
-                        if (lo == BC_PERIODIC) o[d][0] = (len[d] - 1) * stride;
+                        if (lo == BC_PERIODIC) sm = len[d] - 1;
                         else if (lo == BC_WALL) wallm |= dirmask<L>(d, -1);
                         else openm |= dirmask<L>(d, -1);
                     }
                     if (pos[d] == len[d] - 1) {
-                        if (hi == BC_PERIODIC) o[d][1] = -(len[d] - 1) * stride;
+                        if (hi == BC_PERIODIC) sp = -(len[d] - 1);
                         else if (hi == BC_WALL) wallm |= dirmask<L>(d, 1);
                         else openm |= dirmask<L>(d, 1);
                     }
-                    stride *= len[d];
+                    if (d == 0) {       // within a row: the block and lane of the target
+                        o[0][0] = pel<L>(n0 + uint32_t(sm)) - e0;
+                        o[0][1] = pel<L>(n0 + uint32_t(sp)) - e0;
+                    } else {
+                        o[d][0] = uint32_t(sm) * nstep[d] * uint32_t(Q);
+                        o[d][1] = uint32_t(sp) * nstep[d] * uint32_t(Q);
+                    }
                 }
             }
             const uint32_t offm = wallm | openm;
-            const int inode = int(node);
             auto emit = [&](int a, float fs, float gs) {
                 const float wa = L::w(a);           // w of a and of its opposite
                 const uint32_t bit = 1u << a;
                 if (!(offm & bit)) {
-                    int t = inode;
+                    uint32_t t = e0;
                     if (L::ex(a)) t += o[0][L::ex(a) > 0];
-                    if (L::D == 3) {
-                        if (L::ey(a)) t += o[1][L::ey(a) > 0];
-                        if (L::ez(a)) t += o[2][L::ez(a) > 0];
-                    } else {
-                        if (L::ey(a)) t += o[1][L::ey(a) > 0];
-                    }
-                    fB[a * N + t] = S::ef(fs, wa, P);
-                    gB[a * N + t] = S::eg(gs, wa);
+                    if (L::ey(a)) t += o[1][L::ey(a) > 0];
+                    if (L::D == 3 && L::ez(a)) t += o[2][L::ez(a) > 0];
+                    (fB + t)[32 * a] = S::ef(fs, wa, P);
+                    (gB + t)[32 * a] = S::eg(gs, wa);
                 } else if (wallm & bit) {           // wall: back to this node, opposite slot
-                    fB[L::opp(a) * N + inode] = S::ef(fs, wa, P);
-                    gB[L::opp(a) * N + inode] = S::eg(gs, wa);
+                    (fB + e0)[32 * L::opp(a)] = S::ef(fs, wa, P);
+                    (gB + e0)[32 * L::opp(a)] = S::eg(gs, wa);
                 }                                   // open face: leaves the domain
             };
             node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, emit);
@@ -680,13 +723,13 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typen
 // one launch per size class and step, over the class's work list of items
 // (case, tile segment).  Blocks are persistent and take items from a counter
 // (zeroed before each launch), so that items of unequal size balance
-// themselves.  Each case keeps its own population planes, pop[a * N_c + node]
-// from element offset off of the batch arrays, and its own parameters, which
+// themselves.  Each case keeps its own populations (the blocked layout above,
+// from element offset off of the batch arrays) and its own parameters, which
 // the block copies into shared memory per item.  Per node the arithmetic is
 // that of k_step_fused, so each case evolves exactly as it would alone.
 struct BatchCase {
     DevParams P;       // parameters of the case (P.N = its nodes)
-    int64_t off;       // first element of the case's planes in the batch arrays
+    int64_t off;       // first element of the case's populations in the batch arrays
     FusedGeom G;       // its tiles and segments for the class's tile shape
     int pad;
 };
@@ -737,8 +780,10 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __re
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
     if (t >= nface) return;
-    const int64_t N = P.N;
-    const int64_t node = t;                    // last-axis coordinate 0
+    // the node (t mod nx, t / nx) of the last-axis plane 0
+    const uint32_t e = (L::D == 2) ? pel<L>(pnode(P, t, 0, 0)) : pel<L>(pnode(P, t % P.nx, t / P.nx, 0));
+    typename S::T* fn = fB + e;
+    typename S::T* gn = gB + e;
     const float phin = P.phi_in[t], un = P.u_in[t];
     const float ux = 0.0f, uy = (L::D == 2) ? un : 0.0f, uz = (L::D == 3) ? un : 0.0f;
     const float uu = un * un;
@@ -746,8 +791,8 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __re
     float f[Q], g[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        f[a] = S::f(fB[a * N + node], L::w(a), P);
-        g[a] = S::g(gB[a * N + node], L::w(a));
+        f[a] = S::f(fn[32 * a], L::w(a), P);
+        g[a] = S::g(gn[32 * a], L::w(a));
     }
     float Mx = 0.0f, My = 0.0f, theta = 0.0f;
     int ndiag = 0;
@@ -774,10 +819,10 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __re
         const int ab = L::opp(a);
         const float da = gdev<L>(a, ux, uy, uz, uu), db = gdev<L>(ab, ux, uy, uz, uu);
         const float eM = float(t0) * Mx + float(t1) * My;
-        fB[a * N + node] = S::ef(f[ab] + (da - db) - 0.5f * eM, L::w(a), P);   // eq:velocity_boundary_distribution
+        fn[32 * a] = S::ef(f[ab] + (da - db) - 0.5f * eM, L::w(a), P);   // eq:velocity_boundary_distribution
         const float corr = (t0 != 0 || t1 != 0) ? th_n : 0.0f;
         // eq:unknown_distribution_*: g_a = geq_a - (g_abar - geq_abar) - corr, w_a = w_abar
-        gB[a * N + node] = S::eg(phin * (2.0f * L::w(a) + da + db) - g[ab] - corr, L::w(a));
+        gn[32 * a] = S::eg(phin * (2.0f * L::w(a) + da + db) - g[ab] - corr, L::w(a));
     }
 }
 
@@ -793,24 +838,25 @@ __global__ void k_outlet(const __grid_constant__ DevParams P, const typename S::
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
     if (t >= nface) return;
-    const int64_t N = P.N;
     const int nL = (L::D == 2) ? P.ny : P.nz;
-    const int64_t iN = int64_t(nL - 1) * nface + t, iM = int64_t(nL - 2) * nface + t;
+    const int tx = (L::D == 2) ? t : t % P.nx, ty = (L::D == 2) ? 0 : t / P.nx;
+    const uint32_t iN = (L::D == 2) ? pel<L>(pnode(P, tx, nL - 1, 0)) : pel<L>(pnode(P, tx, ty, nL - 1));
+    const uint32_t iM = (L::D == 2) ? pel<L>(pnode(P, tx, nL - 2, 0)) : pel<L>(pnode(P, tx, ty, nL - 2));
     float U = 0.0f;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
-        if (en) U += float(en) * S::f(fB[a * N + iM], L::w(a), P);
+        if (en) U += float(en) * S::f(fB[iM + 32 * a], L::w(a), P);
     }
     const float lam = fminf(fmaxf(U, 0.0f), 1.0f);
     const float inv = 1.0f / (1.0f + lam);
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const float wa = L::w(a);
-        const float fo = S::f(fA[a * N + iN], wa, P), fm = S::f(fB[a * N + iM], wa, P);
-        const float go = S::g(gA[a * N + iN], wa), gm = S::g(gB[a * N + iM], wa);
-        fB[a * N + iN] = S::ef((fo + lam * fm) * inv, wa, P);
-        gB[a * N + iN] = S::eg((go + lam * gm) * inv, wa);
+        const float fo = S::f(fA[iN + 32 * a], wa, P), fm = S::f(fB[iM + 32 * a], wa, P);
+        const float go = S::g(gA[iN + 32 * a], wa), gm = S::g(gB[iM + 32 * a], wa);
+        fB[iN + 32 * a] = S::ef((fo + lam * fm) * inv, wa, P);
+        gB[iN + 32 * a] = S::eg((go + lam * gm) * inv, wa);
     }
 }
 
@@ -847,10 +893,12 @@ __global__ void k_init(const __grid_constant__ DevParams P, const float* __restr
     const float ps = pstar ? pstar[i] : 0.0f, ph = phi[i];
     float geq[L::Q], feq[L::Q];
     equilibria<L>(ph, ps, ux, uy, uz, geq, feq);
+    const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
+    const uint32_t e = pel<L>(pnode(P, x, y, z));
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-        g[a * P.N + i] = S::eg(geq[a], L::w(a));
-        f[a * P.N + i] = S::ef(feq[a], L::w(a), P);
+        g[e + 32 * a] = S::eg(geq[a], L::w(a));
+        f[e + 32 * a] = S::ef(feq[a], L::w(a), P);
     }
 }
 
@@ -868,11 +916,12 @@ __global__ void __launch_bounds__(128) k_fields(const __grid_constant__ DevParam
     if (x >= P.nx) return;
     const int64_t N = P.N;
     const int64_t node = (int64_t(z) * P.ny + y) * P.nx + x;
+    const uint32_t e = pel<L>(pnode(P, x, y, z));
     float f[Q], g[Q], phin[Q], out[5];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        f[a] = S::f(fA[a * N + node], L::w(a), P);
-        g[a] = S::g(gA[a * N + node], L::w(a));
+        f[a] = S::f(fA[e + 32 * a], L::w(a), P);
+        g[a] = S::g(gA[e + 32 * a], L::w(a));
     }
     gather_phi<L>(P, phi, x, y, z, phin);
     const bool inlet_node = ((L::D == 3) ? z : y) == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
@@ -894,7 +943,7 @@ struct DiagPartial {
     int pad;
 };
 
-template <class L, class S>
+template <class L, class S, bool PLANAR>
 __global__ void __launch_bounds__(256) k_diag(const __grid_constant__ DevParams P,
                                               const typename S::T* __restrict__ fA,
                                               const typename S::T* __restrict__ gA,
@@ -915,10 +964,11 @@ __global__ void __launch_bounds__(256) k_diag(const __grid_constant__ DevParams 
         const int y = int((node / P.nx) % P.ny);
         const int z = int(node / (int64_t(P.nx) * P.ny));
         float f[Q], g[Q], phin[Q], out[5];
+        const int64_t b = pop_base<L, PLANAR>(P, node, x, y, z), st = pop_stride<PLANAR>(P);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            f[a] = S::f(fA[a * N + node], L::w(a), P);
-            g[a] = S::g(gA[a * N + node], L::w(a));
+            f[a] = S::f(fA[b + a * st], L::w(a), P);
+            g[a] = S::g(gA[b + a * st], L::w(a));
             if (!isfinite(f[a]) || !isfinite(g[a])) bad = 1;
         }
         gather_phi<L>(P, phi, x, y, z, phin);
@@ -1016,6 +1066,10 @@ struct Launch {
                               cudaStream_t s);
     static cudaError_t diag(const DevParams& P, const Buffers& b, double eps, DiagPartial* part, int nparts,
                             DiagPartial* res, cudaStream_t s);
+    // the same diagnostics of populations in the external population-major
+    // planes [Q][N] (f32 planes of the caller)
+    static cudaError_t diag_planar(const DevParams& P, const Buffers& b, double eps, DiagPartial* part, int nparts,
+                                   DiagPartial* res, cudaStream_t s);
     // populations of the state <-> float32 planes [Q][N] (checkpoints)
     static cudaError_t unpack(const DevParams& P, const void* f, const void* g, float* fo, float* go, cudaStream_t s);
     static cudaError_t pack(const DevParams& P, const float* fi, const float* gi, void* f, void* g, cudaStream_t s);
@@ -1115,7 +1169,7 @@ cudaError_t Launch<L, S>::fields(const DevParams& P, const Buffers& b, float* op
 {
     const T* fA = static_cast<const T*>(b.fA);
     const T* gA = static_cast<const T*>(b.gA);
-    k_phi<L, S><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.phi);
+    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.phi);
     dim3 grid((P.nx + 127) / 128, P.ny, (L::D == 3) ? P.nz : 1);
     k_fields<L, S><<<grid, 128, 0, s>>>(P, fA, gA, b.phi, ophi, ou, op);
     return cudaGetLastError();
@@ -1127,8 +1181,20 @@ cudaError_t Launch<L, S>::diag(const DevParams& P, const Buffers& b, double eps,
 {
     const T* fA = static_cast<const T*>(b.fA);
     const T* gA = static_cast<const T*>(b.gA);
-    k_phi<L, S><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.phi);
-    k_diag<L, S><<<nparts, 256, 0, s>>>(P, fA, gA, b.phi, eps, part);
+    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.phi);
+    k_diag<L, S, false><<<nparts, 256, 0, s>>>(P, fA, gA, b.phi, eps, part);
+    k_diag_final<L><<<1, 32, 0, s>>>(part, nparts, res);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::diag_planar(const DevParams& P, const Buffers& b, double eps, DiagPartial* part,
+                                      int nparts, DiagPartial* res, cudaStream_t s)
+{
+    const T* fA = static_cast<const T*>(b.fA);
+    const T* gA = static_cast<const T*>(b.gA);
+    k_phi<L, S, true><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.phi);
+    k_diag<L, S, true><<<nparts, 256, 0, s>>>(P, fA, gA, b.phi, eps, part);
     k_diag_final<L><<<1, 32, 0, s>>>(part, nparts, res);
     return cudaGetLastError();
 }
@@ -1139,10 +1205,12 @@ __global__ void k_unpack(const __grid_constant__ DevParams P, const typename S::
 {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
+    const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
+    const uint32_t e = pel<L>(pnode(P, x, y, z));
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-        fo[a * P.N + i] = S::f(f[a * P.N + i], L::w(a), P);
-        go[a * P.N + i] = S::g(g[a * P.N + i], L::w(a));
+        fo[a * P.N + i] = S::f(f[e + 32 * a], L::w(a), P);
+        go[a * P.N + i] = S::g(g[e + 32 * a], L::w(a));
     }
 }
 
@@ -1152,10 +1220,12 @@ __global__ void k_pack(const __grid_constant__ DevParams P, const float* __restr
 {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
+    const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
+    const uint32_t e = pel<L>(pnode(P, x, y, z));
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
-        f[a * P.N + i] = S::ef(fi[a * P.N + i], L::w(a), P);
-        g[a * P.N + i] = S::eg(gi[a * P.N + i], L::w(a));
+        f[e + 32 * a] = S::ef(fi[a * P.N + i], L::w(a), P);
+        g[e + 32 * a] = S::eg(gi[a * P.N + i], L::w(a));
     }
 }
 

@@ -127,8 +127,8 @@ extern "C" int lbm_diag_noalloc(const lbm_params* p, const float* f, const float
                                                            base + kMaxNodes + kMaxFace, s);
     }
     if (e == cudaSuccess)
-        e = D == 2 ? lbm::Launch<lbm::D2Q9, lbm::StoreF32>::diag(dp, b, phase_eps, part, kParts, res, s)
-                   : lbm::Launch<lbm::D3Q19, lbm::StoreF32>::diag(dp, b, phase_eps, part, kParts, res, s);
+        e = D == 2 ? lbm::Launch<lbm::D2Q9, lbm::StoreF32>::diag_planar(dp, b, phase_eps, part, kParts, res, s)
+                   : lbm::Launch<lbm::D3Q19, lbm::StoreF32>::diag_planar(dp, b, phase_eps, part, kParts, res, s);
     lbm::DiagPartial h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, res, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
