@@ -2,7 +2,8 @@
 
 The translation units (kernels per lattice and storage format, batched-step
 kernels, the C ABI of contexts and of batches, the allocation-free
-diagnostics) are compiled in parallel with nvcc and linked into a shared library with a static CUDA
+diagnostics, the kernels of the learned fast-forward) are compiled in parallel
+with nvcc and linked into a shared library with a static CUDA
 runtime.  A content hash of the sources and flags decides whether a rebuild
 is needed.
 """
@@ -20,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm.so")
 UNITS = ["lbm_d3q19.cu", "lbm_d3q19_f16.cu", "lbm_d3q19_bf16.cu", "lbm_d2q9.cu", "lbm_batch_d2q9.cu",
-         "lbm_batch_d3q19.cu", "lbm_api.cu", "lbm_batch.cu", "lbm_noalloc.cu"]
+         "lbm_batch_d3q19.cu", "lbm_api.cu", "lbm_batch.cu", "lbm_noalloc.cu", "nn_kernels.cu"]
 HEADERS = ["lbm_lattice.cuh", "lbm_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
@@ -38,8 +39,9 @@ def _digest() -> str:
     for name in UNITS + HEADERS:
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(name.encode() + f.read())
-    with open(os.path.join(ROOT, "include", "lbm.h"), "rb") as f:
-        h.update(f.read())
+    for hdr in ("lbm.h", "lbm_nn.h"):
+        with open(os.path.join(ROOT, "include", hdr), "rb") as f:
+            h.update(f.read())
     h.update(" ".join(ARCH + FLAGS).encode())
     return h.hexdigest()
 

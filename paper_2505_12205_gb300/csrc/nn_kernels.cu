@@ -1,0 +1,575 @@
+// Kernels of the learned fast-forward (include/lbm_nn.h): a convolutional
+// encoder-decoder on coarse-grained (phi, u, v) fields, trained and run on the
+// GPU.  Activations are bfloat16 in channels-last layout, x[m * stride + c]
+// with m = (b * H + y) * W + x; weights are bfloat16 [co][taps * ci] (k = tap
+// * ci + c, tap = 3 ky + kx); accumulation is float32.
+//
+// The convolutions are implicit GEMMs on the tensor cores (warp-level
+// mma.sync m16n8k16, bfloat16 operands, float32 accumulators): forward
+// Y[m][co] = sum_k A[m][k] W[co][k] with A the patches of X gathered on the
+// fly; backward-data is the forward kernel with the weights flipped in space
+// and transposed in channels; the weight gradient dW[co][k] = sum_m dZ[m][co]
+// A[m][k] reduces over the spatial positions, split over blocks, with float32
+// atomics.
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "lbm_nn.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int BM = 64, BN = 64, BK = 32, LDS = BK + 8;   // tile sizes; smem row pitch (bf16)
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ uint32_t lds32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// One 64 x 64 x 32 step of the block tile from As[row m][k] and Bs[col n][k]
+// (both k-contiguous): 4 warps in 2 x 2, each 32 x 32 = 2 x 4 mma tiles.
+__device__ __forceinline__ void tile_mma(const bf16 (*As)[LDS], const bf16 (*Bs)[LDS], float (&acc)[2][4][4],
+                                         int wm, int wn, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+        uint32_t a[2][4], b[4][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int r = wm * 32 + i * 16 + g;
+            a[i][0] = lds32(&As[r][kk + 2 * t]);
+            a[i][1] = lds32(&As[r + 8][kk + 2 * t]);
+            a[i][2] = lds32(&As[r][kk + 2 * t + 8]);
+            a[i][3] = lds32(&As[r + 8][kk + 2 * t + 8]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = wn * 32 + j * 8 + g;
+            b[j][0] = lds32(&Bs[n][kk + 2 * t]);
+            b[j][1] = lds32(&Bs[n][kk + 2 * t + 8]);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
+    }
+}
+
+// 8 consecutive k of row m of the patch matrix A of X (zero outside the image
+// and beyond K); k is a multiple of 8 and ci a multiple of 8, so the 8 values
+// are one tap and one 16-byte vector.
+__device__ __forceinline__ uint4 patch8(const bf16* __restrict__ X, int xs, int ci, int taps, int m, int k, int M,
+                                        int K, int H, int W)
+{
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (m >= M || k >= K) return v;
+    const int tap = taps == 9 ? k / ci : 0, c = k - tap * ci;
+    const int x = m % W, r = m / W, y = r % H, b = r / H;
+    const int yy = y + (taps == 9 ? tap / 3 - 1 : 0), xx = x + (taps == 9 ? tap % 3 - 1 : 0);
+    if (yy < 0 || yy >= H || xx < 0 || xx >= W) return v;
+    return *reinterpret_cast<const uint4*>(X + int64_t((b * H + yy) * W + xx) * xs + c);
+}
+
+// Y[m][yo + co] (bf16, optional) and Yf[m][co] (f32, optional) =
+// relu?(sum_k A[m][k] Wt[co][k] + bias[co])
+__global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, int xs, int ci, int taps,
+                                                  const bf16* __restrict__ Wt, const float* __restrict__ bias,
+                                                  int co, bf16* __restrict__ Y, int ys, int yo,
+                                                  float* __restrict__ Yf, int yfs, int relu, int M, int H, int W)
+{
+    __shared__ __align__(16) bf16 As[BM][LDS];
+    __shared__ __align__(16) bf16 Bs[BN][LDS];
+    const int K = taps * ci;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, wm = warp >> 1, wn = warp & 1;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        for (int v = tid; v < BM * (BK / 8); v += 128) {
+            const int r = v / (BK / 8), q = v % (BK / 8);
+            *reinterpret_cast<uint4*>(&As[r][q * 8]) = patch8(X, xs, ci, taps, m0 + r, k0 + q * 8, M, K, H, W);
+        }
+        for (int v = tid; v < BN * (BK / 8); v += 128) {
+            const int r = v / (BK / 8), q = v % (BK / 8), n = n0 + r, k = k0 + q * 8;
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            if (n < co && k < K) w = *reinterpret_cast<const uint4*>(Wt + int64_t(n) * K + k);
+            *reinterpret_cast<uint4*>(&Bs[r][q * 8]) = w;
+        }
+        __syncthreads();
+        tile_mma(As, Bs, acc, wm, wn, lane);
+        __syncthreads();
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int m = m0 + wm * 32 + i * 16 + g + (e >= 2 ? 8 : 0);
+                const int n = n0 + wn * 32 + j * 8 + 2 * t + (e & 1);
+                if (m >= M || n >= co) continue;
+                float v = acc[i][j][e] + (bias ? bias[n] : 0.0f);
+                if (relu) v = fmaxf(v, 0.0f);
+                if (Y) Y[int64_t(m) * ys + yo + n] = __float2bfloat16_rn(v);
+                if (Yf) Yf[int64_t(m) * yfs + n] = v;
+            }
+}
+
+// dWt[co][k] += sum over this block's positions of dZ[m][co] A[m][k]
+// (grid: co tiles x k tiles x position splits; float32 atomics)
+__global__ void __launch_bounds__(128) k_conv_wgrad(const bf16* __restrict__ X, int xs, int ci, int taps,
+                                                    const bf16* __restrict__ dZ, int zs, int co,
+                                                    float* __restrict__ dW, int M, int H, int W, int mchunk)
+{
+    __shared__ __align__(16) bf16 As[BM][LDS];   // [co][m]
+    __shared__ __align__(16) bf16 Bs[BN][LDS];   // [k][m]
+    const int K = taps * ci;
+    const int c0 = blockIdx.x * BM, k0 = blockIdx.y * BN;
+    const int mb = blockIdx.z * mchunk, me = min(M, mb + mchunk);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, wm = warp >> 1, wn = warp & 1;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
+    for (int mm = mb; mm < me; mm += BK) {
+        // BK positions x 64 channels of dZ, stored transposed
+        for (int v = tid; v < BK * (BM / 8); v += 128) {
+            const int r = v / (BM / 8), q = v % (BM / 8), m = mm + r, c = c0 + q * 8;
+            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+            if (m < me && c < co) w = *reinterpret_cast<const uint4*>(dZ + int64_t(m) * zs + c);
+            const bf16* e8 = reinterpret_cast<const bf16*>(&w);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) As[q * 8 + e][r] = e8[e];
+        }
+        // BK positions x 64 k of the patch matrix, stored transposed
+        for (int v = tid; v < BK * (BN / 8); v += 128) {
+            const int r = v / (BN / 8), q = v % (BN / 8), m = mm + r;
+            const uint4 w = m < me ? patch8(X, xs, ci, taps, m, k0 + q * 8, M, K, H, W) : make_uint4(0u, 0u, 0u, 0u);
+            const bf16* e8 = reinterpret_cast<const bf16*>(&w);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) Bs[q * 8 + e][r] = e8[e];
+        }
+        __syncthreads();
+        tile_mma(As, Bs, acc, wm, wn, lane);
+        __syncthreads();
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = c0 + wm * 32 + i * 16 + g + (e >= 2 ? 8 : 0);
+                const int k = k0 + wn * 32 + j * 8 + 2 * t + (e & 1);
+                if (c < co && k < K) atomicAdd(&dW[int64_t(c) * K + k], acc[i][j][e]);
+            }
+}
+
+// dbias[c] += sum_m dZ[m][c]
+__global__ void k_bias_grad(const bf16* __restrict__ dZ, int zs, int c, int M, int mchunk, float* __restrict__ db)
+{
+    const int ch = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ch >= c) return;
+    const int mb = blockIdx.y * mchunk, me = min(M, mb + mchunk);
+    float s = 0.0f;
+    for (int m = mb; m < me; ++m) s += __bfloat162float(dZ[int64_t(m) * zs + ch]);
+    atomicAdd(&db[ch], s);
+}
+
+// Wflip[c][tap' * co + o] = Wt[o][(taps - 1 - tap') * ci + c]
+__global__ void k_flip(const bf16* __restrict__ Wt, int ci, int co, int taps, bf16* __restrict__ Wf)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t n = int64_t(ci) * co * taps;
+    if (i >= n) return;
+    const int c = int(i / (int64_t(taps) * co)), rem = int(i % (int64_t(taps) * co));
+    const int tp = rem / co, o = rem % co;
+    Wf[i] = Wt[int64_t(o) * taps * ci + int64_t(taps - 1 - tp) * ci + c];
+}
+
+// dZ[m][c] = dY[m][c] (Y[m][yo + c] > 0), dY read at dy_stride / dy_offset
+__global__ void k_relu_bwd(const bf16* __restrict__ dY, int dys, int dyo, const bf16* __restrict__ Y, int ys, int yo,
+                           bf16* __restrict__ dZ, int zs, int c, int64_t M)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= M * c) return;
+    const int64_t m = i / c;
+    const int ch = int(i % c);
+    const float y = __bfloat162float(Y[m * ys + yo + ch]);
+    dZ[m * zs + ch] = y > 0.0f ? dY[m * dys + dyo + ch] : __float2bfloat16_rn(0.0f);
+}
+
+// 2 x 2 average pooling: Y[b][y][x][c] = mean of X[b][2y..2y+1][2x..2x+1][c]
+__global__ void k_pool(const bf16* __restrict__ X, int xs, int xo, bf16* __restrict__ Y, int ys, int yo, int c, int nb,
+                       int H, int W)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= int64_t(nb) * Ho * Wo * c) return;
+    const int ch = int(i % c);
+    const int64_t mo = i / c;
+    const int x = int(mo % Wo), r = int(mo / Wo), y = r % Ho, b = r / Ho;
+    float s = 0.0f;
+    for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx)
+            s += __bfloat162float(X[int64_t((b * H + 2 * y + dy) * W + 2 * x + dx) * xs + xo + ch]);
+    Y[mo * ys + yo + ch] = __float2bfloat16_rn(0.25f * s);
+}
+
+// adjoint of k_pool, accumulated: dX[b][y][x][c] += dY[b][y/2][x/2][c] / 4
+__global__ void k_pool_bwd(const bf16* __restrict__ dY, int dys, bf16* __restrict__ dX, int dxs, int dxo, int c, int nb,
+                           int H, int W)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= int64_t(nb) * H * W * c) return;
+    const int ch = int(i % c);
+    const int64_t m = i / c;
+    const int x = int(m % W), r = int(m / W), y = r % H, b = r / H;
+    const float g = __bfloat162float(dY[int64_t((b * (H / 2) + y / 2) * (W / 2) + x / 2) * dys + ch]);
+    bf16* p = dX + m * dxs + dxo + ch;
+    *p = __float2bfloat16_rn(__bfloat162float(*p) + 0.25f * g);
+}
+
+// nearest 2x upsampling: Y[b][y][x][yo + c] = X[b][y/2][x/2][c] (Y is H x W)
+__global__ void k_up(const bf16* __restrict__ X, int xs, bf16* __restrict__ Y, int ys, int yo, int c, int nb, int H,
+                     int W)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= int64_t(nb) * H * W * c) return;
+    const int ch = int(i % c);
+    const int64_t m = i / c;
+    const int x = int(m % W), r = int(m / W), y = r % H, b = r / H;
+    Y[m * ys + yo + ch] = X[int64_t((b * (H / 2) + y / 2) * (W / 2) + x / 2) * xs + ch];
+}
+
+// adjoint of k_up: dX[b][y][x][c] = sum of dY over the 2 x 2 children (dY channels at dyo)
+__global__ void k_up_bwd(const bf16* __restrict__ dY, int dys, int dyo, bf16* __restrict__ dX, int dxs, int c, int nb,
+                         int H, int W)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= int64_t(nb) * Ho * Wo * c) return;
+    const int ch = int(i % c);
+    const int64_t mo = i / c;
+    const int x = int(mo % Wo), r = int(mo / Wo), y = r % Ho, b = r / Ho;
+    float s = 0.0f;
+    for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx)
+            s += __bfloat162float(dY[int64_t((b * H + 2 * y + dy) * W + 2 * x + dx) * dys + dyo + ch]);
+    dX[mo * dxs + ch] = __float2bfloat16_rn(s);
+}
+
+// residual head and loss: pred = x[:, :c] + d, r = pred - target;
+// loss += sum r^2 / n (atomic); dd = 2 r / n (bf16, the gradient of the head)
+__global__ void k_mse(const float* __restrict__ d, int dstr, const bf16* __restrict__ x, int xs, const float* __restrict__ target,
+                      int c, int64_t M, float inv_n, float* __restrict__ pred, bf16* __restrict__ dd, int dds,
+                      float* __restrict__ loss)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    float r2 = 0.0f;
+    if (i < M * c) {
+        const int64_t m = i / c;
+        const int ch = int(i % c);
+        const float p = __bfloat162float(x[m * xs + ch]) + d[m * dstr + ch];
+        if (pred) pred[i] = p;
+        if (target) {
+            const float r = p - target[i];
+            r2 = r * r * inv_n;
+            if (dd) dd[m * dds + ch] = __float2bfloat16_rn(2.0f * r * inv_n);
+        }
+    }
+    if (loss) {
+        for (int o = 16; o > 0; o >>= 1) r2 += __shfl_down_sync(0xffffffffu, r2, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(loss, r2);
+    }
+}
+
+// Adam on float32 master weights; writes the bf16 copy the kernels read
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ mo, float* __restrict__ ve, const float* __restrict__ g,
+                       bf16* __restrict__ wb, int64_t n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float m = b1 * mo[i] + (1.0f - b1) * gi;
+    const float v = b2 * ve[i] + (1.0f - b2) * gi * gi;
+    mo[i] = m;
+    ve[i] = v;
+    const float wi = w[i] - lr * (m * c1) / (sqrtf(v * c2) + eps);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16_rn(wi);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ b, int64_t n)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+}
+
+// dA += dB over c channels (bf16 tensors with strides/offsets)
+__global__ void k_add(const bf16* __restrict__ s, int ss, int so, bf16* __restrict__ d, int ds, int dof, int c, int64_t M)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= M * c) return;
+    const int64_t m = i / c;
+    const int ch = int(i % c);
+    bf16* p = d + m * ds + dof + ch;
+    *p = __float2bfloat16_rn(__bfloat162float(*p) + __bfloat162float(s[m * ss + so + ch]));
+}
+
+// Coarse input of the network from solver fields (planes [H][W] of phi, u, v
+// at the fine resolution): mean over f x f cells, scaled, channels-last bf16
+// x[b][y][x][c] with c = 0 phi, 1 u * su, 2 v * su, 3 cond, 4..cs-1 zero.
+__global__ void k_coarsen(const float* __restrict__ phi, const float* __restrict__ u, const float* __restrict__ v,
+                          int Hf, int Wf, int f, float su, float cond, bf16* __restrict__ x, int cs, float* __restrict__ xf)
+{
+    const int Hc = Hf / f, Wc = Wf / f;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Hc * Wc) return;
+    const int cx = i % Wc, cy = i / Wc;
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+    for (int dy = 0; dy < f; ++dy)
+        for (int dx = 0; dx < f; ++dx) {
+            const int64_t j = int64_t(cy * f + dy) * Wf + cx * f + dx;
+            s0 += phi[j];
+            s1 += u[j];
+            s2 += v[j];
+        }
+    const float inv = 1.0f / float(f * f);
+    const float vals[4] = {s0 * inv, s1 * inv * su, s2 * inv * su, cond};
+    for (int c = 0; c < cs; ++c) {
+        const float val = c < 4 ? vals[c] : 0.0f;
+        if (x) x[int64_t(i) * cs + c] = __float2bfloat16_rn(val);
+        if (xf && c < 3) xf[int64_t(i) * 3 + c] = val;
+    }
+}
+
+// Fine fields from a coarse prediction pred[y][x][3] (phi, u su, v su):
+// bilinear interpolation between coarse cell centres (clamped at the edges).
+__global__ void k_refine(const float* __restrict__ pred, int Hc, int Wc, int f, float inv_su, float* __restrict__ phi,
+                         float* __restrict__ u, float* __restrict__ v)
+{
+    const int Hf = Hc * f, Wf = Wc * f;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= int64_t(Hf) * Wf) return;
+    const int x = int(i % Wf), y = int(i / Wf);
+    const float cx = (x + 0.5f) / f - 0.5f, cy = (y + 0.5f) / f - 0.5f;
+    const int x0 = min(max(int(floorf(cx)), 0), Wc - 1), y0 = min(max(int(floorf(cy)), 0), Hc - 1);
+    const int x1 = min(x0 + 1, Wc - 1), y1 = min(y0 + 1, Hc - 1);
+    const float tx = fminf(fmaxf(cx - x0, 0.0f), 1.0f), ty = fminf(fmaxf(cy - y0, 0.0f), 1.0f);
+    float out[3];
+    for (int c = 0; c < 3; ++c) {
+        const float a = pred[(int64_t(y0) * Wc + x0) * 3 + c], b = pred[(int64_t(y0) * Wc + x1) * 3 + c];
+        const float d = pred[(int64_t(y1) * Wc + x0) * 3 + c], e = pred[(int64_t(y1) * Wc + x1) * 3 + c];
+        out[c] = (1.0f - ty) * ((1.0f - tx) * a + tx * b) + ty * ((1.0f - tx) * d + tx * e);
+    }
+    phi[i] = out[0];
+    u[i] = out[1] * inv_su;
+    v[i] = out[2] * inv_su;
+}
+
+thread_local std::string g_nn_err;
+
+int nn_fail(int code, const std::string& msg)
+{
+    g_nn_err = msg;
+    return code;
+}
+
+int nn_launch_status(const char* what)
+{
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return LBM_NN_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+unsigned blocks_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_nn_last_error(void) { return g_nn_err.c_str(); }
+
+int lbm_nn_conv_fwd(const void* x, int32_t x_stride, int32_t ci, int32_t taps, const void* wt, const float* bias,
+                    int32_t co, void* y, int32_t y_stride, int32_t y_offset, float* yf, int32_t yf_stride, int32_t relu,
+                    int32_t nb, int32_t h, int32_t w, void* stream)
+{
+    if (!x || !wt || (!y && !yf) || nb < 1 || h < 1 || w < 1 || co < 1) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: bad arguments");
+    if (taps != 9 && taps != 1) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: taps must be 9 or 1");
+    if (ci < 8 || ci % 8 || x_stride % 8 || x_stride < ci) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: ci and the input stride must be multiples of 8");
+    if (!aligned16(x) || !aligned16(wt)) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: x and wt must be 16-byte aligned");
+    if (y && (y_offset < 0 || y_offset + co > y_stride)) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: output channels exceed the stride");
+    if (yf && yf_stride < co) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: f32 output stride below co");
+    const int M = nb * h * w;
+    dim3 grid(blocks_for(M, BM), blocks_for(co, BN));
+    k_conv_fwd<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const bf16*>(x), x_stride, ci, taps, static_cast<const bf16*>(wt), bias, co, static_cast<bf16*>(y),
+        y_stride, y_offset, yf, yf_stride, relu, M, h, w);
+    return nn_launch_status("conv_fwd");
+}
+
+int lbm_nn_conv_wgrad(const void* x, int32_t x_stride, int32_t ci, int32_t taps, const void* dz, int32_t dz_stride,
+                      int32_t co, float* dwt, float* dbias, int32_t nb, int32_t h, int32_t w, void* stream)
+{
+    if (!x || !dz || !dwt || nb < 1 || h < 1 || w < 1 || co < 1) return nn_fail(LBM_NN_ERR_ARG, "conv_wgrad: bad arguments");
+    if (taps != 9 && taps != 1) return nn_fail(LBM_NN_ERR_ARG, "conv_wgrad: taps must be 9 or 1");
+    if (ci < 8 || ci % 8 || x_stride % 8 || co % 8 || dz_stride % 8) return nn_fail(LBM_NN_ERR_ARG, "conv_wgrad: channels and strides must be multiples of 8");
+    if (x_stride < ci || dz_stride < co) return nn_fail(LBM_NN_ERR_ARG, "conv_wgrad: strides below the channel counts");
+    if (!aligned16(x) || !aligned16(dz)) return nn_fail(LBM_NN_ERR_ARG, "conv_wgrad: x and dz must be 16-byte aligned");
+    const int M = nb * h * w, K = taps * ci;
+    const int mchunk = 1024;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    dim3 grid(blocks_for(co, BM), blocks_for(K, BN), blocks_for(M, mchunk));
+    k_conv_wgrad<<<grid, 128, 0, s>>>(static_cast<const bf16*>(x), x_stride, ci, taps, static_cast<const bf16*>(dz),
+                                      dz_stride, co, dwt, M, h, w, mchunk);
+    if (dbias) {
+        dim3 gb(blocks_for(co, 64), blocks_for(M, 4096));
+        k_bias_grad<<<gb, 64, 0, s>>>(static_cast<const bf16*>(dz), dz_stride, co, M, 4096, dbias);
+    }
+    return nn_launch_status("conv_wgrad");
+}
+
+int lbm_nn_flip_weights(const void* wt, int32_t ci, int32_t co, int32_t taps, void* wflip, void* stream)
+{
+    if (!wt || !wflip || ci < 1 || co < 1 || (taps != 9 && taps != 1)) return nn_fail(LBM_NN_ERR_ARG, "flip: bad arguments");
+    const int64_t n = int64_t(ci) * co * taps;
+    k_flip<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const bf16*>(wt), ci, co, taps,
+                                                                              static_cast<bf16*>(wflip));
+    return nn_launch_status("flip");
+}
+
+int lbm_nn_relu_bwd(const void* dy, int32_t dy_stride, int32_t dy_offset, const void* y, int32_t y_stride,
+                    int32_t y_offset, void* dz, int32_t dz_stride, int32_t c, int64_t m, void* stream)
+{
+    if (!dy || !y || !dz || c < 1 || m < 1) return nn_fail(LBM_NN_ERR_ARG, "relu_bwd: bad arguments");
+    k_relu_bwd<<<blocks_for(m * c, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const bf16*>(dy), dy_stride, dy_offset, static_cast<const bf16*>(y), y_stride, y_offset,
+        static_cast<bf16*>(dz), dz_stride, c, m);
+    return nn_launch_status("relu_bwd");
+}
+
+int lbm_nn_pool(const void* x, int32_t x_stride, int32_t x_offset, void* y, int32_t y_stride, int32_t y_offset,
+                int32_t c, int32_t nb, int32_t h, int32_t w, void* stream)
+{
+    if (!x || !y || c < 1 || h % 2 || w % 2) return nn_fail(LBM_NN_ERR_ARG, "pool: bad arguments");
+    const int64_t n = int64_t(nb) * (h / 2) * (w / 2) * c;
+    k_pool<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const bf16*>(x), x_stride, x_offset, static_cast<bf16*>(y), y_stride, y_offset, c, nb, h, w);
+    return nn_launch_status("pool");
+}
+
+int lbm_nn_pool_bwd(const void* dy, int32_t dy_stride, void* dx, int32_t dx_stride, int32_t dx_offset, int32_t c,
+                    int32_t nb, int32_t h, int32_t w, void* stream)
+{
+    if (!dy || !dx || c < 1 || h % 2 || w % 2) return nn_fail(LBM_NN_ERR_ARG, "pool_bwd: bad arguments");
+    const int64_t n = int64_t(nb) * h * w * c;
+    k_pool_bwd<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const bf16*>(dy), dy_stride, static_cast<bf16*>(dx), dx_stride, dx_offset, c, nb, h, w);
+    return nn_launch_status("pool_bwd");
+}
+
+int lbm_nn_upsample(const void* x, int32_t x_stride, void* y, int32_t y_stride, int32_t y_offset, int32_t c,
+                    int32_t nb, int32_t h, int32_t w, void* stream)
+{
+    if (!x || !y || c < 1 || h % 2 || w % 2) return nn_fail(LBM_NN_ERR_ARG, "upsample: bad arguments");
+    const int64_t n = int64_t(nb) * h * w * c;
+    k_up<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const bf16*>(x), x_stride, static_cast<bf16*>(y), y_stride, y_offset, c, nb, h, w);
+    return nn_launch_status("upsample");
+}
+
+int lbm_nn_upsample_bwd(const void* dy, int32_t dy_stride, int32_t dy_offset, void* dx, int32_t dx_stride, int32_t c,
+                        int32_t nb, int32_t h, int32_t w, void* stream)
+{
+    if (!dy || !dx || c < 1 || h % 2 || w % 2) return nn_fail(LBM_NN_ERR_ARG, "upsample_bwd: bad arguments");
+    const int64_t n = int64_t(nb) * (h / 2) * (w / 2) * c;
+    k_up_bwd<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const bf16*>(dy), dy_stride, dy_offset, static_cast<bf16*>(dx), dx_stride, c, nb, h, w);
+    return nn_launch_status("upsample_bwd");
+}
+
+int lbm_nn_mse(const float* d, int32_t d_stride, const void* x, int32_t x_stride, const float* target, int32_t c,
+               int64_t m, float* pred, void* dd, int32_t dd_stride, float* loss, void* stream)
+{
+    if (!d || !x || c < 1 || m < 1 || d_stride < c || x_stride < c) return nn_fail(LBM_NN_ERR_ARG, "mse: bad arguments");
+    const int64_t n = m * c;
+    k_mse<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        d, d_stride, static_cast<const bf16*>(x), x_stride, target, c, m, 1.0f / float(n), pred, static_cast<bf16*>(dd),
+        dd_stride, loss);
+    return nn_launch_status("mse");
+}
+
+int lbm_nn_adam(float* w, float* m, float* v, const float* g, void* w_bf16, int64_t n, float lr, float beta1,
+                float beta2, float eps, int32_t t, void* stream)
+{
+    if (!w || !m || !v || !g || n < 1 || t < 1) return nn_fail(LBM_NN_ERR_ARG, "adam: bad arguments");
+    const float c1 = 1.0f / (1.0f - powf(beta1, float(t))), c2 = 1.0f / (1.0f - powf(beta2, float(t)));
+    k_adam<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(w, m, v, g, static_cast<bf16*>(w_bf16), n,
+                                                                             lr, beta1, beta2, eps, c1, c2);
+    return nn_launch_status("adam");
+}
+
+int lbm_nn_to_bf16(const float* a, void* b, int64_t n, void* stream)
+{
+    if (!a || !b || n < 1) return nn_fail(LBM_NN_ERR_ARG, "to_bf16: bad arguments");
+    k_to_bf16<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(a, static_cast<bf16*>(b), n);
+    return nn_launch_status("to_bf16");
+}
+
+int lbm_nn_add(const void* src, int32_t src_stride, int32_t src_offset, void* dst, int32_t dst_stride,
+               int32_t dst_offset, int32_t c, int64_t m, void* stream)
+{
+    if (!src || !dst || c < 1 || m < 1) return nn_fail(LBM_NN_ERR_ARG, "add: bad arguments");
+    k_add<<<blocks_for(m * c, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const bf16*>(src), src_stride, src_offset, static_cast<bf16*>(dst), dst_stride, dst_offset, c, m);
+    return nn_launch_status("add");
+}
+
+int lbm_nn_coarsen(const float* phi, const float* u, const float* v, int32_t hf, int32_t wf, int32_t factor,
+                   float u_scale, float cond, void* x, int32_t x_channels, float* xf, void* stream)
+{
+    if (!phi || !u || !v || factor < 1 || hf % factor || wf % factor || (!x && !xf) || (x && x_channels < 4))
+        return nn_fail(LBM_NN_ERR_ARG, "coarsen: bad arguments");
+    const int n = (hf / factor) * (wf / factor);
+    k_coarsen<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(phi, u, v, hf, wf, factor, u_scale, cond,
+                                                                                 static_cast<bf16*>(x), x_channels, xf);
+    return nn_launch_status("coarsen");
+}
+
+int lbm_nn_refine(const float* pred, int32_t hc, int32_t wc, int32_t factor, float u_scale, float* phi, float* u,
+                  float* v, void* stream)
+{
+    if (!pred || !phi || !u || !v || factor < 1 || hc < 1 || wc < 1 || !(u_scale > 0.0f))
+        return nn_fail(LBM_NN_ERR_ARG, "refine: bad arguments");
+    const int64_t n = int64_t(hc) * factor * wc * factor;
+    k_refine<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(pred, hc, wc, factor, 1.0f / u_scale, phi,
+                                                                               u, v);
+    return nn_launch_status("refine");
+}
+
+}  // extern "C"
