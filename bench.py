@@ -20,6 +20,11 @@ the FP64 oracle on a slab of the same workload on the host cores.
 `--impl reference` times the FP64 CPU oracle (the baseline of this project)
 on a bounded slab of the same workload instead.
 
+`--workload learned` measures the learned fast-forward of planar-jet sweeps
+(D2Q9 512 x 2048, We in [1, 10]): snapshots generated by the solver, the
+network trained on the GPU by the library's kernels, then held-out cases run
+with the network in the loop against the solver alone.
+
 `--workload sweep` measures the batched sweep instead: 512 seeded 2D cases
 (drops and capillary waves, L x L with L uniform in 64..512, about 51 M nodes,
 float16 storage by default) advanced together by the batch API, reported as
@@ -478,6 +483,58 @@ def run_sweep(args):
     return 0
 
 
+LEARNED = dict(name="planar-jet fast-forward, D2Q9 512x2048, We in [1,10], K=200",
+               train_We=[1.0, 2.3, 3.6, 4.9, 6.1, 7.4, 8.7, 10.0], t0=4000, t1=12000)
+
+
+def run_learned(args):
+    """Cases per hour of planar-jet runs with the learned fast-forward in the
+    loop vs the solver alone, on held-out Weber numbers."""
+    import torch
+    from paper_2505_12205_gb300 import build, nn, surrogate as S
+    build.build()
+    torch.cuda.set_device(0)
+    t0, t1 = LEARNED["t0"], LEARNED["t1"]
+    log = lambda msg: print("[learned] " + msg, file=sys.stderr, flush=True)
+    tic = time.perf_counter()
+    X, Y, cases = S.generate(LEARNED["train_We"], t0, t1)
+    t_gen = time.perf_counter() - tic
+    r = np.random.Generator(np.random.PCG64(C.SEED + 5))
+    test_We = sorted(float(w) for w in r.uniform(1.0, 10.0, 4))
+    Xt, Yt, _ = S.generate(test_We, t0, t1)
+    net = nn.UNet(cin=S.CIN, ch=(32, 64, 128, 256))
+    net.init_he(seed=7)
+    tic = time.perf_counter()
+    hist = S.train(net, X, Y, np.arange(X.shape[0]), epochs=args.epochs, accum=4, lr=1e-3, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - tic
+    val, pers = S.evaluate(net, Xt, Yt, np.arange(Xt.shape[0]))
+    res = [S.fast_forward(net, w, t0, t1, skip=args.skip) for w in test_We]
+    ms_solver = sum(x["ms_solver"] for x in res)
+    ms_ff = sum(x["ms_fast_forward"] for x in res)
+    steps = t1 - t0
+    accepted = [x for x in res if x["accepted_at_end"]]
+    line = {
+        "metric": "cases_per_hour_learned", "value": len(res) * 3600e3 / ms_ff, "unit": "cases/h",
+        "n_gpus": 1, "steps": steps, "warmup": 0, "ms_per_step": ms_ff / len(res) / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 solver, bf16 network with f32 accumulation", "data": "synthetic (generated by the solver)",
+        "config": {"workload": LEARNED["name"], "train_We": LEARNED["train_We"], "test_We": test_We,
+                   "span_steps": [t0, t1], "pairs": int(X.shape[0]), "epochs": args.epochs, "skip": args.skip,
+                   "network": "4-level encoder-decoder, channels 32-256, 128x512 input"},
+        "solver_alone": {"value": len(res) * 3600e3 / ms_solver, "unit": "cases/h"},
+        "speedup_vs_solver": ms_solver / ms_ff,
+        "accepted_at_end": len(accepted), "cases": len(res),
+        "train": {"seconds": t_train, "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
+                  "generate_seconds": t_gen},
+        "held_out": {"loss": val, "persistence_loss": pers},
+        "per_case": [{k: v for k, v in x.items() if k != "judged"} for x in res],
+        "judged_windows": [[{k: round(v, 4) for k, v in j.items()} for j in x["judged"]] for x in res],
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,7 +545,9 @@ def main():
     ap.add_argument("--storage", default=None, choices=["fp32", "fp16", "bf16"],
                     help="population storage format (arithmetic is float32); default fp32 for the "
                          "jet, fp16 for the sweep")
-    ap.add_argument("--workload", default="jet", choices=["jet", "sweep"])
+    ap.add_argument("--workload", default="jet", choices=["jet", "sweep", "learned"])
+    ap.add_argument("--epochs", type=int, default=8, help="training epochs of the learned workload")
+    ap.add_argument("--skip", type=int, default=1, help="windows predicted after each passing check (learned)")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
                     help="reduced grid of the same jet workload (profiling captures)")
     args = ap.parse_args()
@@ -498,6 +557,8 @@ def main():
         return run_reference(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "learned":
+        return run_learned(args)
     if args.storage is None:
         args.storage = "fp32"
     return run_gpu(args)

@@ -102,9 +102,32 @@ int lbm_nn_coarsen(const float* phi, const float* u, const float* v, int32_t hf,
 
 /* Solver fields from a coarse prediction pred[m][3] = (phi, u u_scale, v
  * u_scale) of an hc x wc grid: bilinear interpolation between coarse cell
- * centres (clamped at the edges) onto the hc factor x wc factor grid. */
-int lbm_nn_refine(const float* pred, int32_t hc, int32_t wc, int32_t factor, float u_scale, float* phi, float* u,
-                  float* v, void* stream);
+ * centres (clamped at the edges) onto the hc factor x wc factor grid, phi
+ * clamped to [0, 1] and the speed limited to u_max (a restart state the
+ * solver can take). */
+int lbm_nn_refine(const float* pred, int32_t hc, int32_t wc, int32_t factor, float u_scale, float u_max, float* phi,
+                  float* u, float* v, void* stream);
+
+/* Interface-localised mass projection of a phase field (n values): phi +=
+ * c 4 q (1 - q), q = phi clamped to [0, 1], with c such that sum phi =
+ * target before rounding (the correction vanishes in the pure phases).  sums: 2 doubles of scratch; on
+ * return (after the stream completes) they hold sum phi and sum 4 phi (1 -
+ * phi) of the field before the correction. */
+int lbm_nn_mass_project(float* phi, int64_t n, double target, double* sums, void* stream);
+
+/* Comparison of the phase fields a (e.g. a prediction) and b (the solver's)
+ * on an ny x nx grid (x fastest): out[0] = cells on different sides of
+ * phi = 1/2, out[1] = grid edges across which b crosses 1/2 (x-neighbours
+ * periodic), out[2] = sum a, out[3] = sum b.  out[0] / out[1] is the mean
+ * distance between the two interfaces in cells. */
+int lbm_nn_interface_stats(const float* a, const float* b, int32_t ny, int32_t nx, double* out, void* stream);
+
+/* Intact length of a jet issued along y from y = 0 (the quantity behind a
+ * breakup length): per column x in [x0, x1) the number of cells from y = 0
+ * up to the first phi <= 1/2; out[0] / out[1] = its largest value over the
+ * columns for a / b (int32). */
+int lbm_nn_jet_length(const float* a, const float* b, int32_t ny, int32_t nx, int32_t x0, int32_t x1, int32_t* out,
+                      void* stream);
 
 #ifdef __cplusplus
 }

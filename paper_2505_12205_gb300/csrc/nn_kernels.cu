@@ -367,9 +367,10 @@ __global__ void k_coarsen(const float* __restrict__ phi, const float* __restrict
 }
 
 // Fine fields from a coarse prediction pred[y][x][3] (phi, u su, v su):
-// bilinear interpolation between coarse cell centres (clamped at the edges).
-__global__ void k_refine(const float* __restrict__ pred, int Hc, int Wc, int f, float inv_su, float* __restrict__ phi,
-                         float* __restrict__ u, float* __restrict__ v)
+// bilinear interpolation between coarse cell centres (clamped at the edges);
+// phi clamped to [0, 1] and the speed to umax.
+__global__ void k_refine(const float* __restrict__ pred, int Hc, int Wc, int f, float inv_su, float umax,
+                         float* __restrict__ phi, float* __restrict__ u, float* __restrict__ v)
 {
     const int Hf = Hc * f, Wf = Wc * f;
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -385,9 +386,89 @@ __global__ void k_refine(const float* __restrict__ pred, int Hc, int Wc, int f, 
         const float d = pred[(int64_t(y1) * Wc + x0) * 3 + c], e = pred[(int64_t(y1) * Wc + x1) * 3 + c];
         out[c] = (1.0f - ty) * ((1.0f - tx) * a + tx * b) + ty * ((1.0f - tx) * d + tx * e);
     }
-    phi[i] = out[0];
-    u[i] = out[1] * inv_su;
-    v[i] = out[2] * inv_su;
+    const float uu = out[1] * inv_su, vv = out[2] * inv_su;
+    const float sp = sqrtf(uu * uu + vv * vv), k = sp > umax ? umax / sp : 1.0f;
+    phi[i] = fminf(fmaxf(out[0], 0.0f), 1.0f);
+    u[i] = uu * k;
+    v[i] = vv * k;
+}
+
+// sums[0] += sum phi, sums[1] += sum 4 phi (1 - phi) over n values (float64 atomics per warp)
+__global__ void k_mass_sums(const float* __restrict__ phi, int64_t n, double* __restrict__ sums)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    double a = 0.0, b = 0.0;
+    if (i < n) {
+        const double p = phi[i], q = fmin(fmax(p, 0.0), 1.0);
+        a = p;
+        b = 4.0 * q * (1.0 - q);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sums[0], a);
+        atomicAdd(&sums[1], b);
+    }
+}
+
+// phi += c 4 phi (1 - phi), c = (target - sums[0]) / sums[1] (no change where sums[1] == 0)
+__global__ void k_mass_apply(float* __restrict__ phi, int64_t n, double target, const double* __restrict__ sums)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n || !(sums[1] > 0.0)) return;
+    const float c = float((target - sums[0]) / sums[1]);
+    const float p = phi[i], q = fminf(fmaxf(p, 0.0f), 1.0f);
+    phi[i] = p + c * 4.0f * q * (1.0f - q);
+}
+
+// Interface comparison of two phase fields on an ny x nx grid:
+// out[0] += cells where (a > 1/2) != (b > 1/2); out[1] += grid edges
+// (x- and y-neighbours, periodic in x) across which b crosses 1/2;
+// out[2] += sum a; out[3] += sum b.
+__global__ void k_interface(const float* __restrict__ a, const float* __restrict__ b, int ny, int nx,
+                            double* __restrict__ out)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    double d = 0.0, e = 0.0, sa = 0.0, sb = 0.0;
+    if (i < int64_t(ny) * nx) {
+        const int x = int(i % nx), y = int(i / nx);
+        const bool ia = a[i] > 0.5f, ib = b[i] > 0.5f;
+        d = ia != ib ? 1.0 : 0.0;
+        const int64_t ir = int64_t(y) * nx + (x + 1) % nx;
+        e = ((b[ir] > 0.5f) != ib) ? 1.0 : 0.0;
+        if (y + 1 < ny) e += ((b[i + nx] > 0.5f) != ib) ? 1.0 : 0.0;
+        sa = a[i];
+        sb = b[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        d += __shfl_down_sync(0xffffffffu, d, o);
+        e += __shfl_down_sync(0xffffffffu, e, o);
+        sa += __shfl_down_sync(0xffffffffu, sa, o);
+        sb += __shfl_down_sync(0xffffffffu, sb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], d);
+        atomicAdd(&out[1], e);
+        atomicAdd(&out[2], sa);
+        atomicAdd(&out[3], sb);
+    }
+}
+
+// Intact length of a jet issued along y from y = 0: per column x of
+// [x0, x1), the number of cells from y = 0 up to the first phi <= 1/2;
+// out[0] / out[1] = the largest over the columns, for a / b.
+__global__ void k_jet_length(const float* __restrict__ a, const float* __restrict__ b, int ny, int nx, int x0, int x1,
+                             int* __restrict__ out)
+{
+    const int x = x0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= x1) return;
+    int la = 0, lb = 0;
+    while (la < ny && a[int64_t(la) * nx + x] > 0.5f) ++la;
+    while (lb < ny && b[int64_t(lb) * nx + x] > 0.5f) ++lb;
+    atomicMax(&out[0], la);
+    atomicMax(&out[1], lb);
 }
 
 thread_local std::string g_nn_err;
@@ -561,15 +642,48 @@ int lbm_nn_coarsen(const float* phi, const float* u, const float* v, int32_t hf,
     return nn_launch_status("coarsen");
 }
 
-int lbm_nn_refine(const float* pred, int32_t hc, int32_t wc, int32_t factor, float u_scale, float* phi, float* u,
-                  float* v, void* stream)
+int lbm_nn_refine(const float* pred, int32_t hc, int32_t wc, int32_t factor, float u_scale, float u_max, float* phi,
+                  float* u, float* v, void* stream)
 {
-    if (!pred || !phi || !u || !v || factor < 1 || hc < 1 || wc < 1 || !(u_scale > 0.0f))
+    if (!pred || !phi || !u || !v || factor < 1 || hc < 1 || wc < 1 || !(u_scale > 0.0f) || !(u_max > 0.0f))
         return nn_fail(LBM_NN_ERR_ARG, "refine: bad arguments");
     const int64_t n = int64_t(hc) * factor * wc * factor;
-    k_refine<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(pred, hc, wc, factor, 1.0f / u_scale, phi,
-                                                                               u, v);
+    k_refine<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(pred, hc, wc, factor, 1.0f / u_scale,
+                                                                               u_max, phi, u, v);
     return nn_launch_status("refine");
+}
+
+int lbm_nn_mass_project(float* phi, int64_t n, double target, double* sums, void* stream)
+{
+    if (!phi || !sums || n < 1) return nn_fail(LBM_NN_ERR_ARG, "mass_project: bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), s);
+    if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("mass_project: ") + cudaGetErrorString(e));
+    k_mass_sums<<<blocks_for(n, 256), 256, 0, s>>>(phi, n, sums);
+    k_mass_apply<<<blocks_for(n, 256), 256, 0, s>>>(phi, n, target, sums);
+    return nn_launch_status("mass_project");
+}
+
+int lbm_nn_interface_stats(const float* a, const float* b, int32_t ny, int32_t nx, double* out, void* stream)
+{
+    if (!a || !b || !out || ny < 1 || nx < 1) return nn_fail(LBM_NN_ERR_ARG, "interface_stats: bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(out, 0, 4 * sizeof(double), s);
+    if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("interface_stats: ") + cudaGetErrorString(e));
+    k_interface<<<blocks_for(int64_t(ny) * nx, 256), 256, 0, s>>>(a, b, ny, nx, out);
+    return nn_launch_status("interface_stats");
+}
+
+int lbm_nn_jet_length(const float* a, const float* b, int32_t ny, int32_t nx, int32_t x0, int32_t x1, int32_t* out,
+                      void* stream)
+{
+    if (!a || !b || !out || ny < 1 || nx < 1 || x0 < 0 || x1 > nx || x0 >= x1)
+        return nn_fail(LBM_NN_ERR_ARG, "jet_length: bad arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(int32_t), s);
+    if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("jet_length: ") + cudaGetErrorString(e));
+    k_jet_length<<<blocks_for(x1 - x0, 128), 128, 0, s>>>(a, b, ny, nx, x0, x1, out);
+    return nn_launch_status("jet_length");
 }
 
 }  // extern "C"

@@ -24,7 +24,8 @@ from . import lbm as _lbm
 LBM_NN_OK, LBM_NN_ERR_ARG, LBM_NN_ERR_CUDA = 0, -1, -2
 NN_EXPORTS = ["lbm_nn_last_error", "lbm_nn_conv_fwd", "lbm_nn_conv_wgrad", "lbm_nn_flip_weights", "lbm_nn_relu_bwd",
               "lbm_nn_pool", "lbm_nn_pool_bwd", "lbm_nn_upsample", "lbm_nn_upsample_bwd", "lbm_nn_mse", "lbm_nn_adam",
-              "lbm_nn_to_bf16", "lbm_nn_add", "lbm_nn_coarsen", "lbm_nn_refine"]
+              "lbm_nn_to_bf16", "lbm_nn_add", "lbm_nn_coarsen", "lbm_nn_refine", "lbm_nn_mass_project",
+              "lbm_nn_interface_stats", "lbm_nn_jet_length"]
 
 _lib = None
 
@@ -53,7 +54,10 @@ def load():
         "lbm_nn_to_bf16": [fp, vp, i64, vp],
         "lbm_nn_add": [vp, i32, i32, vp, i32, i32, i32, i64, vp],
         "lbm_nn_coarsen": [fp, fp, fp, i32, i32, i32, f32, f32, vp, i32, fp, vp],
-        "lbm_nn_refine": [fp, i32, i32, i32, f32, fp, fp, fp, vp],
+        "lbm_nn_refine": [fp, i32, i32, i32, f32, f32, fp, fp, fp, vp],
+        "lbm_nn_mass_project": [fp, i64, ctypes.c_double, fp, vp],
+        "lbm_nn_interface_stats": [fp, fp, i32, i32, fp, vp],
+        "lbm_nn_jet_length": [fp, fp, i32, i32, i32, i32, fp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -138,6 +142,15 @@ class UNet:
             self.view[name]["w"].copy_(torch.from_numpy(np.ascontiguousarray(params[name + ".w"], np.float32).reshape(-1)))
             self.view[name]["b"].copy_(torch.from_numpy(np.ascontiguousarray(params[name + ".b"], np.float32)))
         self.sync_copies()
+
+    def init_he(self, seed=0):
+        """Seeded He-normal weights (std sqrt(2 / fan-in)), zero biases."""
+        r = np.random.Generator(np.random.PCG64(seed))
+        p = {}
+        for name, ci, co, taps in self.layers:
+            p[name + ".w"] = r.standard_normal((co, taps * ci)) * np.sqrt(2.0 / (taps * ci))
+            p[name + ".b"] = np.zeros(co)
+        self.set_params(p)
 
     def get_params(self) -> dict:
         out = {}
@@ -252,12 +265,14 @@ class UNet:
         dst.view(m, ds)[:, do:do + c].zero_()
         call("lbm_nn_add", _p(src), ss, 0, _p(dst), ds, do, c, m, _s(self.stream))
 
-    def backward(self, x, B, H, W):
-        """Gradients (accumulated into the f32 gradient buffer, zeroed here)
-        of the loss of the last forward with a target."""
+    def backward(self, x, B, H, W, zero_grad=True):
+        """Gradients of the loss of the last forward with a target, added to
+        the f32 gradient buffer (zeroed first unless zero_grad is False, which
+        accumulates over several samples)."""
         A = self._alloc(B, H, W)
         L, ch = self.L, self.ch
-        self.g.zero_()
+        if zero_grad:
+            self.g.zero_()
         s = _s(self.stream)
         # head (1 x 1, no activation): dhead is the gradient of its output
         self._wgrad("head", A["dd0"], ch[0], A["dhead"], self.head, B, H, W)
