@@ -40,13 +40,19 @@ typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 } lbm_lattice;
 /* Face conditions, App. B: periodic (eq:periodic_f/g/phi), halfway
  * bounce-back wall (eq:no_slip_f/g), velocity + phase-field inlet
  * (eq:velocity_boundary_distribution, eq:unknown_distribution_*), convective
- * outlet (eq:convective_f/g).  The inlet is allowed only on the low face and
- * the outlet only on the high face of the last axis (y in 2D, z in 3D). */
+ * outlet (eq:convective_f/g), free slip (eq:free_slip_f/g: specular
+ * reflection, the population returns to the tangential neighbour with its
+ * normal component reversed; over an edge of two slip faces both components
+ * are reversed; a crossing of a wall as well bounces back).  The inlet is
+ * allowed only on the low face and the outlet only on the high face of the
+ * last axis (y in 2D, z in 3D).  The ghost phi of walls, slip faces and the
+ * outlet is that of the adjacent node (zero normal gradient). */
 typedef enum {
     LBM_BC_PERIODIC = 0,
     LBM_BC_WALL = 1,
     LBM_BC_INLET = 2,
-    LBM_BC_OUTFLOW = 3
+    LBM_BC_OUTFLOW = 3,
+    LBM_BC_FREESLIP = 4
 } lbm_bc;
 
 typedef enum {
@@ -65,6 +71,9 @@ typedef enum {
  *  visc_model   0: dynamic viscosity linear in phi (eq:dynamic_viscosity),
  *                  tau = mu(phi) / (rho(phi) c_s^2), mu_X = rho_X tau_X c_s^2;
  *               1: relaxation time linear in phi (eq:relaxation_time)
+ *  outlet_scheme the outlet speed U of the convective outlet
+ *               (eq:velocity_options): 0 local u(x, N-1), 1 its maximum, 2 its
+ *               average over the layer N-1
  *  storage      population storage format (arithmetic is float32 always):
  *               0 = float32; 1 = float16 and 2 = bfloat16, both storing
  *               each population normalised by its weight: f as
@@ -88,6 +97,8 @@ typedef struct {
     int32_t bc[6];
     int32_t visc_model;
     int32_t storage;
+    int32_t outlet_scheme;
+    int32_t reserved;       /* 0 */
     double rho_L, rho_H, tau_L, tau_H;
     double sigma, W, mobility;
     double force[3];
@@ -194,6 +205,17 @@ const char* lbm_last_error(const lbm_ctx* ctx);
 
 /* Free all device memory of ctx (after synchronising its stream). */
 int lbm_destroy(lbm_ctx* ctx);
+
+/* Advance only the phase field by nsteps in the prescribed velocity field
+ * scale * u (u: D planes [nz][ny][nx], host or device per on_device): the
+ * conservative Allen-Cahn step of eq:lbe_interface with the forcing term
+ * eq:forcing_term and g^eq = phi Gamma(u), then streaming of g with the face
+ * rules; f is left as it is.  This is the frozen-velocity mode of the
+ * paper's circular interface in a shear flow (Sec. 5.3, eq:velocity_u,
+ * eq:velocity_v).  Faces must be periodic, walls or free slip (LBM_ERR_ARG
+ * otherwise).
+ * With host u the call synchronises the stream. */
+int lbm_advect_phase(lbm_ctx* ctx, const float* u, double scale, int64_t nsteps, int on_device);
 
 /* Test hook: macroscopic update and collision of n independent cells with
  * the device code of the step (Algorithm 1 with eq:mrt_collision in moment

@@ -11,7 +11,8 @@ Field layout: ``[nz][ny][nx]`` with x fastest; the velocity is ``D``
 consecutive planes.  Parameters are a plain dict whose keys mirror the C
 parameter struct (visc_model 0: mu linear in phi, 1: tau linear in phi) (``lattice, nx, ny, nz, bc[6], visc_model, rho_L, rho_H,
 tau_L, tau_H, sigma, W, mobility, force[3], rho_ref, inlet_u,
-inlet_center[2], inlet_radius``).
+inlet_center[2], inlet_radius``, optionally ``outlet_scheme`` 0/1/2 for the
+local / maximum / average outlet speed).
 
 Case recipes follow the paper's validation and application sections and the
 workload sizes used by the benchmark:
@@ -37,7 +38,7 @@ import numpy as np
 SEED = 0x250512205
 
 D2Q9, D3Q19 = 0, 1
-PERIODIC, WALL, INLET, OUTFLOW = 0, 1, 2, 3
+PERIODIC, WALL, INLET, OUTFLOW, FREESLIP = 0, 1, 2, 3, 4
 
 
 def rng(seed_offset: int = 0) -> np.random.Generator:
@@ -302,6 +303,26 @@ def sweep_cases(n=512, L_min=64, L_max=512, seed_offset=4):
         sigma = float(np.exp(r.uniform(np.log(1e-5), np.log(1e-3))))
         out.append(sweep_case(kind, L, rho_ratio, sigma, R=R))
     return out
+
+
+# ------------------------------------------ circular interface in shear flow
+
+def shear_flow_interface(L0=200, U0=0.04, mobility=0.0002, W=3.0, R=None, centre=(100.0, 60.0)):
+    """Circular interface in a reversing shear flow (Sec. 5.3): periodic
+    L0 x L0 box, circle of radius L0/5 centred at (100, 60) (scaled with L0),
+    velocity U(x, y) cos(pi t / (2 T_f)), T_f = L0 / U0, with
+    U = (U0 sin^2(pi x / L0) sin(2 pi y / L0), -U0 sin^2(pi y / L0) sin(2 pi x / L0)).
+    Returns (params, phi0, U planes [2][1][L0][L0], T_f)."""
+    R = L0 / 5.0 if R is None else R
+    cx, cy = centre[0] * L0 / 200.0, centre[1] * L0 / 200.0
+    p = base_params(D2Q9, L0, L0, 1, rho_L=1.0, rho_H=1.0, tau_L=0.5, tau_H=0.5, sigma=0.0, W=W,
+                    mobility=mobility)
+    y, x = np.meshgrid(np.arange(L0, dtype=np.float64), np.arange(L0, dtype=np.float64), indexing="ij")
+    phi = tanh_profile(R - np.sqrt((x - cx) ** 2 + (y - cy) ** 2), W).astype(np.float32)[None]
+    U = np.zeros((2, 1, L0, L0), np.float32)
+    U[0, 0] = U0 * np.sin(np.pi * x / L0) ** 2 * np.sin(2 * np.pi * y / L0)
+    U[1, 0] = -U0 * np.sin(np.pi * y / L0) ** 2 * np.sin(2 * np.pi * x / L0)
+    return p, phi, U, int(round(L0 / U0))
 
 
 # ------------------------------------------------- random states (1 step)

@@ -77,13 +77,13 @@
 #define QMAX 19
 
 enum { ORC_D2Q9 = 0, ORC_D3Q19 = 1 };
-enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTFLOW = 3 };
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTFLOW = 3, BC_FREESLIP = 4 };
 
 typedef struct {
     int32_t lattice, nx, ny, nz;
     int32_t bc[6];           /* faces -x,+x,-y,+y,-z,+z */
     int32_t visc_model;      /* 0: mu linear in phi, 1: tau linear in phi */
-    int32_t reserved;
+    int32_t outlet_scheme;   /* outlet speed U of eq:velocity_options: 0 local, 1 max, 2 average */
     double rho_L, rho_H, tau_L, tau_H;
     double sigma, W, mobility;
     double force[3];         /* body-force acceleration g */
@@ -424,24 +424,38 @@ static void gather_phi(const orc_ctx* c, const double* phi, int x, int y, int z,
     }
 }
 
-/* Classify the pull source of population a at node (x,y,z):
- * returns 0 and the source node, 1 for a wall link (bounce-back), 2 for a
- * link through an open face (unknown, fixed by the inlet/outlet rule). */
-static int pull_source(const orc_ctx* c, int x, int y, int z, int a, int64_t* src)
+/* Classify the pull source of population a at node (x,y,z): returns 0 with
+ * the source node and the source direction *asrc (a, or its mirror image
+ * after a free-slip reflection), 1 for a wall link (bounce-back), 2 for a link
+ * through an open face (unknown, fixed by the inlet/outlet rule).  Free slip
+ * (eq:free_slip_f/g, App. B): a population that crossed slip faces was
+ * reflected specularly there: it left the node x - e_a with the coordinates
+ * of the crossed axes reset to those of x, in the direction whose components
+ * along the crossed axes are reversed. */
+static int pull_source(const orc_ctx* c, int x, int y, int z, int a, int64_t* src, int* asrc)
 {
     int v[3] = {x - c->e[a][0], y - c->e[a][1], z - c->e[a][2]};
-    int wall = 0, open = 0;
+    const int pos[3] = {x, y, z};
+    int wall = 0, open = 0, flip[3] = {0, 0, 0};
     for (int d = 0; d < 3; ++d) {
         if (v[d] >= 0 && v[d] < c->n[d]) continue;
         int face = 2 * d + (v[d] < 0 ? 0 : 1);
         int bc = c->p.bc[face];
         if (bc == BC_PERIODIC) v[d] = (v[d] + c->n[d]) % c->n[d];
         else if (bc == BC_WALL) wall = 1;
+        else if (bc == BC_FREESLIP) { v[d] = pos[d]; flip[d] = 1; }
         else open = 1;
     }
     if (wall) return 1;
     if (open) return 2;
     *src = nid(c, v[0], v[1], v[2]);
+    *asrc = a;
+    if (flip[0] || flip[1] || flip[2]) {
+        int m[3];
+        for (int d = 0; d < 3; ++d) m[d] = flip[d] ? -c->e[a][d] : c->e[a][d];
+        for (int b = 0; b < c->Q; ++b)
+            if (c->e[b][0] == m[0] && c->e[b][1] == m[1] && c->e[b][2] == m[2]) *asrc = b;
+    }
     return 0;
 }
 
@@ -456,15 +470,18 @@ int orc_validate(const orc_params* p)
     if (!(p->W > 0 && p->mobility > 0 && p->sigma >= 0)) return -1;
     if (p->visc_model != 0 && p->visc_model != 1) return -1;
     int D = p->lattice == ORC_D2Q9 ? 2 : 3, L = D - 1;
+    if (p->outlet_scheme < 0 || p->outlet_scheme > 2) return -1;
     for (int d = 0; d < D; ++d) {
         int lo = p->bc[2 * d], hi = p->bc[2 * d + 1];
-        if (lo < 0 || lo > 3 || hi < 0 || hi > 3) return -1;
+        if (lo < 0 || lo > 4 || hi < 0 || hi > 4) return -1;
         if ((lo == BC_PERIODIC) != (hi == BC_PERIODIC)) return -1;
         if (lo == BC_OUTFLOW || hi == BC_INLET) return -1;
-        if (d != L && (lo >= BC_INLET || hi >= BC_INLET)) return -1;
+        int open_lo = lo == BC_INLET || lo == BC_OUTFLOW, open_hi = hi == BC_INLET || hi == BC_OUTFLOW;
+        if (d != L && (open_lo || open_hi)) return -1;
     }
     int n[3] = {p->nx, p->ny, p->nz};
-    if ((p->bc[2 * L] >= BC_INLET || p->bc[2 * L + 1] >= BC_INLET) && n[L] < 4) return -1;
+    int lo = p->bc[2 * L], hi = p->bc[2 * L + 1];
+    if ((lo == BC_INLET || hi == BC_OUTFLOW) && n[L] < 4) return -1;
     return 0;
 }
 
@@ -555,10 +572,11 @@ static void step_once(orc_ctx* c)
         int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
         for (int a = 0; a < Q; ++a) {
             int64_t s;
-            int k = pull_source(c, x, y, z, a, &s);
+            int as;
+            int k = pull_source(c, x, y, z, a, &s, &as);
             if (k == 0) {
-                c->fB[i * Q + a] = c->fs[s * Q + a];
-                c->gB[i * Q + a] = c->gs[s * Q + a];
+                c->fB[i * Q + a] = c->fs[s * Q + as];
+                c->gB[i * Q + a] = c->gs[s * Q + as];
             } else if (k == 1) {
                 c->fB[i * Q + a] = c->fs[i * Q + c->opp[a]];
                 c->gB[i * Q + a] = c->gs[i * Q + c->opp[a]];
@@ -612,9 +630,21 @@ static void step_once(orc_ctx* c)
                 }
             }
     }
-    /* Convective outlet, eq:implicit_convective, Reading R9. */
+    /* Convective outlet, eq:implicit_convective, Reading R9; the outlet
+     * speed U of eq:velocity_options: local (the bare first moment at layer
+     * N-1 after streaming), or its maximum or average over the layer. */
     if (c->p.bc[2 * L + 1] == BC_OUTFLOW) {
         int nL = c->n[L];
+        double Umax = -1e300, Usum = 0.0;
+        for (int t1 = 0; t1 < nt1; ++t1)
+            for (int t0 = 0; t0 < nt0; ++t0) {
+                int64_t iM = (c->D == 2) ? nid(c, t0, nL - 2, 0) : nid(c, t0, t1, nL - 2);
+                double U = 0.0;
+                for (int a = 0; a < Q; ++a) U += c->fB[iM * Q + a] * c->e[a][L];
+                if (U > Umax) Umax = U;
+                Usum += U;
+            }
+        const double Uglob = c->p.outlet_scheme == 1 ? Umax : Usum / ((double)nt0 * nt1);
         for (int t1 = 0; t1 < nt1; ++t1)
             for (int t0 = 0; t0 < nt0; ++t0) {
                 int64_t iN, iM;
@@ -622,6 +652,7 @@ static void step_once(orc_ctx* c)
                 else { iN = nid(c, t0, t1, nL - 1); iM = nid(c, t0, t1, nL - 2); }
                 double U = 0.0;
                 for (int a = 0; a < Q; ++a) U += c->fB[iM * Q + a] * c->e[a][L];
+                if (c->p.outlet_scheme != 0) U = Uglob;
                 double lam = U < 0.0 ? 0.0 : (U > 1.0 ? 1.0 : U);
                 for (int a = 0; a < Q; ++a) {
                     c->fB[iN * Q + a] = (c->fA[iN * Q + a] + lam * c->fB[iM * Q + a]) / (1.0 + lam);
@@ -638,6 +669,61 @@ static void step_once(orc_ctx* c)
 void orc_step(orc_ctx* c, int64_t nsteps)
 {
     for (int64_t s = 0; s < nsteps; ++s) step_once(c);
+}
+
+/* Advection of the phase field alone in a prescribed velocity field (the
+ * circular interface in a shear flow of Sec. 5.3): eq:lbe_interface with the
+ * forcing term eq:forcing_term (Reading R7) and g^eq = phi Gamma(u)
+ * (eq:equilibrium_function) for the velocity u = scale * uf (uf: D planes
+ * [nz][ny][nx], x fastest), then pull streaming of g (eq:streaming_g,
+ * eq:periodic_g, eq:no_slip_g).  f is not changed.  Faces must be periodic
+ * or walls (returns -1 otherwise). */
+int orc_advect(orc_ctx* c, const double* uf, double scale, int64_t nsteps)
+{
+    int Q = c->Q, nx = c->n[0], ny = c->n[1];
+    for (int f = 0; f < 2 * c->D; ++f)
+        if (c->p.bc[f] != BC_PERIODIC && c->p.bc[f] != BC_WALL && c->p.bc[f] != BC_FREESLIP) return -1;
+    const double tau_phi = c->p.mobility / CS2;
+    for (int64_t step = 0; step < nsteps; ++step) {
+        compute_phi(c, c->gA);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < c->N; ++i) {
+            int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+            double phin[QMAX];
+            gather_phi(c, c->phi, x, y, z, phin);
+            const double* g = c->gA + i * Q;
+            double phi = 0.0;
+            for (int a = 0; a < Q; ++a) phi += g[a];
+            double gphi[3] = {0, 0, 0};
+            for (int a = 0; a < Q; ++a)
+                for (int d = 0; d < 3; ++d) gphi[d] += c->w[a] * phin[a] * c->e[a][d] / CS2;   /* eq:gradient_phi */
+            double gn = sqrt(gphi[0] * gphi[0] + gphi[1] * gphi[1] + gphi[2] * gphi[2]);
+            double nrm[3] = {0, 0, 0};
+            if (gn >= 1e-12)
+                for (int d = 0; d < 3; ++d) nrm[d] = gphi[d] / gn;
+            double u[3] = {0, 0, 0};
+            for (int d = 0; d < c->D; ++d) u[d] = scale * uf[(int64_t)d * c->N + i];
+            for (int a = 0; a < Q; ++a) {
+                double en = 0.0;
+                for (int d = 0; d < 3; ++d) en += c->e[a][d] * nrm[d];
+                double Fphi = (1.0 - 4.0 * (phi - 0.5) * (phi - 0.5)) / c->p.W * c->w[a] * en;
+                double gbar = phi * Gamma(c, a, u) - 0.5 * Fphi;
+                c->gs[i * Q + a] = g[a] - (g[a] - gbar) / (tau_phi + 0.5) + Fphi;
+            }
+        }
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < c->N; ++i) {
+            int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+            for (int a = 0; a < Q; ++a) {
+                int64_t src;
+                int as;
+                int k = pull_source(c, x, y, z, a, &src, &as);
+                c->gB[i * Q + a] = k == 0 ? c->gs[src * Q + as] : c->gs[i * Q + c->opp[a]];
+            }
+        }
+        double* t = c->gA; c->gA = c->gB; c->gB = t;
+    }
+    return 0;
 }
 
 /* Macroscopic fields of the current state: phi, u (D planes), p = p* rho c_s^2.

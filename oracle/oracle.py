@@ -55,7 +55,7 @@ class OrcParams(ctypes.Structure):
         ("lattice", ctypes.c_int32), ("nx", ctypes.c_int32),
         ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
         ("bc", ctypes.c_int32 * 6),
-        ("visc_model", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("visc_model", ctypes.c_int32), ("outlet_scheme", ctypes.c_int32),
         ("rho_L", ctypes.c_double), ("rho_H", ctypes.c_double),
         ("tau_L", ctypes.c_double), ("tau_H", ctypes.c_double),
         ("sigma", ctypes.c_double), ("W", ctypes.c_double),
@@ -90,6 +90,8 @@ def lib():
         _lib.orc_matrix.argtypes = [ctypes.c_int, d]
         _lib.orc_collision_matrix.argtypes = [ctypes.c_int, ctypes.c_double, d]
         _lib.orc_collide_node.argtypes = [ctypes.c_void_p, d, d, d, d, d, d, d]
+        _lib.orc_advect.argtypes = [ctypes.c_void_p, d, ctypes.c_double, ctypes.c_int64]
+        _lib.orc_advect.restype = ctypes.c_int
     return _lib
 
 
@@ -133,6 +135,7 @@ def make_params(p: dict) -> OrcParams:
     for i, b in enumerate(p.get("bc", [PERIODIC] * 6)):
         s.bc[i] = int(b)
     s.visc_model = int(p.get("visc_model", 0))
+    s.outlet_scheme = int(p.get("outlet_scheme", 0))
     s.rho_L, s.rho_H = float(p["rho_L"]), float(p["rho_H"])
     s.tau_L, s.tau_H = float(p["tau_L"]), float(p["tau_H"])
     s.sigma, s.W, s.mobility = float(p["sigma"]), float(p["W"]), float(p["mobility"])
@@ -207,6 +210,13 @@ class Oracle:
         g = np.ascontiguousarray(g, np.float64).reshape(-1)
         assert f.size == self.Q * self.N and g.size == self.Q * self.N
         lib().orc_set_pops(self._h, _dp(f), _dp(g))
+
+    def advect(self, u, scale=1.0, nsteps=1):
+        """Advance only the phase field for nsteps in the velocity scale * u
+        (u: D planes [nz][ny][nx]); see orc_advect."""
+        ua = np.ascontiguousarray(u, np.float64).reshape(-1)
+        if lib().orc_advect(self._h, _dp(ua), float(scale), int(nsteps)) != 0:
+            raise ValueError("advection needs periodic or wall faces")
 
     def collide_node(self, f, g, phin):
         f = np.ascontiguousarray(f, np.float64)

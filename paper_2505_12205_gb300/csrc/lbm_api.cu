@@ -57,6 +57,7 @@ struct lbm_ctx {
     DiagPartial* diag_res = nullptr;
     int diag_nparts = 0;
     float* staging = nullptr;       // float32 population-major planes for checkpoints
+    float* uadv = nullptr;          // prescribed velocity of lbm_advect_phase (host input copied here)
     size_t elem = 4;                // bytes per stored population value
     bool initialised = false;
     // kernel timing: 4 events per recorded step (before phi, after phi,
@@ -106,16 +107,18 @@ static int validate(const lbm_params* p, std::string& why)
     if (p->visc_model != 0 && p->visc_model != 1) { why = "visc_model must be 0 or 1"; return -1; }
     if (p->storage < 0 || p->storage > 2) { why = "storage must be 0 (float32), 1 (float16) or 2 (bfloat16)"; return -1; }
     if (!(p->storage_scale >= 0)) { why = "storage_scale must be >= 0"; return -1; }
+    if (p->outlet_scheme < 0 || p->outlet_scheme > 2) { why = "outlet_scheme must be 0, 1 or 2"; return -1; }
     const int D = p->lattice == LBM_D2Q9 ? 2 : 3, L = D - 1;
     const int n[3] = {p->nx, p->ny, p->nz};
+    auto open_face = [](int b) { return b == LBM_BC_INLET || b == LBM_BC_OUTFLOW; };
     for (int d = 0; d < D; ++d) {
         const int lo = p->bc[2 * d], hi = p->bc[2 * d + 1];
-        if (lo < 0 || lo > 3 || hi < 0 || hi > 3) { why = "face condition out of range"; return -1; }
+        if (lo < 0 || lo > 4 || hi < 0 || hi > 4) { why = "face condition out of range"; return -1; }
         if ((lo == LBM_BC_PERIODIC) != (hi == LBM_BC_PERIODIC)) { why = "periodic faces must be paired"; return -1; }
         if (lo == LBM_BC_OUTFLOW || hi == LBM_BC_INLET) { why = "inlet only on a low face, outlet only on a high face"; return -1; }
-        if (d != L && (lo >= LBM_BC_INLET || hi >= LBM_BC_INLET)) { why = "inlet/outlet only on the last axis"; return -1; }
+        if (d != L && (open_face(lo) || open_face(hi))) { why = "inlet/outlet only on the last axis"; return -1; }
     }
-    if ((p->bc[2 * L] >= LBM_BC_INLET || p->bc[2 * L + 1] >= LBM_BC_INLET) && n[L] < 4) {
+    if ((p->bc[2 * L] == LBM_BC_INLET || p->bc[2 * L + 1] == LBM_BC_OUTFLOW) && n[L] < 4) {
         why = "open faces need at least 4 nodes along the last axis";
         return -1;
     }
@@ -133,6 +136,10 @@ static DevParams make_dev(const lbm_params* p, int64_t N)
     for (int i = 0; i < 6; ++i) d.bc[i] = p->bc[i];
     if (p->lattice == LBM_D2Q9) d.bc[4] = d.bc[5] = LBM_BC_PERIODIC;
     d.visc_model = p->visc_model;
+    d.outlet_scheme = p->outlet_scheme;
+    d.has_slip = 0;
+    for (int f = 0; f < (p->lattice == LBM_D2Q9 ? 4 : 6); ++f)
+        if (p->bc[f] == LBM_BC_FREESLIP) d.has_slip = 1;
     d.N = N;
     d.rho_L = float(p->rho_L); d.rho_H = float(p->rho_H);
     d.tau_L = float(p->tau_L); d.tau_H = float(p->tau_H);
@@ -230,7 +237,7 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
     }
     e = cudaMalloc(reinterpret_cast<void**>(&c->b.phi), size_t(c->N) * sizeof(float));
     const int nface = c->D == 2 ? p->nx : p->nx * p->ny;
-    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&c->face), 2 * size_t(nface) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&c->face), (2 * size_t(nface) + 1) * sizeof(float));
     c->diag_nparts = 2 * 152;
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&c->diag_part), (c->diag_nparts + 1) * sizeof(DiagPartial));
     if (e != cudaSuccess) {
@@ -247,6 +254,7 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
     }
     c->dp.phi_in = c->face;
     c->dp.u_in = c->face + nface;
+    c->dp.lam = c->face + 2 * nface;
     const int L = c->D - 1;
     if (p->bc[2 * L] == LBM_BC_INLET) {
         e = c->D == 2 ? Launch<D2Q9, StoreF32>::inlet_profile(c->dp, p->inlet_center[0], 0.0, p->inlet_radius,
@@ -271,7 +279,7 @@ int lbm_destroy(lbm_ctx* c)
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     cudaFree(c->b.fA); cudaFree(c->b.gA); cudaFree(c->b.fB); cudaFree(c->b.gB);
-    cudaFree(c->b.phi); cudaFree(c->face); cudaFree(c->diag_part); cudaFree(c->staging);
+    cudaFree(c->b.phi); cudaFree(c->face); cudaFree(c->diag_part); cudaFree(c->staging); cudaFree(c->uadv);
     delete c;
     return LBM_OK;
 }
@@ -447,6 +455,31 @@ int lbm_diag(lbm_ctx* c, double phase_eps, lbm_diag_out* out)
     out->finite = r.nonfinite ? 0 : 1;
     out->reserved = 0;
     if (r.nonfinite) return fail(c, LBM_ERR_DIVERGED, "non-finite populations");
+    return LBM_OK;
+}
+
+int lbm_advect_phase(lbm_ctx* c, const float* u, double scale, int64_t nsteps, int on_device)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (!u || nsteps < 0) return fail(c, LBM_ERR_ARG, "advect_phase: u is NULL or nsteps < 0");
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "advect_phase before lbm_init_fields/lbm_set_populations");
+    for (int f = 0; f < 2 * c->D; ++f)
+        if (c->p.bc[f] != LBM_BC_PERIODIC && c->p.bc[f] != LBM_BC_WALL && c->p.bc[f] != LBM_BC_FREESLIP)
+            return fail(c, LBM_ERR_ARG, "advect_phase: faces must be periodic, walls or free slip");
+    const float* ud = u;
+    if (!on_device) {
+        if (!c->uadv) LBM_CUDA(c, cudaMalloc(reinterpret_cast<void**>(&c->uadv), size_t(c->N) * c->D * sizeof(float)));
+        LBM_CUDA(c, cudaMemcpyAsync(c->uadv, u, size_t(c->N) * c->D * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        ud = c->uadv;
+    }
+    for (int64_t s = 0; s < nsteps; ++s) {
+        cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+            return decltype(l)::advect(c->dp, c->b, ud, float(scale), c->stream);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e, "advect kernels");
+        std::swap(c->b.gA, c->b.gB);
+    }
+    if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
 

@@ -24,7 +24,7 @@
 
 namespace lbm {
 
-enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTFLOW = 3 };
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_INLET = 2, BC_OUTFLOW = 3, BC_FREESLIP = 4 };
 
 // Parameters as the kernels use them (float32 arithmetic), passed by value.
 struct DevParams {
@@ -32,6 +32,8 @@ struct DevParams {
     int nxp;               // nx rounded up to a multiple of 32 (row pitch of the state)
     int bc[6];
     int visc_model;
+    int has_slip;          // some face is free slip
+    int outlet_scheme;     // 0 local, 1 maximum, 2 average outlet speed (eq:velocity_options)
     int64_t N;             // nodes
     int64_t Np;            // nodes with the padded rows, nxp * ny * nz
     float rho_L, rho_H, tau_L, tau_H, mu_L, mu_H;
@@ -43,6 +45,7 @@ struct DevParams {
     // inlet plane profile (face arrays, precomputed in double on the device)
     const float* phi_in;
     const float* u_in;
+    float* lam;            // outlet: lambda of the maximum / average schemes (one value)
 };
 
 // ------------------------------------------------------------------ layout
@@ -173,6 +176,33 @@ __host__ __device__ constexpr uint32_t dirmask(int d, int sign)
         if (e == sign) m |= 1u << a;
     }
     return m;
+}
+
+// Index of the direction (ex, ey, ez) (-1 if none).
+template <class L>
+__host__ __device__ constexpr int dir_index(int ex, int ey, int ez)
+{
+    for (int a = 0; a < L::Q; ++a)
+        if (L::ex(a) == ex && L::ey(a) == ey && L::ez(a) == ez) return a;
+    return -1;
+}
+
+// Direction a with the components of the axes in mask m (bit d: axis d)
+// reversed: the specular image of a after free-slip reflections.
+template <class L>
+__device__ __forceinline__ int mirrored(int a, int m)
+{
+    const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
+    switch (m & 7) {
+    case 1: return dir_index<L>(-ex, ey, ez);
+    case 2: return dir_index<L>(ex, -ey, ez);
+    case 3: return dir_index<L>(-ex, -ey, ez);
+    case 4: return dir_index<L>(ex, ey, -ez);
+    case 5: return dir_index<L>(-ex, ey, -ez);
+    case 6: return dir_index<L>(ex, -ey, -ez);
+    case 7: return dir_index<L>(-ex, -ey, -ez);
+    default: return a;
+    }
 }
 
 template <class L>
@@ -644,7 +674,7 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
             // so its offset is the node step times Q), and the directions
             // whose target lies behind a wall (bounced back into the opposite
             // slot of this node) or beyond an open face (they leave the domain)
-            uint32_t wallm = 0, openm = 0;
+            uint32_t wallm = 0, openm = 0, slipm[3] = {0u, 0u, 0u};
             uint32_t o[3][2];
             {
                 const int pos[3] = {x, yc, z};
@@ -657,11 +687,13 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
                     if (pos[d] == 0) {
                         if (lo == BC_PERIODIC) sm = len[d] - 1;
                         else if (lo == BC_WALL) wallm |= dirmask<L>(d, -1);
+                        else if (lo == BC_FREESLIP) slipm[d] |= dirmask<L>(d, -1);
                         else openm |= dirmask<L>(d, -1);
                     }
                     if (pos[d] == len[d] - 1) {
                         if (hi == BC_PERIODIC) sp = -(len[d] - 1);
                         else if (hi == BC_WALL) wallm |= dirmask<L>(d, 1);
+                        else if (hi == BC_FREESLIP) slipm[d] |= dirmask<L>(d, 1);
                         else openm |= dirmask<L>(d, 1);
                     }
                     if (d == 0) {       // within a row: the block and lane of the target
@@ -673,7 +705,7 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
                     }
                 }
             }
-            const uint32_t offm = wallm | openm;
+            const uint32_t offm = wallm | openm | slipm[0] | slipm[1] | slipm[2];
             auto emit = [&](int a, float fs, float gs) {
                 const float wa = L::w(a);           // w of a and of its opposite
                 const uint32_t bit = 1u << a;
@@ -687,6 +719,18 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
                 } else if (wallm & bit) {           // wall: back to this node, opposite slot
                     (fB + e0)[32 * L::opp(a)] = S::ef(fs, wa, P);
                     (gB + e0)[32 * L::opp(a)] = S::eg(gs, wa);
+                } else if (P.has_slip && !(openm & bit)) {
+                    // free slip (eq:free_slip_f/g): reflected over the crossed slip
+                    // faces, to the tangential neighbour, components reversed
+                    const int m = int((slipm[0] >> a) & 1u) | int((slipm[1] >> a) & 1u) << 1 |
+                                  int((slipm[2] >> a) & 1u) << 2;
+                    uint32_t t = e0;
+                    if (L::ex(a) && !(m & 1)) t += o[0][L::ex(a) > 0];
+                    if (L::ey(a) && !(m & 2)) t += o[1][L::ey(a) > 0];
+                    if (L::D == 3 && L::ez(a) && !(m & 4)) t += o[2][L::ez(a) > 0];
+                    const int am = mirrored<L>(a, m);
+                    (fB + t)[32 * am] = S::ef(fs, wa, P);
+                    (gB + t)[32 * am] = S::eg(gs, wa);
                 }                                   // open face: leaves the domain
             };
             node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, emit);
@@ -826,6 +870,38 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __re
     }
 }
 
+// Outlet speed of the maximum / average schemes of eq:velocity_options: the
+// bare first moment of f along the outward normal at layer N-1 after
+// streaming, reduced over the layer into *P.lam (one block).
+template <class L, class S>
+__global__ void __launch_bounds__(256) k_outlet_speed(const __grid_constant__ DevParams P, const typename S::T* __restrict__ fB)
+{
+    __shared__ float red[256];
+    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
+    const int nL = (L::D == 2) ? P.ny : P.nz;
+    float acc = P.outlet_scheme == 1 ? -3.0e38f : 0.0f;
+    for (int t = threadIdx.x; t < nface; t += blockDim.x) {
+        const int tx = (L::D == 2) ? t : t % P.nx, ty = (L::D == 2) ? 0 : t / P.nx;
+        const uint32_t iM = (L::D == 2) ? pel<L>(pnode(P, tx, nL - 2, 0)) : pel<L>(pnode(P, tx, ty, nL - 2));
+        float U = 0.0f;
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) {
+            const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
+            if (en) U += float(en) * S::f(fB[iM + 32 * a], L::w(a), P);
+        }
+        acc = P.outlet_scheme == 1 ? fmaxf(acc, U) : acc + U;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            red[threadIdx.x] = P.outlet_scheme == 1 ? fmaxf(red[threadIdx.x], red[threadIdx.x + h])
+                                                    : red[threadIdx.x] + red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *P.lam = P.outlet_scheme == 1 ? red[0] : red[0] / float(nface);
+}
+
 // Convective outlet on the high face of the last axis (eq:implicit_convective,
 // eq:convective_f/g): chi(N, t+1) = (chi(N, t) + lambda chi(N-1, t+1)) / (1 + lambda),
 // lambda = clamp(sum_a f_a e_a.n at layer N-1 after streaming, 0, 1).
@@ -848,7 +924,7 @@ __global__ void k_outlet(const __grid_constant__ DevParams P, const typename S::
         const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
         if (en) U += float(en) * S::f(fB[iM + 32 * a], L::w(a), P);
     }
-    const float lam = fminf(fmaxf(U, 0.0f), 1.0f);
+    const float lam = fminf(fmaxf(P.outlet_scheme ? *P.lam : U, 0.0f), 1.0f);
     const float inv = 1.0f / (1.0f + lam);
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
@@ -933,6 +1009,76 @@ __global__ void __launch_bounds__(128) k_fields(const __grid_constant__ DevParam
         if (L::D == 3) ou[2 * N + node] = out[3];
     }
     if (op) op[node] = out[4];
+}
+
+// Advection of the phase field alone in a prescribed velocity field
+// scale * uf (uf: D planes of the external node order): phi stencil from the
+// phi array (k_phi), the g collision of eq:lbe_interface with the forcing
+// term eq:forcing_term (n = 0 where |grad phi| < 1e-12) and g^eq = phi
+// Gamma(u), then push streaming of g into gB (periodic wrap, bounce-back at
+// walls).  f is not touched.  One thread per node (a test path, not tuned).
+template <class L, class S>
+__global__ void __launch_bounds__(128) k_advect(const __grid_constant__ DevParams P, const float* __restrict__ phi,
+                                                const float* __restrict__ uf, float scale,
+                                                const typename S::T* __restrict__ gA, typename S::T* __restrict__ gB)
+{
+    constexpr int Q = L::Q;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
+    float phin[Q];
+    gather_phi<L>(P, phi, x, y, z, phin);
+    const uint32_t e0 = pel<L>(pnode(P, x, y, z));
+    float g[Q], ph = 0.0f;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        g[a] = S::g(gA[e0 + 32 * a], L::w(a));
+        ph += g[a];
+    }
+    float dx = 0.0f, dy = 0.0f, dz = 0.0f;
+#pragma unroll
+    for (int a = 1; a < Q; ++a) {
+        const float wp = 3.0f * L::w(a) * phin[a];
+        dx += float(L::ex(a)) * wp;
+        dy += float(L::ey(a)) * wp;
+        dz += float(L::ez(a)) * wp;
+    }
+    const float gn2 = dx * dx + dy * dy + dz * dz;
+    const float amp = (gn2 >= 1e-24f) ? (1.0f - 4.0f * (ph - 0.5f) * (ph - 0.5f)) * P.inv_W * rsqrtf(gn2) : 0.0f;
+    const float ux = scale * uf[i], uy = scale * uf[P.N + i], uz = (L::D == 3) ? scale * uf[2 * P.N + i] : 0.0f;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    const float om = P.omega_phi;
+    float sg = 0.0f, gs[Q];
+#pragma unroll
+    for (int a = 1; a < Q; ++a) {
+        const float en = amp * (float(L::ex(a)) * dx + float(L::ey(a)) * dy + float(L::ez(a)) * dz);
+        const float Fphi = L::w(a) * en;
+        const float geq = ph * (L::w(a) + gdev<L>(a, ux, uy, uz, uu));
+        sg += geq;
+        gs[a] = g[a] - om * (g[a] - geq + 0.5f * Fphi) + Fphi;
+    }
+    gs[0] = g[0] - om * (g[0] - (ph - sg));
+    // push streaming of g
+    const int pos[3] = {x, y, z};
+    const int len[3] = {P.nx, P.ny, P.nz};
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const int e[3] = {L::ex(a), L::ey(a), L::ez(a)};
+        int t[3], m = 0;
+        bool wall = false;
+        for (int d = 0; d < 3; ++d) {
+            t[d] = pos[d] + e[d];
+            if (t[d] < 0 || t[d] >= len[d]) {
+                const int bc = P.bc[2 * d + (t[d] < 0 ? 0 : 1)];
+                if (bc == BC_PERIODIC) t[d] = (t[d] + len[d]) % len[d];
+                else if (bc == BC_FREESLIP) { t[d] = pos[d]; m |= 1 << d; }
+                else wall = true;
+            }
+        }
+        const float wa = L::w(a);
+        if (wall) gB[e0 + 32 * L::opp(a)] = S::eg(gs[a], wa);
+        else gB[pel<L>(pnode(P, t[0], t[1], t[2])) + 32 * mirrored<L>(a, m)] = S::eg(gs[a], wa);
+    }
 }
 
 // Per-block FP64 partial reductions for lbm_diag.
@@ -1077,6 +1223,8 @@ struct Launch {
                                      float* phi_in, float* u_in, cudaStream_t s);
     static cudaError_t collide_cells(const DevParams& P, int64_t n, const float* f, const float* g,
                                      const float* phin, float* fs, float* gs, float* out, cudaStream_t s);
+    // one step of the phase field alone in the velocity scale * uf (g: A -> B)
+    static cudaError_t advect(const DevParams& P, const Buffers& b, const float* uf, float scale, cudaStream_t s);
 };
 
 // Tile shapes: 32 x 8 columns in 3D, 128 nodes of a row in 2D.
@@ -1149,7 +1297,10 @@ cudaError_t Launch<L, S>::step_timed(const DevParams& P, const FusedGeom& G, int
     const int lasthi = (L::D == 2) ? P.bc[3] : P.bc[5];
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
     if (lastlo == BC_INLET) k_inlet<L, S><<<(nface + 127) / 128, 128, 0, s>>>(P, fB, gB);
-    if (lasthi == BC_OUTFLOW) k_outlet<L, S><<<(nface + 127) / 128, 128, 0, s>>>(P, fA, gA, fB, gB);
+    if (lasthi == BC_OUTFLOW) {
+        if (P.outlet_scheme) k_outlet_speed<L, S><<<1, 256, 0, s>>>(P, fB);
+        k_outlet<L, S><<<(nface + 127) / 128, 128, 0, s>>>(P, fA, gA, fB, gB);
+    }
     if ((e = mark()) != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -1252,6 +1403,15 @@ cudaError_t Launch<L, S>::inlet_profile(const DevParams& P, double cx, double cy
 {
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
     k_inlet_profile<L><<<(nface + 127) / 128, 128, 0, s>>>(nface, P.nx, cx, cy, R, W, uj, phi_in, u_in);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::advect(const DevParams& P, const Buffers& b, const float* uf, float scale, cudaStream_t s)
+{
+    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, static_cast<const T*>(b.gA), b.phi);
+    k_advect<L, S><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, b.phi, uf, scale, static_cast<const T*>(b.gA),
+                                                               static_cast<T*>(b.gB));
     return cudaGetLastError();
 }
 

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
 
 LBM_D2Q9, LBM_D3Q19 = 0, 1
-LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_INLET, LBM_BC_OUTFLOW = 0, 1, 2, 3
+LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_INLET, LBM_BC_OUTFLOW, LBM_BC_FREESLIP = 0, 1, 2, 3, 4
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6
 
@@ -27,7 +27,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOU
 EXPORTS = ["lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_fields", "lbm_get_populations",
            "lbm_set_populations", "lbm_diag", "lbm_sync", "lbm_shape", "lbm_last_error",
            "lbm_destroy", "lbm_collide_cells", "lbm_set_timing", "lbm_get_timing",
-           "lbm_diag_noalloc", "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step",
+           "lbm_diag_noalloc", "lbm_advect_phase", "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step",
            "lbm_batch_get_fields", "lbm_batch_diag", "lbm_batch_get_plan", "lbm_batch_set_plan",
            "lbm_batch_tune", "lbm_batch_sync", "lbm_batch_last_error", "lbm_batch_destroy"]
 
@@ -40,6 +40,7 @@ class LbmParams(ctypes.Structure):
         ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
         ("bc", ctypes.c_int32 * 6),
         ("visc_model", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("outlet_scheme", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("rho_L", ctypes.c_double), ("rho_H", ctypes.c_double),
         ("tau_L", ctypes.c_double), ("tau_H", ctypes.c_double),
         ("sigma", ctypes.c_double), ("W", ctypes.c_double),
@@ -107,6 +108,7 @@ def load(path: str = LIB_PATH):
     lib.lbm_collide_cells.argtypes = [P, i64, f32p, f32p, f32p, f32p, f32p, f32p, vp]
     lib.lbm_diag_noalloc.argtypes = [P, f32p, f32p, ctypes.c_double, ctypes.POINTER(LbmDiagOut), vp]
     lib.lbm_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.lbm_advect_phase.argtypes = [vp, f32p, ctypes.c_double, i64, ctypes.c_int]
     lib.lbm_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     BP = ctypes.POINTER(LbmBatchPlan)
     lib.lbm_batch_create.argtypes = [P, ctypes.c_int32, vp, ctypes.POINTER(vp)]
@@ -135,6 +137,7 @@ def make_params(p: dict) -> LbmParams:
         s.bc[i] = int(b)
     s.visc_model = int(p.get("visc_model", 0))
     s.storage = int(p.get("storage", 0))
+    s.outlet_scheme = int(p.get("outlet_scheme", 0))
     s.rho_L, s.rho_H = float(p["rho_L"]), float(p["rho_H"])
     s.tau_L, s.tau_H = float(p["tau_L"]), float(p["tau_H"])
     s.sigma, s.W, s.mobility = float(p["sigma"]), float(p["W"]), float(p["mobility"])
@@ -261,6 +264,12 @@ def lbm_destroy(ctx):
     _check(lib, lib.lbm_destroy(ctx))
 
 
+def lbm_advect_phase(ctx, u, scale: float = 1.0, nsteps: int = 1):
+    lib = load()
+    a, k = _ptr(u)
+    _check(lib, lib.lbm_advect_phase(ctx, a, float(scale), int(nsteps), k), ctx)
+
+
 def lbm_set_timing(ctx, enable: bool):
     lib = load()
     _check(lib, lib.lbm_set_timing(ctx, 1 if enable else 0), ctx)
@@ -366,6 +375,12 @@ class LBM:
 
     def diag(self, phase_eps: float = 1e-3) -> dict:
         return lbm_diag(self._h, phase_eps)
+
+    def advect(self, u, scale: float = 1.0, nsteps: int = 1):
+        """Advance only the phase field in the velocity scale * u (see lbm_advect_phase)."""
+        if not _is_torch(u):
+            u = np.ascontiguousarray(u, np.float32)
+        lbm_advect_phase(self._h, u, scale, nsteps)
 
     def set_timing(self, enable: bool = True):
         lbm_set_timing(self._h, enable)

@@ -37,9 +37,9 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_params_struct_layout(lib):
-    # natural alignment of the C struct: 12 int32 then 16 doubles
-    assert ctypes.sizeof(lib.LbmParams) == 12 * 4 + 16 * 8
-    assert lib.LbmParams.rho_L.offset == 48
+    # natural alignment of the C struct: 14 int32 then 16 doubles
+    assert ctypes.sizeof(lib.LbmParams) == 14 * 4 + 16 * 8
+    assert lib.LbmParams.rho_L.offset == 56
     assert ctypes.sizeof(lib.LbmDiagOut) == 4 * 8 + 2 * 8 + 2 * 4
 
 

@@ -250,3 +250,53 @@ def test_inlet_moments_exact(oracle_mod, lat, shape):
         assert np.abs(mom[L] - u_in).max() < 1e-14
         for d in range(L):
             assert np.abs(mom[d]).max() < 1e-14
+
+
+@pytest.mark.slow
+def test_shear_flow_interface_returns_and_conserves_mass(oracle_mod, report):
+    """Circular interface in a reversing shear flow (Sec. 5.3), phase field
+    alone in the prescribed velocity, L0 = 100: sum phi is conserved to
+    round-off and the interface returns close to its start.  (The paper
+    prints a relative error of 8.58e-3 at L0 = 200; the readings of its time
+    factor give 1.4e-2 to 4.4e-2 there, see the design notes.)"""
+    import lbm_cases as C
+    p, phi0, U, Tf = C.shear_flow_interface(L0=100)
+    o = oracle_mod.Oracle(p)
+    o.init_fields(phi0, None, None)
+    T = 2 * Tf
+    for t in range(T):
+        o.advect(U, np.cos(np.pi * t / T), 1)
+    phi = o.fields()[0].astype(np.float64)
+    p0 = phi0.astype(np.float64)
+    err = np.sqrt(((phi - p0) ** 2).sum() / (p0 ** 2).sum())
+    mass = phi.sum() / p0.sum() - 1.0
+    report("oracle_shear_flow_L100", err=err, mass=mass)
+    assert abs(mass) < 1e-10
+    assert err < 0.08
+    # half way the interface is strongly deformed: far from the start
+    o2 = oracle_mod.Oracle(p)
+    o2.init_fields(phi0, None, None)
+    for t in range(Tf):
+        o2.advect(U, np.cos(np.pi * t / T), 1)
+    mid = o2.fields()[0].astype(np.float64)
+    assert np.sqrt(((mid - p0) ** 2).sum() / (p0 ** 2).sum()) > 0.5
+
+
+@pytest.mark.parametrize("lat,shape,u", [(0, (1, 12, 9), (0.0, 0.03, 0.0)), (1, (7, 6, 5), (0.0, 0.02, 0.01))])
+def test_free_slip_keeps_a_tangential_uniform_flow(oracle_mod, lat, shape, u):
+    """Free slip (eq:free_slip_f/g) reflects specularly: a uniform flow along
+    slip faces is a fixed point, while the same flow along no-slip walls is
+    slowed at the walls."""
+    p, phi, uu, ps = C.uniform_flow(lattice=lat, shape=shape, u=u)
+    p["bc"] = [4, 4, 0, 0, 0, 0]
+    o = oracle_mod.Oracle(p)
+    o.init_fields(phi, uu, ps)
+    o.step(50)
+    ph, uo, _ = o.fields()
+    assert np.abs(ph - phi).max() == 0.0
+    assert np.abs(uo - uu).max() < 1e-14
+    p["bc"] = [1, 1, 0, 0, 0, 0]
+    o = oracle_mod.Oracle(p)
+    o.init_fields(phi, uu, ps)
+    o.step(50)
+    assert np.abs(o.fields()[1] - uu).max() > 1e-3
