@@ -217,6 +217,28 @@ int lbm_destroy(lbm_ctx* ctx);
  * With host u the call synchronises the stream. */
 int lbm_advect_phase(lbm_ctx* ctx, const float* u, double scale, int64_t nsteps, int on_device);
 
+/* Jet post-processing (Sec. 6: breakup length L_b and drop size d_e): the
+ * liquid phi > threshold of the current state is split into connected
+ * components (face neighbours, wrapped across periodic faces).  The largest
+ * component touching the first plane of the last axis (the inlet side) is
+ * the intact jet, and breakup_length is its extent along that axis (cells
+ * from the plane to its farthest node, inclusive); every other component is
+ * a drop, with equivalent diameter 2 sqrt(A / pi) (2D) or (6 V / pi)^(1/3)
+ * (3D) from its cell count.  Up to max_drops drop volumes (cells, in no
+ * particular order) are written to drop_volumes (may be NULL).  Allocates
+ * 16 bytes per node of scratch on the first call; synchronises the stream. */
+typedef struct {
+    int32_t n_components;        /* liquid components */
+    int32_t has_jet;             /* 1 if a component touches the first plane */
+    double breakup_length;       /* cells; 0 without a jet */
+    int32_t n_drops;             /* components other than the jet */
+    int32_t truncated;           /* 1 if more drops than max_drops were found */
+    double mean_drop_diameter;   /* cells; 0 without drops */
+    double drop_volume;          /* total cells of the drops */
+} lbm_jet_stats_out;
+
+int lbm_jet_stats(lbm_ctx* ctx, double threshold, int32_t max_drops, double* drop_volumes, lbm_jet_stats_out* out);
+
 /* Test hook: macroscopic update and collision of n independent cells with
  * the device code of the step (Algorithm 1 with eq:mrt_collision in moment
  * space).  Device pointers: f, g [n][Q] post-stream populations; phin

@@ -58,6 +58,8 @@ struct lbm_ctx {
     int diag_nparts = 0;
     float* staging = nullptr;       // float32 population-major planes for checkpoints
     float* uadv = nullptr;          // prescribed velocity of lbm_advect_phase (host input copied here)
+    int* ccl = nullptr;             // jet post-processing scratch: labels, sizes, lo, hi (4 N ints)
+    int* ccl_list = nullptr;        // (size, lo, hi) of the components, count at the end
     size_t elem = 4;                // bytes per stored population value
     bool initialised = false;
     // kernel timing: 4 events per recorded step (before phi, after phi,
@@ -280,6 +282,7 @@ int lbm_destroy(lbm_ctx* c)
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     cudaFree(c->b.fA); cudaFree(c->b.gA); cudaFree(c->b.fB); cudaFree(c->b.gB);
     cudaFree(c->b.phi); cudaFree(c->face); cudaFree(c->diag_part); cudaFree(c->staging); cudaFree(c->uadv);
+    cudaFree(c->ccl); cudaFree(c->ccl_list);
     delete c;
     return LBM_OK;
 }
@@ -480,6 +483,79 @@ int lbm_advect_phase(lbm_ctx* c, const float* u, double scale, int64_t nsteps, i
         std::swap(c->b.gA, c->b.gB);
     }
     if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_jet_stats(lbm_ctx* c, double threshold, int32_t max_drops, double* drop_volumes, lbm_jet_stats_out* out)
+{
+    if (!c || !out || max_drops < 0) return LBM_ERR_ARG;
+    if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
+    const int64_t N = c->N;
+    if (N > int64_t(INT32_MAX) / 4) return fail(c, LBM_ERR_ARG, "jet_stats: grid too large for its labels");
+    constexpr int kCap = 1 << 20;                       // components listed
+    if (!c->ccl) LBM_CUDA(c, cudaMalloc(reinterpret_cast<void**>(&c->ccl), 4 * size_t(N) * sizeof(int)));
+    if (!c->ccl_list) LBM_CUDA(c, cudaMalloc(reinterpret_cast<void**>(&c->ccl_list), (3 * size_t(kCap) + 2) * sizeof(int)));
+    int* lab = c->ccl;
+    int* size = lab + N;
+    int* lo = size + N;
+    int* hi = lo + N;
+    int* list = c->ccl_list;
+    int* count = list + 3 * kCap;
+    int* changed = count + 1;
+    const unsigned nb = unsigned((N + 255) / 256);
+    cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+        using Ln = decltype(l);
+        return Ln::phi(c->dp, c->b, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "phi kernel");
+    if (c->D == 2) lbm::k_ccl_init<D2Q9><<<nb, 256, 0, c->stream>>>(c->dp, c->b.phi, float(threshold), lab);
+    else lbm::k_ccl_init<D3Q19><<<nb, 256, 0, c->stream>>>(c->dp, c->b.phi, float(threshold), lab);
+    int rounds = 0;
+    for (;; ++rounds) {
+        if (rounds >= 100000) return fail(c, LBM_ERR_TIMEOUT, "jet_stats: labels did not converge");
+        LBM_CUDA(c, cudaMemsetAsync(changed, 0, sizeof(int), c->stream));
+        if (c->D == 2) lbm::k_ccl_hook<D2Q9><<<nb, 256, 0, c->stream>>>(c->dp, lab, changed);
+        else lbm::k_ccl_hook<D3Q19><<<nb, 256, 0, c->stream>>>(c->dp, lab, changed);
+        lbm::k_ccl_jump<D2Q9><<<nb, 256, 0, c->stream>>>(N, lab);
+        int h = 0;
+        LBM_CUDA(c, cudaMemcpyAsync(&h, changed, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+        if (!h) break;
+    }
+    LBM_CUDA(c, cudaMemsetAsync(size, 0, size_t(N) * sizeof(int), c->stream));
+    LBM_CUDA(c, cudaMemsetAsync(lo, 0x7f, size_t(N) * sizeof(int), c->stream));
+    LBM_CUDA(c, cudaMemsetAsync(hi, 0xff, size_t(N) * sizeof(int), c->stream));
+    LBM_CUDA(c, cudaMemsetAsync(count, 0, sizeof(int), c->stream));
+    if (c->D == 2) lbm::k_ccl_stats<D2Q9><<<nb, 256, 0, c->stream>>>(c->dp, lab, size, lo, hi);
+    else lbm::k_ccl_stats<D3Q19><<<nb, 256, 0, c->stream>>>(c->dp, lab, size, lo, hi);
+    lbm::k_ccl_list<D2Q9><<<nb, 256, 0, c->stream>>>(N, lab, size, lo, hi, kCap, count, list);
+    LBM_CUDA(c, cudaGetLastError());
+    int ncomp = 0;
+    LBM_CUDA(c, cudaMemcpyAsync(&ncomp, count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int nlist = ncomp < kCap ? ncomp : kCap;
+    std::vector<int> h(3 * size_t(nlist));
+    if (nlist) LBM_CUDA(c, cudaMemcpy(h.data(), list, h.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    int jet = -1;
+    for (int k = 0; k < nlist; ++k)
+        if (h[3 * k + 1] == 0 && (jet < 0 || h[3 * k] > h[3 * jet])) jet = k;
+    out->n_components = ncomp;
+    out->has_jet = jet >= 0 ? 1 : 0;
+    out->breakup_length = jet >= 0 ? double(h[3 * jet + 2] + 1) : 0.0;
+    int nd = 0;
+    double dsum = 0.0, vsum = 0.0;
+    for (int k = 0; k < nlist; ++k) {
+        if (k == jet) continue;
+        const double v = h[3 * k];
+        if (drop_volumes && nd < max_drops) drop_volumes[nd] = v;
+        ++nd;
+        vsum += v;
+        dsum += c->D == 2 ? 2.0 * std::sqrt(v / M_PI) : std::cbrt(6.0 * v / M_PI);
+    }
+    out->n_drops = nd + (ncomp > kCap ? ncomp - kCap : 0);
+    out->truncated = (nd > max_drops || ncomp > kCap) ? 1 : 0;
+    out->mean_drop_diameter = nd ? dsum / nd : 0.0;
+    out->drop_volume = vsum;
     return LBM_OK;
 }
 

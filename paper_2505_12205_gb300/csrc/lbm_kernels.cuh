@@ -1081,6 +1081,91 @@ __global__ void __launch_bounds__(128) k_advect(const __grid_constant__ DevParam
     }
 }
 
+// ------------------------------------------------- jet post-processing
+//
+// Connected components of the liquid phi > threshold (face neighbours,
+// periodic wrap across periodic faces) by minimum-label propagation with
+// pointer jumping; the host repeats the two passes until no label changes
+// (with a bounded number of rounds).  Labels are unpadded node indices; a
+// component's label converges to its smallest node index.
+template <class L>
+__global__ void k_ccl_init(const __grid_constant__ DevParams P, const float* __restrict__ phi, float thr,
+                           int* __restrict__ lab)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < P.N) lab[i] = phi[i] > thr ? int(i) : -1;
+}
+
+template <class L>
+__global__ void k_ccl_hook(const __grid_constant__ DevParams P, int* __restrict__ lab, int* __restrict__ changed)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    const int li = lab[i];
+    if (li < 0) return;
+    const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
+    const int pos[3] = {x, y, z}, len[3] = {P.nx, P.ny, P.nz};
+    const int64_t str[3] = {1, P.nx, int64_t(P.nx) * P.ny};
+    int m = li;
+    for (int d = 0; d < L::D; ++d)
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            int q = pos[d] + sgn;
+            if (q < 0 || q >= len[d]) {
+                if (P.bc[2 * d + (q < 0 ? 0 : 1)] != BC_PERIODIC) continue;
+                q = (q + len[d]) % len[d];
+            }
+            const int lj = lab[i + (q - pos[d]) * str[d]];
+            if (lj >= 0 && lj < m) m = lj;
+        }
+    if (m < li) {
+        atomicMin(&lab[li], m);            // hook the root of this label as well
+        atomicMin(&lab[i], m);
+        *changed = 1;
+    }
+}
+
+template <class L>
+__global__ void k_ccl_jump(int64_t n, int* __restrict__ lab)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int l = lab[i];
+    if (l < 0) return;
+    for (int k = 0; k < 64 && lab[l] != l && lab[l] >= 0; ++k) l = lab[l];
+    lab[i] = l;
+}
+
+// Per root: cells, and the smallest / largest coordinate along the last axis.
+template <class L>
+__global__ void k_ccl_stats(const __grid_constant__ DevParams P, const int* __restrict__ lab, int* __restrict__ size,
+                            int* __restrict__ lo, int* __restrict__ hi)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    const int l = lab[i];
+    if (l < 0) return;
+    const int m = int((L::D == 3) ? i / (int64_t(P.nx) * P.ny) : (i / P.nx) % P.ny);
+    atomicAdd(&size[l], 1);
+    atomicMin(&lo[l], m);
+    atomicMax(&hi[l], m);
+}
+
+// Roots (label == own index) appended to a list of (size, lo, hi).
+template <class L>
+__global__ void k_ccl_list(int64_t n, const int* __restrict__ lab, const int* __restrict__ size,
+                           const int* __restrict__ lo, const int* __restrict__ hi, int cap, int* __restrict__ count,
+                           int* __restrict__ list)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n || lab[i] != int(i)) return;
+    const int k = atomicAdd(count, 1);
+    if (k < cap) {
+        list[3 * k] = size[i];
+        list[3 * k + 1] = lo[i];
+        list[3 * k + 2] = hi[i];
+    }
+}
+
 // Per-block FP64 partial reductions for lbm_diag.
 struct DiagPartial {
     double sum_phi, sum_p_in, sum_p_out, max_speed;
@@ -1223,6 +1308,8 @@ struct Launch {
                                      float* phi_in, float* u_in, cudaStream_t s);
     static cudaError_t collide_cells(const DevParams& P, int64_t n, const float* f, const float* g,
                                      const float* phin, float* fs, float* gs, float* out, cudaStream_t s);
+    // phi = sum_a g_a of the state in A into b.phi (unpadded node order)
+    static cudaError_t phi(const DevParams& P, const Buffers& b, cudaStream_t s);
     // one step of the phase field alone in the velocity scale * uf (g: A -> B)
     static cudaError_t advect(const DevParams& P, const Buffers& b, const float* uf, float scale, cudaStream_t s);
 };
@@ -1403,6 +1490,13 @@ cudaError_t Launch<L, S>::inlet_profile(const DevParams& P, double cx, double cy
 {
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
     k_inlet_profile<L><<<(nface + 127) / 128, 128, 0, s>>>(nface, P.nx, cx, cy, R, W, uj, phi_in, u_in);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::phi(const DevParams& P, const Buffers& b, cudaStream_t s)
+{
+    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, static_cast<const T*>(b.gA), b.phi);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOU
 EXPORTS = ["lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_fields", "lbm_get_populations",
            "lbm_set_populations", "lbm_diag", "lbm_sync", "lbm_shape", "lbm_last_error",
            "lbm_destroy", "lbm_collide_cells", "lbm_set_timing", "lbm_get_timing",
-           "lbm_diag_noalloc", "lbm_advect_phase", "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step",
+           "lbm_diag_noalloc", "lbm_advect_phase", "lbm_jet_stats", "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step",
            "lbm_batch_get_fields", "lbm_batch_diag", "lbm_batch_get_plan", "lbm_batch_set_plan",
            "lbm_batch_tune", "lbm_batch_sync", "lbm_batch_last_error", "lbm_batch_destroy"]
 
@@ -59,6 +59,15 @@ class LbmDiagOut(ctypes.Structure):
         ("sum_p_out", ctypes.c_double), ("max_speed", ctypes.c_double),
         ("n_in", ctypes.c_int64), ("n_out", ctypes.c_int64),
         ("finite", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class LbmJetStats(ctypes.Structure):
+    _fields_ = [
+        ("n_components", ctypes.c_int32), ("has_jet", ctypes.c_int32),
+        ("breakup_length", ctypes.c_double),
+        ("n_drops", ctypes.c_int32), ("truncated", ctypes.c_int32),
+        ("mean_drop_diameter", ctypes.c_double), ("drop_volume", ctypes.c_double),
     ]
 
 
@@ -109,6 +118,7 @@ def load(path: str = LIB_PATH):
     lib.lbm_diag_noalloc.argtypes = [P, f32p, f32p, ctypes.c_double, ctypes.POINTER(LbmDiagOut), vp]
     lib.lbm_set_timing.argtypes = [vp, ctypes.c_int]
     lib.lbm_advect_phase.argtypes = [vp, f32p, ctypes.c_double, i64, ctypes.c_int]
+    lib.lbm_jet_stats.argtypes = [vp, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(LbmJetStats)]
     lib.lbm_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
     BP = ctypes.POINTER(LbmBatchPlan)
     lib.lbm_batch_create.argtypes = [P, ctypes.c_int32, vp, ctypes.POINTER(vp)]
@@ -270,6 +280,17 @@ def lbm_advect_phase(ctx, u, scale: float = 1.0, nsteps: int = 1):
     _check(lib, lib.lbm_advect_phase(ctx, a, float(scale), int(nsteps), k), ctx)
 
 
+def lbm_jet_stats(ctx, threshold: float = 0.5, max_drops: int = 4096) -> dict:
+    """Breakup length and drops of the current state (see include/lbm.h)."""
+    lib = load()
+    out = LbmJetStats()
+    vols = np.zeros(max(int(max_drops), 1), np.float64)
+    _check(lib, lib.lbm_jet_stats(ctx, float(threshold), int(max_drops), vols.ctypes.data, ctypes.byref(out)), ctx)
+    d = {k: getattr(out, k) for k, _ in LbmJetStats._fields_}
+    d["drop_volumes"] = vols[:min(out.n_drops, int(max_drops))].copy()
+    return d
+
+
 def lbm_set_timing(ctx, enable: bool):
     lib = load()
     _check(lib, lib.lbm_set_timing(ctx, 1 if enable else 0), ctx)
@@ -375,6 +396,9 @@ class LBM:
 
     def diag(self, phase_eps: float = 1e-3) -> dict:
         return lbm_diag(self._h, phase_eps)
+
+    def jet_stats(self, threshold: float = 0.5, max_drops: int = 4096) -> dict:
+        return lbm_jet_stats(self._h, threshold, max_drops)
 
     def advect(self, u, scale: float = 1.0, nsteps: int = 1):
         """Advance only the phase field in the velocity scale * u (see lbm_advect_phase)."""
