@@ -25,6 +25,11 @@ on a bounded slab of the same workload instead.
 network trained on the GPU by the library's kernels, then held-out cases run
 with the network in the loop against the solver alone.
 
+`--workload jet-sweep` runs the 3D jet of the application section in the
+paper's domain shape (6D x 6D x 20D, D = 32: 192 x 192 x 640, free-slip
+sides, plug inlet, convective outlet) for Weber numbers around the critical
+one and reports the breakup length and drop size of each (lbm_jet_stats).
+
 `--workload sweep` measures the batched sweep instead: 512 seeded 2D cases
 (drops and capillary waves, L x L with L uniform in 64..512, about 51 M nodes,
 float16 storage by default) advanced together by the batch API, reported as
@@ -535,6 +540,51 @@ def run_learned(args):
     return 0
 
 
+JETSWEEP = dict(We=[1.0, 2.2, 3.5, 5.0], nx=192, ny=192, nz=640, Rn=16.0, steps=24000, sample_from=12000,
+                sample_every=500)
+
+
+def run_jet_sweep(args):
+    """Breakup length L_b / D and mean drop diameter d_e / D against We."""
+    import torch
+    from paper_2505_12205_gb300 import build, lbm
+    build.build()
+    torch.cuda.set_device(0)
+    cfg = JETSWEEP
+    D = 2.0 * cfg["Rn"]
+    rows = []
+    tic = time.perf_counter()
+    for We in cfg["We"]:
+        p, phi, u, ps = C.jet3d(nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], Rn=cfg["Rn"], We=We)
+        p["bc"] = [C.FREESLIP, C.FREESLIP, C.FREESLIP, C.FREESLIP, C.INLET, C.OUTFLOW]
+        sim = lbm.LBM(p)
+        sim.init_fields(phi, u, ps)
+        sim.step(cfg["sample_from"])
+        Lb, de, nd = [], [], []
+        t = cfg["sample_from"]
+        while t < cfg["steps"]:
+            sim.step(cfg["sample_every"])
+            t += cfg["sample_every"]
+            st = sim.jet_stats(0.5)
+            Lb.append(st["breakup_length"] / D)
+            nd.append(st["n_drops"])
+            if st["n_drops"]:
+                de.append(st["mean_drop_diameter"] / D)
+        finite = sim.diag()["finite"] == 1
+        sim.close()
+        rows.append(dict(We=We, breakup_length_over_D=float(np.mean(Lb)), breakup_length_std=float(np.std(Lb)),
+                         drop_diameter_over_D=float(np.mean(de)) if de else None, drops_mean=float(np.mean(nd)),
+                         samples=len(Lb), finite=bool(finite)))
+    line = {"metric": "jet_breakup_vs_We", "value": None, "unit": "L_b/D", "n_gpus": 1,
+            "steps": cfg["steps"], "higher_is_better": None, "data": "synthetic",
+            "config": {"workload": "3D jet 6Dx6Dx20D (D = 32), free-slip sides, Re = 200, rho* = 100, mu* = 10",
+                       "grid": [cfg["nx"], cfg["ny"], cfg["nz"]], "sampled_steps": [cfg["sample_from"], cfg["steps"]],
+                       "sample_every": cfg["sample_every"]},
+            "seconds": time.perf_counter() - tic, "rows": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -545,7 +595,7 @@ def main():
     ap.add_argument("--storage", default=None, choices=["fp32", "fp16", "bf16"],
                     help="population storage format (arithmetic is float32); default fp32 for the "
                          "jet, fp16 for the sweep")
-    ap.add_argument("--workload", default="jet", choices=["jet", "sweep", "learned"])
+    ap.add_argument("--workload", default="jet", choices=["jet", "sweep", "learned", "jet-sweep"])
     ap.add_argument("--epochs", type=int, default=8, help="training epochs of the learned workload")
     ap.add_argument("--skip", type=int, default=1, help="windows predicted after each passing check (learned)")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
@@ -559,6 +609,8 @@ def main():
         return run_sweep(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "jet-sweep":
+        return run_jet_sweep(args)
     if args.storage is None:
         args.storage = "fp32"
     return run_gpu(args)
