@@ -20,6 +20,10 @@ the FP64 oracle on a slab of the same workload on the host cores.
 `--impl reference` times the FP64 CPU oracle (the baseline of this project)
 on a bounded slab of the same workload instead.
 
+`--workload rt2d` times the D2Q9 step the same way on the 2D Rayleigh-Taylor
+physics (At = 0.5, Re = 3000, W = 5, the 256 x 1024 case) repeated 32 times along
+x on an 8192 x 32768 domain (268 M nodes, 38.7 GB of float32 populations).
+
 `--workload learned` measures the learned fast-forward of planar-jet sweeps
 (D2Q9 512 x 2048, We in [1, 10]): snapshots generated by the solver, the
 network trained on the GPU by the library's kernels, then held-out cases run
@@ -60,6 +64,11 @@ import lbm_cases as C  # noqa: E402
 
 WORKLOAD = dict(name="jet3d_D3Q19_256x256x1024_fp32", nx=256, ny=256, nz=1024, Rn=16.0, We=2.2)
 SAMPLE_NZ = 8          # slab of the same workload for the CPU oracle
+# 2D Rayleigh-Taylor (At = 0.5, Re = 3000, W = 5, the physics of the 256 x 1024
+# case) repeated 32 times along x on an 8192 x 32768 domain: 268 M nodes,
+# 38.7 GB of float32 populations, the D2Q9 throughput workload
+RT_WORKLOAD = dict(name="rt2d_D2Q9_8192x32768", L=256, periods=32, height=32768)
+SAMPLE_RT_HEIGHT = 64  # strip of the same workload for the CPU oracle
 BYTES_PER_LU = 4 * 19 * 4   # f and g read + written once, float32, D3Q19
 METRIC = "MLUPS"
 
@@ -81,14 +90,14 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    if it was taken on the current kernel source."""
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the fused kernel on the full workload from the
+    committed ncu summary, if it was taken on the current kernel source."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             d = json.load(f)
         if d.get("source_sha256_16") == kernel_source_hash():
-            return float(d["dram_bytes_per_launch_full_workload"])
+            return float(d["workloads"][workload]["dram_bytes_per_launch_full_workload"])
     except Exception:
         pass
     return None
@@ -169,11 +178,23 @@ def max_over_ranks(x: float) -> float:
     return float(t.item())
 
 
-def oracle_baseline(min_seconds=10.0, max_steps=400, steps=None):
-    """FP64 oracle on a slab (nz = SAMPLE_NZ) of the workload, on all host cores."""
-    from oracle import oracle
+def oracle_sample(workload):
+    """(params, phi, u, p*, description) of the bounded sample the CPU oracle is timed on."""
+    if workload == "rt2d":
+        p, phi, u, ps = C.rayleigh_taylor2d(L=RT_WORKLOAD["L"], periods=RT_WORKLOAD["periods"],
+                                            height=SAMPLE_RT_HEIGHT)
+        return p, phi, u, ps, "strip %dx%d of the Rayleigh-Taylor workload (same parameters, walls)" % (
+            p["nx"], p["ny"])
     p, phi, u, ps = C.jet3d(nx=WORKLOAD["nx"], ny=WORKLOAD["ny"], nz=SAMPLE_NZ,
                             Rn=WORKLOAD["Rn"], We=WORKLOAD["We"], stub=4.0)
+    return p, phi, u, ps, "slab %dx%dx%d of the jet workload (same parameters, inlet + outlet)" % (
+        WORKLOAD["nx"], WORKLOAD["ny"], SAMPLE_NZ)
+
+
+def oracle_baseline(min_seconds=10.0, max_steps=400, steps=None, workload="jet"):
+    """FP64 oracle on a bounded sample of the workload, on all host cores."""
+    from oracle import oracle
+    p, phi, u, ps, what = oracle_sample(workload)
     o = oracle.Oracle(p)
     o.init_fields(phi, u, ps)
     nodes = p["nx"] * p["ny"] * p["nz"]
@@ -190,7 +211,7 @@ def oracle_baseline(min_seconds=10.0, max_steps=400, steps=None):
             break
     el = time.perf_counter() - t0
     o.close()
-    return nodes * n / el / 1e6, n, el, oracle.threads(), nodes
+    return nodes * n / el / 1e6, n, el, oracle.threads(), nodes, what
 
 
 def run_reference(args):
@@ -205,15 +226,15 @@ def run_reference(args):
         return 0
     for _ in range(max(args.warmup, 0)):
         pass
-    mlups, n, el, cores, nodes = oracle_baseline(steps=max(args.steps, 1))
-    sample = "slab %dx%dx%d of the jet workload (same parameters, inlet + outlet), %d steps" % (
-        WORKLOAD["nx"], WORKLOAD["ny"], SAMPLE_NZ, n)
+    mlups, n, el, cores, nodes, what = oracle_baseline(steps=max(args.steps, 1), workload=args.workload)
+    sample = "%s, %d steps" % (what, n)
+    name = RT_WORKLOAD["name"] + "_" + (args.storage or "fp32") if args.workload == "rt2d" else WORKLOAD["name"]
     line = {
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / n * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "sample_nodes": nodes},
+        "config": {"workload": name, "sample_nodes": nodes},
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -237,13 +258,30 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import oracle
         oracle.build()
-        mlups, n, el, cores, nodes = oracle_baseline()
+        mlups, n, el, cores, nodes, what = oracle_baseline(workload=args.workload)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": "slab %dx%dx%d of the jet workload (same parameters), %d steps, %.1f s"
-                         % (WORKLOAD["nx"], WORKLOAD["ny"], SAMPLE_NZ, n, el)}
+               "sample": "%s, %d steps, %.1f s" % (what, n, el)}
 
-    nx, ny, nz = args.grid if args.grid else (WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"])
-    p, phi, u, ps = C.jet3d(nx=nx, ny=ny, nz=nz, Rn=WORKLOAD["Rn"], We=WORKLOAD["We"])
+    rt = args.workload == "rt2d"
+    if rt:
+        L = RT_WORKLOAD["L"]
+        per, height = (args.grid[0] // L, args.grid[1]) if args.grid else (RT_WORKLOAD["periods"],
+                                                                          RT_WORKLOAD["height"])
+        p, phi, u, ps = C.rayleigh_taylor2d(L=L, periods=per, height=height)
+        Q, dim, lat, faces = 9, 2, "D2Q9", 0
+        name = "rt2d_D2Q9_%dx%d_%s" % (p["nx"], p["ny"], args.storage)
+        kname = "k_step_fused<D2Q9,64,1> (phi + collide + push-stream, one pass)"
+        extra = {"At": 0.5, "Re": 3000.0, "W": 5.0,
+                 "note": "Rayleigh-Taylor physics of the 256 x 1024 case repeated %d times along x" % per}
+    else:
+        nx, ny, nz = args.grid if args.grid else (WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"])
+        p, phi, u, ps = C.jet3d(nx=nx, ny=ny, nz=nz, Rn=WORKLOAD["Rn"], We=WORKLOAD["We"])
+        Q, dim, lat, faces = 19, 3, "D3Q19", 2
+        name = WORKLOAD["name"] if not args.grid else "jet3d_D3Q19_%dx%dx%d_fp32 (reduced grid)" % tuple(args.grid)
+        if args.storage != "fp32":
+            name = name.replace("fp32", args.storage)
+        kname = "k_step_fused<D3Q19,32,6> (phi + collide + push-stream, one pass)"
+        extra = {"We": WORKLOAD["We"]}
     p["storage"] = {"fp32": 0, "fp16": 1, "bf16": 2}[args.storage]
     elem = 4 if args.storage == "fp32" else 2
     N = p["nx"] * p["ny"] * p["nz"]
@@ -283,11 +321,12 @@ def run_gpu(args):
     # roofline of the fused collide-stream kernel
     peak, peak_kind = peaks()
     step_ms = ms_step / max(nrec, 1)
-    bytes_per_lu = 4 * 19 * elem
+    bytes_per_lu = 4 * Q * elem
     achieved = bytes_per_lu * N / (step_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": ncu_traffic() if args.storage == "fp32" else None,
-            "kernel": "k_step_fused<D3Q19,32,8> (phi + collide + push-stream, one pass)",
+            "frac": achieved / peak,
+            "traffic": ncu_traffic(args.workload) if (args.storage == "fp32" and not args.grid) else None,
+            "kernel": kname,
             "algorithmic_bytes_per_lu": bytes_per_lu, "peak_source": peak_kind + " hbm_gbs",
             "kernel_share_of_step": ms_step / max(ms_phi + ms_step + ms_face, 1e-9)}
 
@@ -296,13 +335,13 @@ def run_gpu(args):
     u_h = torch.from_numpy(u).pin_memory()
     ps_h = torch.zeros(N, dtype=torch.float32).pin_memory()
     o_phi = torch.empty(N, dtype=torch.float32).pin_memory()
-    o_u = torch.empty(3 * N, dtype=torch.float32).pin_memory()
+    o_u = torch.empty(dim * N, dtype=torch.float32).pin_memory()
     o_p = torch.empty(N, dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
     t0 = time.perf_counter()
-    lbm.lbm_init_fields(sim._h, phi_h, u_h, ps_h, n=N, dim=3)
+    lbm.lbm_init_fields(sim._h, phi_h, u_h, ps_h, n=N, dim=dim)
     lbm.lbm_step(sim._h, args.steps)
     lbm.lbm_get_fields(sim._h, o_phi, o_u, o_p)
     te2e = time.perf_counter() - t0
@@ -323,17 +362,16 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.storage == "fp32" else "f32 arithmetic, %s storage" % args.storage,
             "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"] if not args.grid else
-                       "jet3d_D3Q19_%dx%dx%d_fp32 (reduced grid)" % tuple(args.grid), "lattice": "D3Q19",
-                       "grid": [p["nx"], p["ny"], p["nz"]], "nodes_per_gpu": N,
-                       "We": WORKLOAD["We"], "storage": args.storage,
-                       "l2": "inputs larger than L2: %.1f GB of populations per GPU vs 129 MB L2"
-                             % (4 * 19 * elem * N / 1e9),
-                       "parallelism": "replicas" if ws > 1 else "single"},
+            "config": dict({"workload": name, "lattice": lat,
+                            "grid": [p["nx"], p["ny"], p["nz"]], "nodes_per_gpu": N,
+                            "storage": args.storage,
+                            "l2": "inputs larger than L2: %.1f GB of populations per GPU vs 129 MB L2"
+                                  % (4 * Q * elem * N / 1e9),
+                            "parallelism": "replicas" if ws > 1 else "single"}, **extra),
             "hbm_gbs_algorithmic": value / ws * 1e6 * bytes_per_lu / 1e9 if ws == 1 else None,
             "roofline": roof,
             "e2e": e2e,
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": (1 + faces) * args.steps,
             "clocks": clk,
             "cpu_baseline": cpu,
         }
@@ -595,11 +633,12 @@ def main():
     ap.add_argument("--storage", default=None, choices=["fp32", "fp16", "bf16"],
                     help="population storage format (arithmetic is float32); default fp32 for the "
                          "jet, fp16 for the sweep")
-    ap.add_argument("--workload", default="jet", choices=["jet", "sweep", "learned", "jet-sweep"])
+    ap.add_argument("--workload", default="jet", choices=["jet", "rt2d", "sweep", "learned", "jet-sweep"])
     ap.add_argument("--epochs", type=int, default=8, help="training epochs of the learned workload")
     ap.add_argument("--skip", type=int, default=1, help="windows predicted after each passing check (learned)")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
-                    help="reduced grid of the same jet workload (profiling captures)")
+                    help="reduced grid of the same jet workload (profiling captures); for rt2d NX "
+                         "(a multiple of 256) and NY, NZ ignored")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

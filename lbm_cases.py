@@ -100,8 +100,13 @@ def drop3d(n=32, R=8.0, rho_ratio=1000.0, mu_ratio=100.0, sigma=1e-3, W=4.0,
 # -------------------------------------------------------- Rayleigh-Taylor
 
 def rayleigh_taylor2d(L=256, height=None, W=5.0, At=0.5, Re=3000.0, Pe=1000.0,
-                      Ca=0.26, U0=0.04, mu_ratio=1.0):
-    """2D Rayleigh-Taylor instability, D2Q9, L x 4L, walls top/bottom, periodic x."""
+                      Ca=0.26, U0=0.04, mu_ratio=1.0, periods=1):
+    """2D Rayleigh-Taylor instability, D2Q9, L x 4L, walls top/bottom, periodic x.
+
+    periods > 1 repeats the same physics (the parameters of wavelength L)
+    periods times along x, on a domain periods*L wide and `height` high: the
+    throughput workload of the HBM roofline (8192 x 32768 = 32 x 32 copies of
+    the 256 x 1024 case's area)."""
     ny = 4 * L if height is None else height
     rho_H = 1.0
     rho_L = rho_H * (1.0 - At) / (1.0 + At)
@@ -110,15 +115,18 @@ def rayleigh_taylor2d(L=256, height=None, W=5.0, At=0.5, Re=3000.0, Pe=1000.0,
     tau_H = mu_H / (rho_H / 3.0)
     mu_L = mu_H / mu_ratio
     tau_L = mu_L / (rho_L / 3.0)
-    p = base_params(D2Q9, L, ny, 1, rho_H=rho_H, rho_L=rho_L, tau_H=tau_H, tau_L=tau_L,
+    nx = L * periods
+    p = base_params(D2Q9, nx, ny, 1, rho_H=rho_H, rho_L=rho_L, tau_H=tau_H, tau_L=tau_L,
                     sigma=mu_H * U0 / Ca, W=W, mobility=U0 * L / Pe,
                     force=[0.0, -g, 0.0], rho_ref=rho_L)
     p["bc"] = [PERIODIC, PERIODIC, WALL, WALL, PERIODIC, PERIODIC]
-    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(L, dtype=np.float64),
-                       indexing="ij")
+    x = np.arange(nx, dtype=np.float64)
     y0 = ny / 2.0 + 0.1 * L * np.cos(2.0 * np.pi * x / L)
-    phi = tanh_profile(y - y0, W).astype(np.float32)[None]   # heavy on top
-    return p, phi, _zeros_u(2, (1, ny, L)), None
+    phi = np.empty((1, ny, nx), np.float32)                  # heavy on top
+    for r0 in range(0, ny, 1024):                            # row blocks: bounded temporaries
+        y = np.arange(r0, min(r0 + 1024, ny), dtype=np.float64)[:, None]
+        phi[0, r0:r0 + y.shape[0]] = tanh_profile(y - y0[None, :], W)
+    return p, phi, _zeros_u(2, (1, ny, nx)), None
 
 
 # -------------------------------------------------------------- 3D jet

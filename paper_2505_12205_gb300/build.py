@@ -25,6 +25,17 @@ UNITS = ["lbm_d3q19.cu", "lbm_d3q19_f16.cu", "lbm_d3q19_bf16.cu", "lbm_d2q9.cu",
 HEADERS = ["lbm_lattice.cuh", "lbm_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]
+# The lattice Boltzmann units spell every fused multiply-add out (fmaf): with
+# contraction left to the compiler, whether a product and a sum fuse depends
+# on register pressure, so the same node update compiled for another tile
+# shape or register budget would round differently.  With it off, every
+# kernel that runs the node update (single contexts, batches of any tile
+# width) computes bit-identical results.
+NO_CONTRACT = ["-fmad=false"]
+
+
+def unit_flags(name: str) -> list:
+    return FLAGS + ([] if name.startswith("nn_") else NO_CONTRACT)
 
 
 def nvcc() -> str:
@@ -42,7 +53,7 @@ def _digest() -> str:
     for hdr in ("lbm.h", "lbm_nn.h"):
         with open(os.path.join(ROOT, "include", hdr), "rb") as f:
             h.update(f.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(" ".join(ARCH + FLAGS + NO_CONTRACT).encode())
     return h.hexdigest()
 
 
@@ -59,7 +70,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_unit(name):
         obj = os.path.join(BUILD, name.replace(".cu", ".o"))
         log = os.path.join(BUILD, name.replace(".cu", ".ptxas.log"))
-        cmd = [cc] + FLAGS + ARCH + ["-I", os.path.join(ROOT, "include"), "-c",
+        cmd = [cc] + unit_flags(name) + ARCH + ["-I", os.path.join(ROOT, "include"), "-c",
                                      os.path.join(CSRC, name), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         with open(log, "w") as f:

@@ -274,15 +274,15 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
 
     // phi clamped inside the material properties only
     const float ph = fminf(fmaxf(phi, 0.0f), 1.0f);
-    const float rho = P.rho_L + ph * (P.rho_H - P.rho_L);      // eq:density_interpolation
+    const float rho = fmaf(ph, P.rho_H - P.rho_L, P.rho_L);      // eq:density_interpolation
     const float inv_rho = 1.0f / rho;
     float tau;
-    if (P.visc_model == 1) tau = P.tau_L + ph * (P.tau_H - P.tau_L);   // eq:relaxation_time
-    else tau = (P.mu_L + ph * (P.mu_H - P.mu_L)) * (3.0f * inv_rho);  // eq:dynamic_viscosity, nu = c_s^2 tau
+    if (P.visc_model == 1) tau = fmaf(ph, P.tau_H - P.tau_L, P.tau_L);   // eq:relaxation_time
+    else tau = fmaf(ph, P.mu_H - P.mu_L, P.mu_L) * (3.0f * inv_rho);   // eq:dynamic_viscosity, nu = c_s^2 tau
     const float s_nu = 1.0f / (tau + 0.5f);
 
     // chemical potential (sign reading: 4 beta (phi - phi_L)(phi - phi_H)(phi - phi_0))
-    const float mu_phi = 4.0f * P.beta * phi * (phi - 1.0f) * (phi - 0.5f) - P.kappa * lap;
+    const float mu_phi = fmaf(-P.kappa, lap, 4.0f * P.beta * phi * (phi - 1.0f) * (phi - 0.5f));
 
     // zeroth, first and second moments of f (eq:normalized_pressure) from
     // the pair sums s = f_a + f_abar and differences d = f_a - f_abar
@@ -314,9 +314,9 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
     const float rx = drho * dx, ry = drho * dy, rz = drho * dz;
     const float cp = -pstar * (1.0f / 3.0f);                  // eq:pressure_force
     const float fb = rho - P.rho_ref;                          // eq:gravity_force
-    float Fx = mu_phi * dx + cp * rx + fb * P.gx;              // F_s + F_p + F_b
-    float Fy = mu_phi * dy + cp * ry + fb * P.gy;
-    float Fz = (L::D == 2) ? 0.0f : mu_phi * dz + cp * rz + fb * P.gz;
+    float Fx = fmaf(fb, P.gx, fmaf(cp, rx, mu_phi * dx));      // F_s + F_p + F_b
+    float Fy = fmaf(fb, P.gy, fmaf(cp, ry, mu_phi * dy));
+    float Fz = (L::D == 2) ? 0.0f : fmaf(fb, P.gz, fmaf(cp, rz, mu_phi * dz));
     const float h_rho = 0.5f * inv_rho;
     const float p3 = pstar * (1.0f / 3.0f);
 
@@ -327,28 +327,30 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
     // at s_nu and the trace at 1, so the relaxed stress is
     // s_nu D + (1 - s_nu) tr(D) / dim I.
     {
-        const float u0x = jx + Fx * h_rho, u0y = jy + Fy * h_rho, u0z = (L::D == 2) ? 0.0f : jz + Fz * h_rho;
-        const float dxx = sxx - p3 - u0x * u0x, dyy = syy - p3 - u0y * u0y;
-        const float dzz = (L::D == 2) ? 0.0f : szz - p3 - u0z * u0z;
-        const float dxy = sxy - u0x * u0y;
+        const float u0x = fmaf(Fx, h_rho, jx), u0y = fmaf(Fy, h_rho, jy);
+        const float u0z = (L::D == 2) ? 0.0f : fmaf(Fz, h_rho, jz);
+        const float dxx = fmaf(-u0x, u0x, sxx - p3), dyy = fmaf(-u0y, u0y, syy - p3);
+        const float dzz = (L::D == 2) ? 0.0f : fmaf(-u0z, u0z, szz - p3);
+        const float dxy = fmaf(-u0x, u0y, sxy);
         const float iso = (1.0f - s_nu) * (dxx + dyy + dzz) * (1.0f / float(L::D));
-        const float txx = s_nu * dxx + iso, tyy = s_nu * dyy + iso;
+        const float txx = fmaf(s_nu, dxx, iso), tyy = fmaf(s_nu, dyy, iso);
         const float txy = s_nu * dxy;
         // nu / c_s^2 = tau
         if constexpr (L::D == 2) {
-            Fx -= tau * (txx * rx + txy * ry);
-            Fy -= tau * (txy * rx + tyy * ry);
+            Fx = fmaf(-tau, fmaf(txy, ry, txx * rx), Fx);
+            Fy = fmaf(-tau, fmaf(tyy, ry, txy * rx), Fy);
         } else {
-            const float dxz = sxz - u0x * u0z, dyz = syz - u0y * u0z;
-            const float tzz = s_nu * dzz + iso, txz = s_nu * dxz, tyz = s_nu * dyz;
-            Fx -= tau * (txx * rx + txy * ry + txz * rz);
-            Fy -= tau * (txy * rx + tyy * ry + tyz * rz);
-            Fz -= tau * (txz * rx + tyz * ry + tzz * rz);
+            const float dxz = fmaf(-u0x, u0z, sxz), dyz = fmaf(-u0y, u0z, syz);
+            const float tzz = fmaf(s_nu, dzz, iso), txz = s_nu * dxz, tyz = s_nu * dyz;
+            Fx = fmaf(-tau, fmaf(txz, rz, fmaf(txy, ry, txx * rx)), Fx);
+            Fy = fmaf(-tau, fmaf(tyz, rz, fmaf(tyy, ry, txy * rx)), Fy);
+            Fz = fmaf(-tau, fmaf(tzz, rz, fmaf(tyz, ry, txz * rx)), Fz);
         }
     }
 
     // eq:velocity_update
-    const float ux = jx + Fx * h_rho, uy = jy + Fy * h_rho, uz = (L::D == 2) ? 0.0f : jz + Fz * h_rho;
+    const float ux = fmaf(Fx, h_rho, jx), uy = fmaf(Fy, h_rho, jy);
+    const float uz = (L::D == 2) ? 0.0f : fmaf(Fz, h_rho, jz);
 
     if (out) {
         out[0] = phi;
@@ -360,11 +362,12 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
     if constexpr (!collide) {
         return;
     } else {
-        const float uu = ux * ux + uy * uy + uz * uz;
+        const float uu = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
 
         // g forcing: eq:forcing_term, n = 0 where |grad phi| < 1e-12
-        const float gn2 = dx * dx + dy * dy + dz * dz;
-        const float amp = (gn2 >= 1e-24f) ? (1.0f - 4.0f * (phi - 0.5f) * (phi - 0.5f)) * P.inv_W * rsqrtf(gn2) : 0.0f;
+        const float gn2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float hp = phi - 0.5f;
+        const float amp = (gn2 >= 1e-24f) ? fmaf(-4.0f * hp, hp, 1.0f) * P.inv_W * rsqrtf(gn2) : 0.0f;
         const float nx = amp * dx, ny = amp * dy, nz = amp * dz;
 
         // f: eq:force_term, eq:equilibrium_modified, eq:mrt_collision with
@@ -372,9 +375,9 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
         //   f* = f - M^-1 S M (f - feq + F/2) + F = feq + F/2 + (1 - s_nu) P (f - feq + F/2).
         // The stress-row moments of f - feq + F/2 are combinations of the
         // non-equilibrium stress E = Pi(f) - p* c_s^2 I - u u (F/2 has none).
-        const float exx = sxx - p3 - ux * ux, eyy = syy - p3 - uy * uy;
-        const float ezz = (L::D == 2) ? 0.0f : szz - p3 - uz * uz;
-        const float exy = sxy - ux * uy, exz = sxz - ux * uz, eyz = syz - uy * uz;
+        const float exx = fmaf(-ux, ux, sxx - p3), eyy = fmaf(-uy, uy, syy - p3);
+        const float ezz = (L::D == 2) ? 0.0f : fmaf(-uz, uz, szz - p3);
+        const float exy = fmaf(-ux, uy, sxy), exz = fmaf(-ux, uz, sxz), eyz = fmaf(-uy, uz, syz);
         float ck[L::NS];
         const float r = 1.0f - s_nu;
         if constexpr (L::D == 2) {
@@ -384,7 +387,7 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
             ck[0] = r * exy;                                // rows 5-9 of eq:A2
             ck[1] = r * eyz;
             ck[2] = r * exz;
-            ck[3] = r * (2.0f * exx - eyy - ezz);
+            ck[3] = r * (fmaf(2.0f, exx, -eyy) - ezz);
             ck[4] = r * (eyy - ezz);
         }
 
@@ -414,8 +417,7 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
             const float W = diag ? W2 : W1;
             const float eu = edot<L>(a, ux, uy, uz);
             const float even = fmaf((4.5f * W) * eu, eu, diag ? uw2 : uw1);
-            const float odd = (3.0f * W) * eu;
-            const float da = even + odd, db = even - odd;
+            const float da = fmaf(3.0f * W, eu, even), db = fmaf(-3.0f * W, eu, even);
             const float fph = edot<L>(a, nx, ny, nz) * (diag ? kw2 : kw1);
             const float hf = edot<L>(a, frx, fry, frz) * W;
             float proj = -0.0f;
@@ -743,10 +745,14 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
     }
 }
 
-// Three resident blocks per SM for D3Q19 (24 warps; the pair-form node update
-// keeps the register count within 85), four for D2Q9.
+// Resident blocks per SM: for D3Q19 as many as hold 24 warps (the pair-form
+// node update needs up to 85 registers), for D2Q9 as many as hold 32 warps
+// (64 registers, no spills).
+template <class L, int NT>
+constexpr int fused_min_blocks() { return (L::D == 3) ? 768 / NT : 1024 / NT; }
+
 template <class L, class S, int TX, int TY>
-__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (L::D == 3) ? 3 : 4)
+__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (fused_min_blocks<L, TX *((L::D == 3) ? TY : 1)>()))
 k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typename S::T* __restrict__ fA,
              const typename S::T* __restrict__ gA, typename S::T* __restrict__ fB, typename S::T* __restrict__ gB)
 {
@@ -779,7 +785,7 @@ struct BatchCase {
 };
 
 template <class L, class S, int TX, int TY>
-__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (L::D == 3) ? 3 : 4)
+__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (fused_min_blocks<L, TX *((L::D == 3) ? TY : 1)>()))
 k_step_batch(const BatchCase* __restrict__ cases, const int2* __restrict__ items, int nitems,
              int* __restrict__ counter, const typename S::T* __restrict__ fA, const typename S::T* __restrict__ gA,
              typename S::T* __restrict__ fB, typename S::T* __restrict__ gB)
@@ -1314,10 +1320,13 @@ struct Launch {
     static cudaError_t advect(const DevParams& P, const Buffers& b, const float* uf, float scale, cudaStream_t s);
 };
 
-// Tile shapes: 32 x 8 columns in 3D, 128 nodes of a row in 2D.
+// Tile shapes: 32 x 6 columns in 3D (four 192-thread blocks per SM), 64 nodes
+// of a row in 2D (sixteen 64-thread blocks per SM); measured best of
+// 32 x {4..8} and {32..256} x 1 on the 3D jet and the 2D Rayleigh-Taylor
+// workloads.
 template <class L> struct FusedTile;
-template <> struct FusedTile<D2Q9> { static constexpr int TX = 128, TY = 1; };
-template <> struct FusedTile<D3Q19> { static constexpr int TX = 32, TY = 8; };
+template <> struct FusedTile<D2Q9> { static constexpr int TX = 64, TY = 1; };
+template <> struct FusedTile<D3Q19> { static constexpr int TX = 32, TY = 6; };
 
 template <class L, class S>
 cudaError_t Launch<L, S>::fused_geom(const DevParams& P, FusedGeom* G, int* nblocks)

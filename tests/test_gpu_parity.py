@@ -95,10 +95,13 @@ STEP_CASES = {
     "d3q19_periodic": (1, (9, 7, 131), [0] * 6),
     "d3q19_walls": (1, (11, 9, 13), [1, 1, 0, 0, 1, 1]),
     "d3q19_jet": (1, (12, 10, 129), [0, 0, 1, 1, 2, 3]),
-    # grids whose x-y planes are whole numbers of 32 x 8 tiles
-    "d3q19_aligned_periodic": (1, (10, 16, 64), [0] * 6),
-    "d3q19_aligned_walls": (1, (9, 8, 32), [1, 1, 1, 1, 1, 1]),
-    "d3q19_aligned_jet": (1, (12, 16, 32), [0, 0, 0, 0, 2, 3]),
+    # grids whose planes are whole numbers of tiles (32 x 6 in 3D, 64 x 1 in 2D)
+    "d2q9_aligned_walls": (0, (1, 12, 128), [0, 0, 1, 1, 0, 0]),
+    "d3q19_aligned_periodic": (1, (10, 12, 64), [0] * 6),
+    "d3q19_aligned_walls": (1, (9, 6, 32), [1, 1, 1, 1, 1, 1]),
+    "d3q19_aligned_jet": (1, (12, 18, 32), [0, 0, 0, 0, 2, 3]),
+    # rows a multiple of 8 (ragged against 6-row tiles)
+    "d3q19_rows16_periodic": (1, (10, 16, 64), [0] * 6),
     # free slip (App. B): slip x faces with wall y faces (slip-wall corners),
     # slip sides of a jet, slip-slip edges in 3D, and the paper's jet faces
     "d2q9_freeslip": (0, (1, 23, 71), [4, 4, 1, 1, 0, 0]),
@@ -187,8 +190,8 @@ def test_rt2d_parity_full_size(lib, orc, report):
 
 
 def test_jet3d_aligned_parity(lib, orc, report):
-    """Jet on a 32 x 32 x 64 grid (whole 32 x 8 tiles), 100 steps."""
-    p, phi, u, ps = C.jet3d(nx=32, ny=32, nz=64, Rn=5.0)
+    """Jet on a 32 x 36 x 64 grid (whole 32 x 6 tiles), 100 steps."""
+    p, phi, u, ps = C.jet3d(nx=32, ny=36, nz=64, Rn=5.0)
     sim = lib.LBM(p)
     sim.init_fields(phi, u, ps)
     sim.step(100)
