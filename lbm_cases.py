@@ -335,6 +335,26 @@ def shear_flow_interface(L0=200, U0=0.04, mobility=0.0002, W=3.0, R=None, centre
 
 # ------------------------------------------------- random states (1 step)
 
+def random_state_device(params, seed_offset=0, du=0.02, dphi=0.6, device="cuda"):
+    """The recipe of random_state drawn on the GPU (torch's seeded generator)
+    for grids too large to build on the host: float32 tensors f, g of shape
+    [Q][nz][ny][nx] on the device."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(SEED + seed_offset)
+    lat = params["lattice"]
+    Q = 9 if lat == D2Q9 else 19
+    shape = (params.get("nz", 1), params["ny"], params["nx"])
+
+    def rnd(*s):
+        return torch.rand(*s, generator=gen, device=device, dtype=torch.float32)
+
+    phi = 0.5 + dphi * (rnd(*shape) - 0.5)
+    f = rnd(Q, *shape).sub_(0.5).mul_(du).add_(1e-3 * (rnd(*shape) - 0.5)).div_(Q)
+    g = rnd(Q, *shape).sub_(0.5).mul_(du).add_(1.0).mul_(phi / Q)
+    return f, g
+
+
 def random_state(params, seed_offset=0, du=0.02, dphi=0.6):
     """Seeded random but physical-looking post-stream populations:
     returns (f, g) float64 arrays [Q][nz][ny][nx] built as smooth random
