@@ -214,6 +214,24 @@ def oracle_baseline(min_seconds=10.0, max_steps=400, steps=None, workload="jet")
     return nodes * n / el / 1e6, n, el, oracle.threads(), nodes, what
 
 
+def oracle_one_thread(workload, seconds=6.0):
+    """The same oracle sample on one host thread (serial), in a fresh process
+    with OMP_NUM_THREADS=1: MLUPS, or None if that run fails."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "r = bench.oracle_baseline(min_seconds=%r, max_steps=200, workload=%r); "
+            "print(json.dumps({'mlups': r[0], 'steps': r[1], 'seconds': r[2], 'threads': r[3]}))"
+            % (ROOT, seconds, workload))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=300).stdout
+        d = json.loads(out.strip().splitlines()[-1])
+        return {"value": d["mlups"], "unit": "MLUPS", "cores": d["threads"],
+                "sample": "the same sample, %d steps, %.1f s" % (d["steps"], d["seconds"])}
+    except Exception:
+        return None
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -260,7 +278,8 @@ def run_gpu(args):
         oracle.build()
         mlups, n, el, cores, nodes, what = oracle_baseline(workload=args.workload)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": "%s, %d steps, %.1f s" % (what, n, el)}
+               "sample": "%s, %d steps, %.1f s" % (what, n, el),
+               "one_thread": oracle_one_thread(args.workload)}
 
     rt = args.workload == "rt2d"
     if rt:
@@ -552,7 +571,7 @@ def run_learned(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - tic
     val, pers = S.evaluate(net, Xt, Yt, np.arange(Xt.shape[0]))
-    res = [S.fast_forward(net, w, t0, t1, skip=args.skip) for w in test_We]
+    res = [S.fast_forward(net, w, t0, t1, skip=args.skip, twins=True) for w in test_We]
     ms_solver = sum(x["ms_solver"] for x in res)
     ms_ff = sum(x["ms_fast_forward"] for x in res)
     steps = t1 - t0
@@ -568,6 +587,10 @@ def run_learned(args):
         "solver_alone": {"value": len(res) * 3600e3 / ms_solver, "unit": "cases/h"},
         "speedup_vs_solver": ms_solver / ms_ff,
         "accepted_at_end": len(accepted), "cases": len(res),
+        "final_interface_distance": {
+            "network_in_the_loop": [x["final_interface_distance"] for x in res],
+            "solver_perturbed_1e-6": [x["twin_perturb"]["final_interface_distance"] for x in res],
+            "solver_restarted_from_itself": [x["twin_restart"]["final_interface_distance"] for x in res]},
         "train": {"seconds": t_train, "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1],
                   "generate_seconds": t_gen},
         "held_out": {"loss": val, "persistence_loss": pers},

@@ -179,7 +179,57 @@ def evaluate(net, X, Y, idx, nx=512, ny=2048):
     return loss / len(idx), pers / len(idx)
 
 
-def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, nx=512, ny=2048, stream=None):
+def solver_twin(We, t0, t1, ref_phi, mode, eps=1e-6, every=2, seed=0, nx=512, ny=2048, stream=None):
+    """The solver alone from t0 to t1 under a controlled disturbance, compared
+    at t1 with the undisturbed solver's phi (ref_phi):
+      'perturb': every g population scaled by 1 + eps r (r uniform in [-1, 1],
+                 seeded) at t0 -- how far the flow itself carries a
+                 disturbance at the level of float32 rounding;
+      'restart': every `every`-th window of K steps ends with a restart from
+                 the solver's own coarse-grained state (refined, mass-projected,
+                 equilibrium with p* = 0) -- what a perfect network would give
+                 through the same restart.
+    Returns (mean interface distance, jet-length change, mass error, restarts)."""
+    import torch
+    c = Case(We, nx=nx, ny=ny, stream=stream)
+    c.step(t0)
+    restarts = 0
+    if mode == "perturb":
+        Q = 9
+        f = torch.empty(Q * c.N, dtype=torch.float32, device="cuda")
+        g = torch.empty(Q * c.N, dtype=torch.float32, device="cuda")
+        lbm.lbm_get_populations(c.sim._h, f, g)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(C.SEED + 50 + seed)
+        r = torch.rand(Q * c.N, generator=gen, device="cuda", dtype=torch.float32).mul_(2.0).sub_(1.0)
+        g.mul_(r.mul_(eps).add_(1.0))
+        lbm.lbm_set_populations(c.sim._h, f, g)
+        c.step(t1 - t0)
+    elif mode == "restart":
+        xf = torch.zeros(c.hc * c.wc, 3, dtype=torch.float32, device="cuda")
+        w = 0
+        while c.t + K <= t1:
+            c.step(K)
+            w += 1
+            if w % every == 0 and c.t < t1:
+                c.coarse(xf=xf)
+                c.restart_from(xf, c.mass())
+                restarts += 1
+        if c.t < t1:
+            c.step(t1 - c.t)
+    else:
+        raise ValueError(mode)
+    c.read_fields()
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    iout = torch.zeros(2, dtype=torch.int32, device="cuda")
+    dist, sa, sb = interface_stats(c.phi, ref_phi, ny, nx, out, stream)
+    front = front_error(c.phi, ref_phi, ny, nx, iout, stream=stream)
+    c.close()
+    return dist, front, abs(sa - sb) / max(abs(sb), 1e-30), restarts
+
+
+def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, nx=512, ny=2048, stream=None,
+                 twins=False):
     """Run one case from t0 to t1 with the network in the loop (after a
     passing check the next `skip` windows are predicted, one by one, instead
     of solved), and the same case with the solver alone; returns the
@@ -257,6 +307,11 @@ def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, 
                accepted_at_end=bool(dist_end <= interface_bound and front_end <= interface_bound
                                     and abs(sa - sb) / max(abs(sb), 1e-30) <= mass_bound),
                judged=[dict(interface=d, front=f, mass=e) for d, f, e in errs])
+    if twins:
+        for mode in ("perturb", "restart"):
+            d, f, e, n = solver_twin(We, t0, t1, ref.phi, mode, every=skip + 1, nx=nx, ny=ny, stream=stream)
+            res["twin_" + mode] = dict(final_interface_distance=d, final_front_error=f, final_mass_error=e,
+                                       restarts=n)
     ref.close()
     ff.close()
     return res

@@ -115,3 +115,22 @@ def test_restart_from_a_coarse_grained_state_stays_finite(env, report):
     assert dist < 3.0
     c.close()
     ref.close()
+
+
+def test_solver_twins_on_a_small_jet(env, report):
+    """The twins the fast-forward is measured against: an undisturbed twin
+    (eps = 0) reproduces the solver's interface exactly, a 1e-6 disturbance and
+    restarts from the solver's own coarse-grained state stay finite."""
+    torch, nn, S = env
+    nx, ny, t0, t1 = 128, 512, 1000, 1600
+    ref = S.Case(4.0, nx=nx, ny=ny)
+    ref.step(t1)
+    ref.read_fields()
+    d0, f0, m0, _ = S.solver_twin(4.0, t0, t1, ref.phi, "perturb", eps=0.0, nx=nx, ny=ny)
+    assert d0 == 0.0 and f0 == 0 and m0 < 1e-12     # the mass sums are atomic (order varies)
+    d1, f1, m1, _ = S.solver_twin(4.0, t0, t1, ref.phi, "perturb", eps=1e-6, nx=nx, ny=ny)
+    d2, f2, m2, n2 = S.solver_twin(4.0, t0, t1, ref.phi, "restart", every=2, nx=nx, ny=ny)
+    assert n2 == 1
+    assert np.isfinite([d1, m1, d2, m2]).all() and d2 < 3.0
+    report("surrogate_twins_small", perturbed=d1, restarted=d2, restarted_mass=m2)
+    ref.close()
