@@ -657,7 +657,7 @@ def main():
                     help="population storage format (arithmetic is float32); default fp32 for the "
                          "jet, fp16 for the sweep")
     ap.add_argument("--workload", default="jet", choices=["jet", "rt2d", "sweep", "learned", "jet-sweep"])
-    ap.add_argument("--epochs", type=int, default=8, help="training epochs of the learned workload")
+    ap.add_argument("--epochs", type=int, default=24, help="training epochs of the learned workload")
     ap.add_argument("--skip", type=int, default=1, help="windows predicted after each passing check (learned)")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
                     help="reduced grid of the same jet workload (profiling captures); for rt2d NX "

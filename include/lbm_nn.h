@@ -108,6 +108,18 @@ int lbm_nn_coarsen(const float* phi, const float* u, const float* v, int32_t hf,
 int lbm_nn_refine(const float* pred, int32_t hc, int32_t wc, int32_t factor, float u_scale, float u_max, float* phi,
                   float* u, float* v, void* stream);
 
+/* Re-sharpening of a phase field refined from a coarse grid (n values, in
+ * place): phi <- 1/2 + 1/2 tanh(ratio atanh(2 q - 1)), q = phi clamped to
+ * [1e-6, 1 - 1e-6].  A tanh interface profile of width W' becomes one of
+ * width W' / ratio with the same phi = 1/2 level set; for a profile of width W
+ * coarse-grained by 4 and refined bilinearly ratio ~ 1.35 restores W.
+ * Restarting the solver from a field refined from a coarse grid otherwise
+ * starts from a too-wide interface (the phase-field equation of
+ * eq:lbe_interface relaxes it back, moving the interface while it does).
+ * No counterpart in the paper.  Errors: LBM_NN_ERR_ARG (null, n < 1,
+ * ratio <= 0). */
+int lbm_nn_sharpen(float* phi, int64_t n, float ratio, void* stream);
+
 /* Interface-localised mass projection of a phase field (n values): phi +=
  * c 4 q (1 - q), q = phi clamped to [0, 1], with c such that sum phi =
  * target before rounding (the correction vanishes in the pure phases).  sums: 2 doubles of scratch; on

@@ -105,11 +105,13 @@ struct StoreF32 {
 
 // The conversions use explicitly rounded operations (no contraction into a
 // neighbouring multiply-add), so that every kernel that stores or loads a
-// population rounds it the same way.
+// population rounds it the same way.  g is decoded as one fma: h + 1/2 is
+// exact in float32 for every 16-bit h and w/2 is exact, so
+// fma(w, h, w/2) = round(w (h + 1/2)).
 struct StoreF16 {
     using T = __half;
     __device__ static float f(T v, float wa, const DevParams& P) { return __fmul_rn(__half2float(v), wa * P.inv_fscale); }
-    __device__ static float g(T v, float wa) { return __fmul_rn(wa, __fadd_rn(__half2float(v), 0.5f)); }
+    __device__ static float g(T v, float wa) { return __fmaf_rn(wa, __half2float(v), 0.5f * wa); }
     __device__ static T ef(float v, float wa, const DevParams& P) { return __float2half_rn(__fmul_rn(v, P.fscale / wa)); }
     __device__ static T eg(float v, float wa) { return __float2half_rn(__fmaf_rn(v, 1.0f / wa, -0.5f)); }
 };
@@ -117,7 +119,7 @@ struct StoreF16 {
 struct StoreBF16 {
     using T = __nv_bfloat16;
     __device__ static float f(T v, float wa, const DevParams& P) { return __fmul_rn(__bfloat162float(v), wa * P.inv_fscale); }
-    __device__ static float g(T v, float wa) { return __fmul_rn(wa, __fadd_rn(__bfloat162float(v), 0.5f)); }
+    __device__ static float g(T v, float wa) { return __fmaf_rn(wa, __bfloat162float(v), 0.5f * wa); }
     __device__ static T ef(float v, float wa, const DevParams& P) { return __float2bfloat16_rn(__fmul_rn(v, P.fscale / wa)); }
     __device__ static T eg(float v, float wa) { return __float2bfloat16_rn(__fmaf_rn(v, 1.0f / wa, -0.5f)); }
 };

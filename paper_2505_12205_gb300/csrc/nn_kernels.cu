@@ -423,6 +423,19 @@ __global__ void k_mass_apply(float* __restrict__ phi, int64_t n, double target, 
     phi[i] = p + c * 4.0f * q * (1.0f - q);
 }
 
+// Re-sharpening of a phase field whose interface profile is wider than the
+// equilibrium one (a field refined from a coarse grid): phi <- 1/2 +
+// 1/2 tanh(ratio atanh(2 q - 1)), q = phi clamped to [eps, 1 - eps].  On the
+// profile 1/2 + 1/2 tanh(2 x / W') this gives the profile of width W' / ratio
+// with the same phi = 1/2 crossing.
+__global__ void k_sharpen(float* __restrict__ phi, int64_t n, float ratio)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float q = fminf(fmaxf(phi[i], 1e-6f), 1.0f - 1e-6f);
+    phi[i] = 0.5f + 0.5f * tanhf(ratio * atanhf(2.0f * q - 1.0f));
+}
+
 // Interface comparison of two phase fields on an ny x nx grid:
 // out[0] += cells where (a > 1/2) != (b > 1/2); out[1] += grid edges
 // (x- and y-neighbours, periodic in x) across which b crosses 1/2;
@@ -651,6 +664,13 @@ int lbm_nn_refine(const float* pred, int32_t hc, int32_t wc, int32_t factor, flo
     k_refine<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(pred, hc, wc, factor, 1.0f / u_scale,
                                                                                u_max, phi, u, v);
     return nn_launch_status("refine");
+}
+
+int lbm_nn_sharpen(float* phi, int64_t n, float ratio, void* stream)
+{
+    if (!phi || n < 1 || !(ratio > 0.0f)) return nn_fail(LBM_NN_ERR_ARG, "sharpen: bad arguments");
+    k_sharpen<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(phi, n, ratio);
+    return nn_launch_status("sharpen");
 }
 
 int lbm_nn_mass_project(float* phi, int64_t n, double target, double* sums, void* stream)

@@ -24,7 +24,7 @@ from . import lbm as _lbm
 LBM_NN_OK, LBM_NN_ERR_ARG, LBM_NN_ERR_CUDA = 0, -1, -2
 NN_EXPORTS = ["lbm_nn_last_error", "lbm_nn_conv_fwd", "lbm_nn_conv_wgrad", "lbm_nn_flip_weights", "lbm_nn_relu_bwd",
               "lbm_nn_pool", "lbm_nn_pool_bwd", "lbm_nn_upsample", "lbm_nn_upsample_bwd", "lbm_nn_mse", "lbm_nn_adam",
-              "lbm_nn_to_bf16", "lbm_nn_add", "lbm_nn_coarsen", "lbm_nn_refine", "lbm_nn_mass_project",
+              "lbm_nn_to_bf16", "lbm_nn_add", "lbm_nn_coarsen", "lbm_nn_refine", "lbm_nn_sharpen", "lbm_nn_mass_project",
               "lbm_nn_interface_stats", "lbm_nn_jet_length"]
 
 _lib = None
@@ -55,6 +55,7 @@ def load():
         "lbm_nn_add": [vp, i32, i32, vp, i32, i32, i32, i64, vp],
         "lbm_nn_coarsen": [fp, fp, fp, i32, i32, i32, f32, f32, vp, i32, fp, vp],
         "lbm_nn_refine": [fp, i32, i32, i32, f32, f32, fp, fp, fp, vp],
+        "lbm_nn_sharpen": [fp, i64, ctypes.c_float, vp],
         "lbm_nn_mass_project": [fp, i64, ctypes.c_double, fp, vp],
         "lbm_nn_interface_stats": [fp, fp, i32, i32, fp, vp],
         "lbm_nn_jet_length": [fp, fp, i32, i32, i32, i32, fp, vp],

@@ -8,8 +8,9 @@ writes snapshots every K steps; the network sees them 4x coarse-grained
 predicts the coarse fields K steps later.
 
 The solver is both the fallback and the judge.  A prediction is refined to
-the solver grid (bilinear), its phase field is corrected towards the mass
-budget by a correction localised on the interface, and the solver restarts
+the solver grid (bilinear), its interface re-sharpened to the equilibrium
+width, its phase field corrected towards the mass budget by a correction
+localised on the interface, and the solver restarts
 from it (equilibrium populations, p* = 0, which the solver re-equilibrates).
 It is accepted when the interface-position error is at most
 ``interface_bound`` cells of the solver grid -- both the mean distance
@@ -46,6 +47,11 @@ U_SCALE = 20.0        # velocities are scaled to O(1) for the network (u_j = 0.0
 CIN = 8               # input channels: phi, u, v, Weber, zero padding
 NOZZLE_HALF = 16      # half width of the inlet slot (lbm_cases.jet2d)
 U_MAX = 0.15          # speed limit of a restart state (3 u_j)
+# Width ratio of the phi = 1/2 interface profile after 4x box coarse-graining
+# and bilinear refinement to that of the tanh profile of width W = 5 it came
+# from (1.32 .. 1.39 over the sub-cell offsets of the interface); the restart
+# re-sharpens the refined field by it (lbm_nn_sharpen).
+SHARPEN = 1.35
 
 
 def we_cond(We: float) -> float:
@@ -90,14 +96,25 @@ class Case:
 
     def restart_from(self, pred, mass_target):
         """Solver state from a coarse prediction pred (f32 [m][3]): refined,
-        mass-projected, equilibrium populations with p* = 0."""
-        nn.call("lbm_nn_refine", nn._p(pred), self.hc, self.wc, FACTOR, U_SCALE, U_MAX, nn._p(self.phi),
-                nn._p(self.u[:self.N]), nn._p(self.u[self.N:]), nn._s(self.stream))
-        nn.call("lbm_nn_mass_project", nn._p(self.phi), self.N, float(mass_target), nn._p(self.sums), nn._s(self.stream))
+        re-sharpened, mass-projected, equilibrium populations with p* = 0."""
+        restart_fields(pred, self.hc, self.wc, mass_target, self.phi, self.u, self.sums, self.stream)
         lbm.lbm_init_fields(self.sim._h, self.phi, self.u, None, n=self.N, dim=2)
 
     def mass(self):
         return float(self.sim.diag()["sum_phi"])
+
+
+def restart_fields(pred, hc, wc, mass_target, phi, u, sums, stream=None):
+    """The solver-grid fields a restart starts from, given a coarse prediction
+    pred (f32 [hc * wc][3]): bilinear refinement (phi clamped to [0, 1],
+    speed limited to U_MAX), the interface re-sharpened to the equilibrium
+    width, and phi projected onto mass_target by an interface-localised
+    correction.  phi: [N], u: [2 N] device buffers; sums: 2 doubles of scratch."""
+    n = phi.numel()
+    nn.call("lbm_nn_refine", nn._p(pred), hc, wc, FACTOR, U_SCALE, U_MAX, nn._p(phi), nn._p(u[:n]),
+            nn._p(u[n:]), nn._s(stream))
+    nn.call("lbm_nn_sharpen", nn._p(phi), n, SHARPEN, nn._s(stream))
+    nn.call("lbm_nn_mass_project", nn._p(phi), n, float(mass_target), nn._p(sums), nn._s(stream))
 
 
 def interface_stats(phi_a, phi_b, ny, nx, out, stream=None):
@@ -279,14 +296,13 @@ def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, 
             windows["skipped"] += 1
             trusted -= 1
             continue
-        # solver window, which also judges the network's prediction of it
-        nn.call("lbm_nn_refine", nn._p(A["pred"]), H, W, FACTOR, U_SCALE, U_MAX, nn._p(phi_pred), nn._p(u_pred[:ff.N]),
-                nn._p(u_pred[ff.N:]), nn._s(stream))
+        # solver window, which also judges the network's prediction of it (the
+        # fields a restart from the prediction would start from)
         ff.step(K)
         windows["solver"] += 1
         m1 = ff.mass()
         rate = (m1 - m0) / K
-        nn.call("lbm_nn_mass_project", nn._p(phi_pred), ff.N, m1, nn._p(out), nn._s(stream))
+        restart_fields(A["pred"], H, W, m1, phi_pred, u_pred, out, stream)
         ff.read_fields()
         dist, sa, sb = interface_stats(phi_pred, ff.phi, ff.ny, ff.nx, out, stream)
         front = front_error(phi_pred, ff.phi, ff.ny, ff.nx, iout, stream)

@@ -41,6 +41,21 @@ def test_coarsen_refine_mass_and_interface_kernels(env):
     nn.call("lbm_nn_refine", nn._p(xf), ny // f, nx // f, f, 20.0, 1.0, nn._p(pf), nn._p(uf), nn._p(vf), None)
     assert np.allclose(vf.cpu().numpy(), 0.02, atol=1e-7)                             # constants survive
     assert np.abs(pf.cpu().numpy() - phi.reshape(-1)).mean() < 0.05                   # smooth field, 4x coarse
+    # re-sharpening: the formula of include/lbm_nn.h in float64, the phi = 1/2
+    # level set kept, a coarse-grained and refined tanh profile brought back
+    # to its width
+    xs = np.linspace(-12.0, 12.0, 4001)
+    prof = (0.5 + 0.5 * np.tanh(2.0 * xs / (5.0 * 1.35))).astype(np.float32)
+    sd = d(prof)
+    nn.call("lbm_nn_sharpen", nn._p(sd), prof.size, 1.35, None)
+    q = np.clip(prof.astype(np.float64), 1e-6, 1 - 1e-6)
+    ref_s = 0.5 + 0.5 * np.tanh(1.35 * np.arctanh(2 * q - 1))
+    got_s = sd.cpu().numpy()
+    assert np.abs(got_s - ref_s).max() < 2e-6
+    assert np.abs(got_s - (0.5 + 0.5 * np.tanh(2.0 * xs / 5.0))).max() < 2e-6
+    half = d(np.full(7, 0.5, np.float32))
+    nn.call("lbm_nn_sharpen", nn._p(half), 7, 1.35, None)
+    assert np.all(half.cpu().numpy() == 0.5)
     # mass projection onto the interface band
     sums = torch.zeros(2, dtype=torch.float64, device="cuda")
     target = float(phi.sum()) * 1.01
