@@ -139,8 +139,12 @@ int lbm_init_fields(lbm_ctx* ctx, const float* phi, const float* u, const float*
                     int on_device);
 
 /* Advance nsteps >= 0 time steps (collision, streaming, boundary conditions
- * and macroscopic update of Algorithms 1-3, fused).  Asynchronous.
- * Errors: LBM_ERR_STATE before lbm_init_fields / lbm_set_populations. */
+ * and macroscopic update of Algorithms 1-3, fused).  Asynchronous.  Runs of
+ * 16 steps are replayed as one CUDA graph (captured on first use, kept until
+ * lbm_destroy; not while kernel timing is on), the rest launched one by one;
+ * the results are the same either way.
+ * Errors: LBM_ERR_STATE before lbm_init_fields / lbm_set_populations;
+ * LBM_ERR_CUDA when a launch or the graph capture fails. */
 int lbm_step(lbm_ctx* ctx, int64_t nsteps);
 
 /* Macroscopic fields of the current state, computed with the same device

@@ -67,8 +67,18 @@ struct lbm_ctx {
     bool timing = false;
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
+    // lbm_step replays kStepGraph steps as one CUDA graph, captured on first
+    // use for each assignment of the allocations to A and B (f and g swap
+    // together in a step; lbm_advect_phase swaps g alone), on a private
+    // stream, and launched on the context's stream
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* f0 = nullptr;             // the f and g allocations that start as A
+    void* g0 = nullptr;
+    cudaStream_t cap = nullptr;
     std::string err;
 };
+
+constexpr int64_t kStepGraph = 16;  // steps per graph replay (even: A and B end where they began)
 
 static thread_local std::string g_create_err;
 
@@ -194,6 +204,33 @@ static cudaError_t dispatch_step(lbm_ctx* c)
     return e;
 }
 
+// Capture kStepGraph steps from the current assignment of A and B into
+// c->graph[slot].  Nothing runs during the capture; the buffer pointers are
+// restored whatever happens.
+static int capture_steps(lbm_ctx* c, int slot)
+{
+    if (!c->cap) LBM_CUDA(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    const lbm::Buffers saved = c->b;
+    cudaStream_t user = c->stream;
+    c->stream = c->cap;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (int64_t s = 0; s < kStepGraph && e == cudaSuccess; ++s) e = dispatch_step(c);
+        const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    c->stream = user;
+    c->b = saved;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[slot], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph[slot] = nullptr;
+        return cuda_fail(c, e, "step graph");
+    }
+    return LBM_OK;
+}
+
 // Entry points for the other translation units of the library.
 namespace lbm {
 int api_validate(const lbm_params* p, std::string& why) { return validate(p, why); }
@@ -237,6 +274,8 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
             return r;
         }
     }
+    c->f0 = c->b.fA;
+    c->g0 = c->b.gA;
     e = cudaMalloc(reinterpret_cast<void**>(&c->b.phi), size_t(c->N) * sizeof(float));
     const int nface = c->D == 2 ? p->nx : p->nx * p->ny;
     if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&c->face), (2 * size_t(nface) + 1) * sizeof(float));
@@ -279,6 +318,9 @@ int lbm_destroy(lbm_ctx* c)
 {
     if (!c) return LBM_OK;
     cudaStreamSynchronize(c->stream);
+    for (cudaGraphExec_t g : c->graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (c->cap) cudaStreamDestroy(c->cap);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     cudaFree(c->b.fA); cudaFree(c->b.gA); cudaFree(c->b.fB); cudaFree(c->b.gB);
     cudaFree(c->b.phi); cudaFree(c->face); cudaFree(c->diag_part); cudaFree(c->staging); cudaFree(c->uadv);
@@ -360,6 +402,17 @@ int lbm_step(lbm_ctx* c, int64_t nsteps)
     if (!c) return LBM_ERR_ARG;
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps < 0");
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_fields/lbm_set_populations");
+    // whole graphs of kStepGraph steps (not while kernel timing is on: its
+    // events are recorded between the launches), then single steps
+    while (!c->timing && nsteps >= kStepGraph) {
+        const int slot = (c->b.fA == c->f0 ? 0 : 1) | (c->b.gA == c->g0 ? 0 : 2);
+        if (!c->graph[slot]) {
+            const int r = capture_steps(c, slot);
+            if (r != LBM_OK) return r;
+        }
+        LBM_CUDA(c, cudaGraphLaunch(c->graph[slot], c->stream));
+        nsteps -= kStepGraph;
+    }
     for (int64_t s = 0; s < nsteps; ++s) {
         cudaError_t e = dispatch_step(c);
         if (e != cudaSuccess) return cuda_fail(c, e, "step kernels");
