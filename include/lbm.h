@@ -141,8 +141,9 @@ int lbm_init_fields(lbm_ctx* ctx, const float* phi, const float* u, const float*
 /* Advance nsteps >= 0 time steps (collision, streaming, boundary conditions
  * and macroscopic update of Algorithms 1-3, fused).  Asynchronous.  Runs of
  * 16 steps are replayed as one CUDA graph (captured on first use, kept until
- * lbm_destroy; not while kernel timing is on), the rest launched one by one;
- * the results are the same either way.
+ * lbm_destroy; not while kernel timing is on, nor after a capture was
+ * refused, e.g. inside the caller's own global-mode stream capture), the rest
+ * launched one by one; the results are the same either way.
  * Errors: LBM_ERR_STATE before lbm_init_fields / lbm_set_populations;
  * LBM_ERR_CUDA when a launch or the graph capture fails. */
 int lbm_step(lbm_ctx* ctx, int64_t nsteps);
@@ -314,8 +315,10 @@ int lbm_batch_diag(lbm_batch* b, int32_t c, double phase_eps, lbm_diag_out* out)
 int lbm_batch_get_plan(const lbm_batch* b, lbm_batch_plan* plan);
 int lbm_batch_set_plan(lbm_batch* b, const lbm_batch_plan* plan);
 
-/* Autotuner: for every class, time each candidate (tile width, planes per
- * item, blocks per SM) over trial_steps launches of that class alone (one
+/* Autotuner: for every class, time each candidate (tile width 32, 64, 128
+ * for D2Q9; planes per item 4, 16, 64 for D2Q9 and 4, 8, 16, 32 for D3Q19;
+ * blocks per SM: the occupancy and half of it) over trial_steps launches of
+ * that class alone (one
  * step from the current state, repeated: the state is not advanced), keep
  * the fastest, and return the resulting plan (may be NULL).  Synchronises. */
 int lbm_batch_tune(lbm_batch* b, int32_t trial_steps, lbm_batch_plan* plan);

@@ -75,6 +75,7 @@ struct lbm_ctx {
     void* f0 = nullptr;             // the f and g allocations that start as A
     void* g0 = nullptr;
     cudaStream_t cap = nullptr;
+    bool no_graphs = false;         // a capture was refused: launch step by step
     std::string err;
 };
 
@@ -206,10 +207,18 @@ static cudaError_t dispatch_step(lbm_ctx* c)
 
 // Capture kStepGraph steps from the current assignment of A and B into
 // c->graph[slot].  Nothing runs during the capture; the buffer pointers are
-// restored whatever happens.
-static int capture_steps(lbm_ctx* c, int slot)
+// restored whatever happens.  Returns the CUDA status (the caller falls back
+// to single launches of the same kernels when the capture is refused, e.g.
+// inside a caller's own global-mode stream capture).
+static cudaError_t capture_steps(lbm_ctx* c, int slot)
 {
-    if (!c->cap) LBM_CUDA(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    if (!c->cap) {
+        const cudaError_t ec = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+        if (ec != cudaSuccess) {
+            c->cap = nullptr;
+            return ec;
+        }
+    }
     const lbm::Buffers saved = c->b;
     cudaStream_t user = c->stream;
     c->stream = c->cap;
@@ -224,11 +233,8 @@ static int capture_steps(lbm_ctx* c, int slot)
     c->b = saved;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[slot], g, 0);
     if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-        c->graph[slot] = nullptr;
-        return cuda_fail(c, e, "step graph");
-    }
-    return LBM_OK;
+    if (e != cudaSuccess) c->graph[slot] = nullptr;
+    return e;
 }
 
 // Entry points for the other translation units of the library.
@@ -404,11 +410,12 @@ int lbm_step(lbm_ctx* c, int64_t nsteps)
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_fields/lbm_set_populations");
     // whole graphs of kStepGraph steps (not while kernel timing is on: its
     // events are recorded between the launches), then single steps
-    while (!c->timing && nsteps >= kStepGraph) {
+    while (!c->timing && !c->no_graphs && nsteps >= kStepGraph) {
         const int slot = (c->b.fA == c->f0 ? 0 : 1) | (c->b.gA == c->g0 ? 0 : 2);
-        if (!c->graph[slot]) {
-            const int r = capture_steps(c, slot);
-            if (r != LBM_OK) return r;
+        if (!c->graph[slot] && capture_steps(c, slot) != cudaSuccess) {
+            cudaGetLastError();                 // a refused capture leaves no sticky error
+            c->no_graphs = true;
+            break;
         }
         LBM_CUDA(c, cudaGraphLaunch(c->graph[slot], c->stream));
         nsteps -= kStepGraph;

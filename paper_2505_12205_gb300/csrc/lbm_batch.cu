@@ -520,7 +520,7 @@ int lbm_batch_tune(lbm_batch* b, int32_t trial_steps, lbm_batch_plan* plan)
     for (size_t k = 0; k < b->cls.size() && rc == LBM_OK; ++k) {
         lbm_batch::Class& c = b->cls[k];
         std::vector<int> txs = b->D == 3 ? std::vector<int>{32} : std::vector<int>{32, 64, 128};
-        std::vector<int> segs = b->D == 3 ? std::vector<int>{8, 16, 32} : std::vector<int>{16, 64};
+        std::vector<int> segs = b->D == 3 ? std::vector<int>{4, 8, 16, 32} : std::vector<int>{4, 16, 64};
         double best = 1e300;
         int btx = c.tx, bseg = c.seglen, bbps = c.bps;
         for (int tx : txs) {

@@ -1420,13 +1420,17 @@ cudaError_t Launch<L, S>::fused_geom(const DevParams& P, FusedGeom* G, int* nblo
     G->tiles_y = (L::D == 3) ? (P.ny + TY - 1) / TY : 1;
     G->ntiles = G->tiles_x * G->tiles_y;
     const int nm = (L::D == 3) ? P.nz : P.ny;
-    // segments: at least 16 planes each, and items a multiple of the slots
-    // when that is possible, so every persistent block gets equal work
+    // segments: the count that maximises the useful share of the slots'
+    // work (items a multiple of the slots when that is possible, so every
+    // persistent block gets equal work; each segment re-forms phi of two
+    // extra planes); at least 2 planes each, so that a small grid is cut into
+    // enough items to fill the GPU (a 128 x 128 grid: 128 items of 2 planes,
+    // 4.5x faster per step than 16 items of 16 planes)
     int best = 1;
     double best_eff = -1.0;
     for (int nseg = 1; nseg <= nm; ++nseg) {
         const int seglen = (nm + nseg - 1) / nseg;
-        if (seglen < 16 && nseg > 1) break;
+        if (seglen < 2 && nseg > 1) break;
         const long items = long(G->ntiles) * nseg;
         const long rounds = (items + slots - 1) / slots;
         const double work = double(nm + 2 * nseg);          // planes incl. the 2-plane prologue
