@@ -595,7 +595,8 @@ def run_learned(args):
                   "generate_seconds": t_gen},
         "held_out": {"loss": val, "persistence_loss": pers},
         "per_case": [{k: v for k, v in x.items() if k != "judged"} for x in res],
-        "judged_windows": [[{k: round(v, 4) for k, v in j.items()} for j in x["judged"]] for x in res],
+        "judged_windows": [[{k: (round(v, 4) if v is not None else None) for k, v in j.items()} for j in x["judged"]]
+                           for x in res],
     }
     print(json.dumps(line))
     return 0

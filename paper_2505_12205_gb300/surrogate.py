@@ -296,17 +296,20 @@ def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, 
             windows["skipped"] += 1
             trusted -= 1
             continue
-        # solver window, which also judges the network's prediction of it (the
-        # fields a restart from the prediction would start from)
+        # solver window, which also judges the network's prediction of it: the
+        # fields a restart from the prediction would start from, with the mass
+        # a skip would take (the budget extrapolated from the previous solver
+        # window; none before the first, which therefore cannot pass)
         ff.step(K)
         windows["solver"] += 1
         m1 = ff.mass()
-        rate = (m1 - m0) / K
-        restart_fields(A["pred"], H, W, m1, phi_pred, u_pred, out, stream)
+        target = m1 if rate is None else m0 + K * rate
+        restart_fields(A["pred"], H, W, target, phi_pred, u_pred, out, stream)
         ff.read_fields()
         dist, sa, sb = interface_stats(phi_pred, ff.phi, ff.ny, ff.nx, out, stream)
         front = front_error(phi_pred, ff.phi, ff.ny, ff.nx, iout, stream)
-        merr = abs(sa - sb) / max(abs(sb), 1e-30)
+        merr = abs(sa - sb) / max(abs(sb), 1e-30) if rate is not None else float("inf")
+        rate = (m1 - m0) / K
         ok = dist <= interface_bound and front <= interface_bound and merr <= mass_bound
         errs.append((dist, front, merr))
         windows["checked_pass" if ok else "checked_fail"] += 1
@@ -322,7 +325,7 @@ def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, 
                final_mass_error=abs(sa - sb) / max(abs(sb), 1e-30), windows=windows,
                accepted_at_end=bool(dist_end <= interface_bound and front_end <= interface_bound
                                     and abs(sa - sb) / max(abs(sb), 1e-30) <= mass_bound),
-               judged=[dict(interface=d, front=f, mass=e) for d, f, e in errs])
+               judged=[dict(interface=d, front=f, mass=e if np.isfinite(e) else None) for d, f, e in errs])
     if twins:
         for mode in ("perturb", "restart"):
             d, f, e, n = solver_twin(We, t0, t1, ref.phi, mode, every=skip + 1, nx=nx, ny=ny, stream=stream)
