@@ -71,6 +71,7 @@ RT_WORKLOAD = dict(name="rt2d_D2Q9_8192x32768", L=256, periods=32, height=32768)
 SAMPLE_RT_HEIGHT = 64  # strip of the same workload for the CPU oracle
 BYTES_PER_LU = 4 * 19 * 4   # f and g read + written once, float32, D3Q19
 METRIC = "MLUPS"
+NOMINAL_HBM_GBS = 7900.0    # HBM3e nominal bandwidth of one GB300 (the measured copy peak is the roofline)
 
 
 def peaks():
@@ -343,7 +344,7 @@ def run_gpu(args):
     bytes_per_lu = 4 * Q * elem
     achieved = bytes_per_lu * N / (step_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak,
+            "frac": achieved / peak, "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS,
             "traffic": ncu_traffic(args.workload) if (args.storage == "fp32" and not args.grid) else None,
             "kernel": kname,
             "algorithmic_bytes_per_lu": bytes_per_lu, "peak_source": peak_kind + " hbm_gbs",
@@ -528,7 +529,8 @@ def run_sweep(args):
                       "note": "one context per case, every case stepped in turn (one launch per case and step)"},
             "speedup_vs_plain": cph / cph_plain,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS,
+                         "traffic": None,
                          "kernel": "k_step_batch<D2Q9> (all classes of one step, concurrent)",
                          "algorithmic_bytes_per_lu": bytes_per_lu, "peak_source": peak_kind + " hbm_gbs"},
             "e2e": {"value": ws * ncases * 3600.0 / (te2e / args.steps * SWEEP["steps_per_case"]),
