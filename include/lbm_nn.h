@@ -39,7 +39,11 @@ const char* lbm_nn_last_error(void);
 
 /* y[m][y_offset + co] (bf16, may be NULL) and yf[m][co] (f32, may be NULL) =
  * relu?(sum_k patch(x)[m][k] wt[co][k] + bias[co]) for the nb * h * w
- * positions; bias may be NULL. */
+ * positions; bias may be NULL.  When the output tiles alone would leave most
+ * of the GPU idle (few positions, many channels), the k range is split over
+ * blocks: their float32 partial sums go to scratch allocated on `stream`
+ * (cudaMallocAsync, at most 16 MB, freed on `stream`) and are added in a fixed
+ * order, so results do not depend on scheduling. */
 int lbm_nn_conv_fwd(const void* x, int32_t x_stride, int32_t ci, int32_t taps, const void* wt, const float* bias,
                     int32_t co, void* y, int32_t y_stride, int32_t y_offset, float* yf, int32_t yf_stride,
                     int32_t relu, int32_t nb, int32_t h, int32_t w, void* stream);

@@ -11,6 +11,7 @@
 // and transposed in channels; the weight gradient dW[co][k] = sum_m dZ[m][co]
 // A[m][k] reduces over the spatial positions, split over blocks, with float32
 // atomics.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -87,12 +88,15 @@ __device__ __forceinline__ uint4 patch8(const bf16* __restrict__ X, int xs, int 
 __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, int xs, int ci, int taps,
                                                   const bf16* __restrict__ Wt, const float* __restrict__ bias,
                                                   int co, bf16* __restrict__ Y, int ys, int yo,
-                                                  float* __restrict__ Yf, int yfs, int relu, int M, int H, int W)
+                                                  float* __restrict__ Yf, int yfs, int relu, int M, int H, int W,
+                                                  int kchunk, float* __restrict__ part)
 {
     __shared__ __align__(16) bf16 As[BM][LDS];
     __shared__ __align__(16) bf16 Bs[BN][LDS];
     const int K = taps * ci;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    // this block's range of k: all of it, or split z of a split-K launch
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, wm = warp >> 1, wn = warp & 1;
     float acc[2][4][4];
 #pragma unroll
@@ -101,18 +105,37 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, in
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int v = tid; v < BM * (BK / 8); v += 128) {
-            const int r = v / (BK / 8), q = v % (BK / 8);
-            *reinterpret_cast<uint4*>(&As[r][q * 8]) = patch8(X, xs, ci, taps, m0 + r, k0 + q * 8, M, K, H, W);
+    // the next k tile's 16-byte vectors are loaded into registers while the
+    // tensor cores work on the current one
+    constexpr int NA = BM * (BK / 8) / 128, NB = BN * (BK / 8) / 128;
+    uint4 ra[NA], rb[NB];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            const int v = tid + i * 128, r = v / (BK / 8), q = v % (BK / 8);
+            ra[i] = patch8(X, xs, ci, taps, m0 + r, k0 + q * 8, M, K, H, W);
         }
-        for (int v = tid; v < BN * (BK / 8); v += 128) {
-            const int r = v / (BK / 8), q = v % (BK / 8), n = n0 + r, k = k0 + q * 8;
-            uint4 w = make_uint4(0u, 0u, 0u, 0u);
-            if (n < co && k < K) w = *reinterpret_cast<const uint4*>(Wt + int64_t(n) * K + k);
-            *reinterpret_cast<uint4*>(&Bs[r][q * 8]) = w;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int v = tid + i * 128, r = v / (BK / 8), q = v % (BK / 8), n = n0 + r, k = k0 + q * 8;
+            rb[i] = (n < co && k < K) ? *reinterpret_cast<const uint4*>(Wt + int64_t(n) * K + k)
+                                      : make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    load(kb);
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            const int v = tid + i * 128, r = v / (BK / 8), q = v % (BK / 8);
+            *reinterpret_cast<uint4*>(&As[r][q * 8]) = ra[i];
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int v = tid + i * 128, r = v / (BK / 8), q = v % (BK / 8);
+            *reinterpret_cast<uint4*>(&Bs[r][q * 8]) = rb[i];
         }
         __syncthreads();
+        if (k0 + BK < ke) load(k0 + BK);
         tile_mma(As, Bs, acc, wm, wn, lane);
         __syncthreads();
     }
@@ -126,11 +149,32 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, in
                 const int m = m0 + wm * 32 + i * 16 + g + (e >= 2 ? 8 : 0);
                 const int n = n0 + wn * 32 + j * 8 + 2 * t + (e & 1);
                 if (m >= M || n >= co) continue;
+                if (part) {                   // split-K: the raw partial sum of this k range
+                    part[(int64_t(blockIdx.z) * M + m) * co + n] = acc[i][j][e];
+                    continue;
+                }
                 float v = acc[i][j][e] + (bias ? bias[n] : 0.0f);
                 if (relu) v = fmaxf(v, 0.0f);
                 if (Y) Y[int64_t(m) * ys + yo + n] = __float2bfloat16_rn(v);
                 if (Yf) Yf[int64_t(m) * yfs + n] = v;
             }
+}
+
+// Sum of the split-K partial sums part[z][m][n] in the order z = 0, 1, ...
+// (deterministic), then bias, ReLU and the outputs of k_conv_fwd.
+__global__ void k_conv_reduce(const float* __restrict__ part, int splits, int M, int co,
+                              const float* __restrict__ bias, int relu, bf16* __restrict__ Y, int ys, int yo,
+                              float* __restrict__ Yf, int yfs)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= int64_t(M) * co) return;
+    const int m = int(i / co), n = int(i % co);
+    float v = part[i];
+    for (int z = 1; z < splits; ++z) v += part[int64_t(z) * M * co + i];
+    v += bias ? bias[n] : 0.0f;
+    if (relu) v = fmaxf(v, 0.0f);
+    if (Y) Y[int64_t(m) * ys + yo + n] = __float2bfloat16_rn(v);
+    if (Yf) Yf[int64_t(m) * yfs + n] = v;
 }
 
 // dWt[co][k] += sum over this block's positions of dZ[m][co] A[m][k]
@@ -503,6 +547,9 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 unsigned blocks_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
 
+constexpr int kTargetBlocks = 2 * 152;                  // two 128-thread blocks per SM of a GB300
+constexpr int64_t kConvWsFloats = int64_t(1) << 22;     // largest split-K workspace (16 MB)
+
 }  // namespace
 
 extern "C" {
@@ -519,11 +566,36 @@ int lbm_nn_conv_fwd(const void* x, int32_t x_stride, int32_t ci, int32_t taps, c
     if (!aligned16(x) || !aligned16(wt)) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: x and wt must be 16-byte aligned");
     if (y && (y_offset < 0 || y_offset + co > y_stride)) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: output channels exceed the stride");
     if (yf && yf_stride < co) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: f32 output stride below co");
-    const int M = nb * h * w;
-    dim3 grid(blocks_for(M, BM), blocks_for(co, BN));
-    k_conv_fwd<<<grid, 128, 0, static_cast<cudaStream_t>(stream)>>>(
-        static_cast<const bf16*>(x), x_stride, ci, taps, static_cast<const bf16*>(wt), bias, co, static_cast<bf16*>(y),
-        y_stride, y_offset, yf, yf_stride, relu, M, h, w);
+    const int M = nb * h * w, K = taps * ci;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int tiles = blocks_for(M, BM) * blocks_for(co, BN);
+    // Split-K when the output tiles alone leave the GPU mostly idle (the deep,
+    // coarse levels of the network): each split writes its partial sums to a
+    // workspace slice, and k_conv_reduce adds them in split order.
+    int splits = 1;
+    if (tiles < kTargetBlocks && K >= 4 * BK) {
+        splits = std::min((kTargetBlocks + tiles - 1) / tiles, K / (2 * BK));
+        while (splits > 1 && int64_t(splits) * M * co > kConvWsFloats) --splits;
+    }
+    float* ws = nullptr;
+    if (splits > 1) {
+        // stream-ordered scratch: concurrent calls on other streams get their own
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), size_t(splits) * M * co * sizeof(float), s);
+        if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("conv_fwd: workspace: ") + cudaGetErrorString(e));
+    }
+    const int kchunk = splits > 1 ? blocks_for(blocks_for(K, splits), BK) * BK : K;
+    splits = blocks_for(K, kchunk);
+    dim3 grid(blocks_for(M, BM), blocks_for(co, BN), splits);
+    k_conv_fwd<<<grid, 128, 0, s>>>(static_cast<const bf16*>(x), x_stride, ci, taps, static_cast<const bf16*>(wt), bias,
+                                    co, static_cast<bf16*>(y), y_stride, y_offset, yf, yf_stride, relu, M, h, w, kchunk,
+                                    splits > 1 ? ws : nullptr);
+    if (ws) {
+        k_conv_reduce<<<blocks_for(int64_t(M) * co, 256), 256, 0, s>>>(ws, splits, M, co, bias, relu,
+                                                                       static_cast<bf16*>(y), y_stride, y_offset, yf,
+                                                                       yf_stride);
+        const cudaError_t e = cudaFreeAsync(ws, s);
+        if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("conv_fwd: workspace: ") + cudaGetErrorString(e));
+    }
     return nn_launch_status("conv_fwd");
 }
 
