@@ -284,14 +284,19 @@ def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, 
     torch.cuda.synchronize()
     ev0.record(st)
     t_wall = time.perf_counter()
+    # the mass of the current state, tracked on the host: measured after a
+    # solver window, the projection target after a skipped one (a restart
+    # sets sum phi to it), so a skipped window needs no device round trip
+    m_cur = ff.mass()
     while ff.t + K <= t1:
-        m0 = ff.mass()
+        m0 = m_cur
         ff.coarse(x=x)
         A = net.forward(x, 1, H, W)
         if trusted:
             # skip this window: restart from the prediction, mass from the budget
             target = m0 + K * (rate or 0.0)
             ff.restart_from(A["pred"], target)
+            m_cur = target
             ff.t += K
             windows["skipped"] += 1
             trusted -= 1
@@ -303,6 +308,7 @@ def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, 
         ff.step(K)
         windows["solver"] += 1
         m1 = ff.mass()
+        m_cur = m1
         target = m1 if rate is None else m0 + K * rate
         restart_fields(A["pred"], H, W, target, phi_pred, u_pred, out, stream)
         ff.read_fields()
