@@ -604,7 +604,7 @@ def run_learned(args):
     return 0
 
 
-JETSWEEP = dict(We=[1.0, 2.2, 3.5, 5.0], nx=192, ny=192, nz=640, Rn=16.0, steps=24000, sample_from=12000,
+JETSWEEP = dict(We=[1.0, 2.2, 3.5, 5.0], nx=192, ny=192, nz=640, Rn=16.0, steps=48000, sample_from=24000,
                 sample_every=500)
 
 

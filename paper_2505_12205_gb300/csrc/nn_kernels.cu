@@ -85,19 +85,24 @@ __device__ __forceinline__ uint4 patch8(const bf16* __restrict__ X, int xs, int 
 
 // Y[m][yo + co] (bf16, optional) and Yf[m][co] (f32, optional) =
 // relu?(sum_k A[m][k] Wt[co][k] + bias[co])
+// Block tile TM x TN (64 x 64, or 128 x 32 for layers with at most 32 output
+// channels), four warps of 32 x 32 each.
+template <int TM, int TN>
 __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, int xs, int ci, int taps,
                                                   const bf16* __restrict__ Wt, const float* __restrict__ bias,
                                                   int co, bf16* __restrict__ Y, int ys, int yo,
                                                   float* __restrict__ Yf, int yfs, int relu, int M, int H, int W,
                                                   int kchunk, float* __restrict__ part)
 {
-    __shared__ __align__(16) bf16 As[BM][LDS];
-    __shared__ __align__(16) bf16 Bs[BN][LDS];
+    static_assert((TM / 32) * (TN / 32) == 4, "four warps of 32 x 32");
+    constexpr int WN = TN / 32;
+    __shared__ __align__(16) bf16 As[TM][LDS];
+    __shared__ __align__(16) bf16 Bs[TN][LDS];
     const int K = taps * ci;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
     // this block's range of k: all of it, or split z of a split-K launch
     const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, wm = warp >> 1, wn = warp & 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, wm = warp / WN, wn = warp % WN;
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -107,7 +112,7 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, in
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.0f;
     // the next k tile's 16-byte vectors are loaded into registers while the
     // tensor cores work on the current one
-    constexpr int NA = BM * (BK / 8) / 128, NB = BN * (BK / 8) / 128;
+    constexpr int NA = TM * (BK / 8) / 128, NB = TN * (BK / 8) / 128;
     uint4 ra[NA], rb[NB];
     auto load = [&](int k0) {
 #pragma unroll
@@ -568,7 +573,9 @@ int lbm_nn_conv_fwd(const void* x, int32_t x_stride, int32_t ci, int32_t taps, c
     if (yf && yf_stride < co) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: f32 output stride below co");
     const int M = nb * h * w, K = taps * ci;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int tiles = blocks_for(M, BM) * blocks_for(co, BN);
+    const bool narrow = co <= 32;                 // 128 x 32 tiles: no idle half of a 64-wide tile
+    const int TM = narrow ? 128 : BM, TN = narrow ? 32 : BN;
+    const int tiles = blocks_for(M, TM) * blocks_for(co, TN);
     // Split-K when the output tiles alone leave the GPU mostly idle (the deep,
     // coarse levels of the network): each split writes its partial sums to a
     // workspace slice, and k_conv_reduce adds them in split order.
@@ -585,10 +592,11 @@ int lbm_nn_conv_fwd(const void* x, int32_t x_stride, int32_t ci, int32_t taps, c
     }
     const int kchunk = splits > 1 ? blocks_for(blocks_for(K, splits), BK) * BK : K;
     splits = blocks_for(K, kchunk);
-    dim3 grid(blocks_for(M, BM), blocks_for(co, BN), splits);
-    k_conv_fwd<<<grid, 128, 0, s>>>(static_cast<const bf16*>(x), x_stride, ci, taps, static_cast<const bf16*>(wt), bias,
-                                    co, static_cast<bf16*>(y), y_stride, y_offset, yf, yf_stride, relu, M, h, w, kchunk,
-                                    splits > 1 ? ws : nullptr);
+    dim3 grid(blocks_for(M, TM), blocks_for(co, TN), splits);
+    auto kern = narrow ? k_conv_fwd<128, 32> : k_conv_fwd<BM, BN>;
+    kern<<<grid, 128, 0, s>>>(static_cast<const bf16*>(x), x_stride, ci, taps, static_cast<const bf16*>(wt), bias, co,
+                              static_cast<bf16*>(y), y_stride, y_offset, yf, yf_stride, relu, M, h, w, kchunk,
+                              splits > 1 ? ws : nullptr);
     if (ws) {
         k_conv_reduce<<<blocks_for(int64_t(M) * co, 256), 256, 0, s>>>(ws, splits, M, co, bias, relu,
                                                                        static_cast<bf16*>(y), y_stride, y_offset, yf,
