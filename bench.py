@@ -29,6 +29,10 @@ x on an 8192 x 32768 domain (268 M nodes, 38.7 GB of float32 populations).
 network trained on the GPU by the library's kernels, then held-out cases run
 with the network in the loop against the solver alone.
 
+`--workload nn` times the learned fast-forward's network alone (inference and
+one training step on a 128 x 512 coarse field) against the measured bf16
+tensor peak.
+
 `--workload jet-sweep` runs the 3D jet of the application section in the
 paper's domain shape (6D x 6D x 20D, D = 32: 192 x 192 x 640, free-slip
 sides, plug inlet, convective outlet) for Weber numbers around the critical
@@ -604,6 +608,79 @@ def run_learned(args):
     return 0
 
 
+def unet_flops(cin, ch, head, H, W):
+    """Multiply-adds x 2 of one forward pass of the encoder-decoder (3x3
+    convolutions with zero padding, 1x1 head) on an H x W input."""
+    macs, L = 0, len(ch)
+    for l in range(L):
+        c_in = cin if l == 0 else ch[l - 1]
+        macs += (H >> l) * (W >> l) * 9 * (c_in * ch[l] + ch[l] * ch[l])
+    for l in range(L - 2, -1, -1):
+        macs += (H >> l) * (W >> l) * 9 * ((ch[l + 1] + ch[l]) * ch[l] + ch[l] * ch[l])
+    macs += H * W * ch[0] * head
+    return 2 * macs
+
+
+def run_nn(args):
+    """Throughput of the learned fast-forward's network (the encoder-decoder
+    of the learned workload on one 128 x 512 coarse field): inference and one
+    training step (forward, backward-data and weight gradients), bfloat16
+    tensor-core convolutions with float32 accumulation."""
+    import torch
+    from paper_2505_12205_gb300 import build, nn
+    build.build()
+    torch.cuda.set_device(0)
+    nn.load()
+    cin, ch, head, H, W = 8, (32, 64, 128, 256), 8, 512, 128
+    net = nn.UNet(cin=cin, ch=ch, head=head)
+    net.init_he(seed=7)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(C.SEED + 9)
+    x = (0.5 * torch.randn(H * W, cin, generator=g, device="cuda")).to(torch.bfloat16).contiguous()
+    t = torch.randn(H * W, 3, generator=g, device="cuda").contiguous()
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        net.forward(x, 1, H, W, target=t)
+        net.backward(x, 1, H, W)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    for _ in range(args.steps):
+        net.forward(x, 1, H, W)
+    e1.record(stream)
+    for _ in range(args.steps):
+        net.forward(x, 1, H, W, target=t)
+        net.backward(x, 1, H, W)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_inf = e0.elapsed_time(e1) / args.steps
+    ms_train = e1.elapsed_time(e2) / args.steps
+    f_inf = unet_flops(cin, ch, head, H, W)
+    tf_inf = f_inf / (ms_inf * 1e-3) / 1e12
+    tf_train = 3 * f_inf / (ms_train * 1e-3) / 1e12
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, kind = float(json.load(f)["bf16_tflops"]), "measured bf16_tflops (burst)"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    line = {"metric": "TFLOP/s", "value": tf_inf, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_inf, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 operands, f32 accumulation", "data": "synthetic",
+            "config": {"workload": "encoder-decoder 32-256 channels on a 128 x 512 x 8 input (learned fast-forward)",
+                       "gflop_per_inference": f_inf / 1e9, "l2": "weights and activations are L2-resident"},
+            "training_step": {"ms": ms_train, "tflops": tf_train},
+            "roofline": {"bound": "tensor", "achieved": tf_inf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tf_inf / peak, "traffic": None, "peak_source": kind,
+                         "kernel": "k_conv_fwd (mma.sync m16n8k16 bf16) + split-K reduction"},
+            "clocks": clk}
+    print(json.dumps(line))
+    return 0
+
+
 JETSWEEP = dict(We=[1.0, 2.2, 3.5, 5.0], nx=192, ny=192, nz=640, Rn=16.0, steps=48000, sample_from=24000,
                 sample_every=500)
 
@@ -659,7 +736,7 @@ def main():
     ap.add_argument("--storage", default=None, choices=["fp32", "fp16", "bf16"],
                     help="population storage format (arithmetic is float32); default fp32 for the "
                          "jet, fp16 for the sweep")
-    ap.add_argument("--workload", default="jet", choices=["jet", "rt2d", "sweep", "learned", "jet-sweep"])
+    ap.add_argument("--workload", default="jet", choices=["jet", "rt2d", "sweep", "learned", "jet-sweep", "nn"])
     ap.add_argument("--epochs", type=int, default=24, help="training epochs of the learned workload")
     ap.add_argument("--skip", type=int, default=1, help="windows predicted after each passing check (learned)")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
@@ -674,6 +751,8 @@ def main():
         return run_sweep(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "nn":
+        return run_nn(args)
     if args.workload == "jet-sweep":
         return run_jet_sweep(args)
     if args.storage is None:
