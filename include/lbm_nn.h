@@ -50,7 +50,10 @@ int lbm_nn_conv_fwd(const void* x, int32_t x_stride, int32_t ci, int32_t taps, c
 
 /* Gradients of a convolution from the gradient dz of its pre-activation
  * output: dwt[co][k] += sum_m dz[m][co] patch(x)[m][k], dbias[co] += sum_m
- * dz[m][co] (dbias may be NULL).  Accumulates: zero the outputs first. */
+ * dz[m][co] (dbias may be NULL).  Accumulates: zero the outputs first.  The
+ * sums over positions are split into chunks whose partial sums go to scratch
+ * allocated on `stream` (cudaMallocAsync, at most 16 MB, freed on `stream`)
+ * and are added in chunk order: the result does not depend on scheduling. */
 int lbm_nn_conv_wgrad(const void* x, int32_t x_stride, int32_t ci, int32_t taps, const void* dz, int32_t dz_stride,
                       int32_t co, float* dwt, float* dbias, int32_t nb, int32_t h, int32_t w, void* stream);
 
@@ -128,7 +131,9 @@ int lbm_nn_sharpen(float* phi, int64_t n, float ratio, void* stream);
  * c 4 q (1 - q), q = phi clamped to [0, 1], with c such that sum phi =
  * target before rounding (the correction vanishes in the pure phases).  sums: 2 doubles of scratch; on
  * return (after the stream completes) they hold sum phi and sum 4 phi (1 -
- * phi) of the field before the correction. */
+ * phi) of the field before the correction, summed in a fixed order (block
+ * partials in scratch allocated and freed on `stream`), so the projection
+ * is the same on every run. */
 int lbm_nn_mass_project(float* phi, int64_t n, double target, double* sums, void* stream);
 
 /* Comparison of the phase fields a (e.g. a prediction) and b (the solver's)

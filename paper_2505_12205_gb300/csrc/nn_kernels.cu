@@ -9,8 +9,9 @@
 // Y[m][co] = sum_k A[m][k] W[co][k] with A the patches of X gathered on the
 // fly; backward-data is the forward kernel with the weights flipped in space
 // and transposed in channels; the weight gradient dW[co][k] = sum_m dZ[m][co]
-// A[m][k] reduces over the spatial positions, split over blocks, with float32
-// atomics.
+// A[m][k] reduces over the spatial positions, split over blocks whose
+// partial sums are added in a fixed order (no atomics: training gives the
+// same weights on every run).
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -182,11 +183,13 @@ __global__ void k_conv_reduce(const float* __restrict__ part, int splits, int M,
     if (Yf) Yf[int64_t(m) * yfs + n] = v;
 }
 
-// dWt[co][k] += sum over this block's positions of dZ[m][co] A[m][k]
-// (grid: co tiles x k tiles x position splits; float32 atomics)
+// Sum over this block's chunk of positions of dZ[m][co] A[m][k]: added to
+// dWt[co][k] when there is one chunk, else written to the chunk's slice
+// part[chunk][co][k] (grid: co tiles x k tiles x position chunks)
 __global__ void __launch_bounds__(128) k_conv_wgrad(const bf16* __restrict__ X, int xs, int ci, int taps,
                                                     const bf16* __restrict__ dZ, int zs, int co,
-                                                    float* __restrict__ dW, int M, int H, int W, int mchunk)
+                                                    float* __restrict__ dW, int M, int H, int W, int mchunk,
+                                                    float* __restrict__ part)
 {
     __shared__ __align__(16) bf16 As[BM][LDS];   // [co][m]
     __shared__ __align__(16) bf16 Bs[BN][LDS];   // [k][m]
@@ -232,19 +235,32 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(const bf16* __restrict__ X, 
             for (int e = 0; e < 4; ++e) {
                 const int c = c0 + wm * 32 + i * 16 + g + (e >= 2 ? 8 : 0);
                 const int k = k0 + wn * 32 + j * 8 + 2 * t + (e & 1);
-                if (c < co && k < K) atomicAdd(&dW[int64_t(c) * K + k], acc[i][j][e]);
+                if (c >= co || k >= K) continue;
+                if (part) part[(int64_t(blockIdx.z) * co + c) * K + k] = acc[i][j][e];
+                else dW[int64_t(c) * K + k] += acc[i][j][e];      // one chunk: the only writer
             }
 }
 
 // dbias[c] += sum_m dZ[m][c]
-__global__ void k_bias_grad(const bf16* __restrict__ dZ, int zs, int c, int M, int mchunk, float* __restrict__ db)
+// part[chunk][ch] = sum over the chunk's positions of dZ[m][ch]
+__global__ void k_bias_grad(const bf16* __restrict__ dZ, int zs, int c, int M, int mchunk, float* __restrict__ part)
 {
     const int ch = blockIdx.x * blockDim.x + threadIdx.x;
     if (ch >= c) return;
     const int mb = blockIdx.y * mchunk, me = min(M, mb + mchunk);
     float s = 0.0f;
     for (int m = mb; m < me; ++m) s += __bfloat162float(dZ[int64_t(m) * zs + ch]);
-    atomicAdd(&db[ch], s);
+    part[int64_t(blockIdx.y) * c + ch] = s;
+}
+
+// acc[i] += sum_z part[z][i], z = 0, 1, ... in order (n values per slice)
+__global__ void k_sum_slices(const float* __restrict__ part, int nz, int64_t n, float* __restrict__ acc)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float v = part[i];
+    for (int z = 1; z < nz; ++z) v += part[int64_t(z) * n + i];
+    acc[i] += v;
 }
 
 // Wflip[c][tap' * co + o] = Wt[o][(taps - 1 - tap') * ci + c]
@@ -442,24 +458,48 @@ __global__ void k_refine(const float* __restrict__ pred, int Hc, int Wc, int f, 
     v[i] = vv * k;
 }
 
-// sums[0] += sum phi, sums[1] += sum 4 phi (1 - phi) over n values (float64 atomics per warp)
-__global__ void k_mass_sums(const float* __restrict__ phi, int64_t n, double* __restrict__ sums)
+// part[block] = (sum phi, sum 4 q (1 - q)) over the block's 256 x 16 values
+// (fixed order: per thread, then a shuffle tree, then the warps in order)
+constexpr int kMassPer = 256 * 16;
+__global__ void __launch_bounds__(256) k_mass_sums(const float* __restrict__ phi, int64_t n, double2* __restrict__ part)
 {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    __shared__ double2 ws[8];
+    const int64_t base = int64_t(blockIdx.x) * kMassPer;
     double a = 0.0, b = 0.0;
-    if (i < n) {
-        const double p = phi[i], q = fmin(fmax(p, 0.0), 1.0);
-        a = p;
-        b = 4.0 * q * (1.0 - q);
+    for (int j = 0; j < 16; ++j) {
+        const int64_t i = base + j * 256 + threadIdx.x;
+        if (i < n) {
+            const double p = phi[i], q = fmin(fmax(p, 0.0), 1.0);
+            a += p;
+            b += 4.0 * q * (1.0 - q);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, o);
         b += __shfl_down_sync(0xffffffffu, b, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&sums[0], a);
-        atomicAdd(&sums[1], b);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = make_double2(a, b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 t = ws[0];
+        for (int w = 1; w < 8; ++w) {
+            t.x += ws[w].x;
+            t.y += ws[w].y;
+        }
+        part[blockIdx.x] = t;
     }
+}
+
+// sums = the block partials added in block order (one thread)
+__global__ void k_mass_final(const double2* __restrict__ part, int nb, double* __restrict__ sums)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        a += part[i].x;
+        b += part[i].y;
+    }
+    sums[0] = a;
+    sums[1] = b;
 }
 
 // phi += c 4 phi (1 - phi), c = (target - sums[0]) / sums[1] (no change where sums[1] == 0)
@@ -616,14 +656,35 @@ int lbm_nn_conv_wgrad(const void* x, int32_t x_stride, int32_t ci, int32_t taps,
     if (x_stride < ci || dz_stride < co) return nn_fail(LBM_NN_ERR_ARG, "conv_wgrad: strides below the channel counts");
     if (!aligned16(x) || !aligned16(dz)) return nn_fail(LBM_NN_ERR_ARG, "conv_wgrad: x and dz must be 16-byte aligned");
     const int M = nb * h * w, K = taps * ci;
-    const int mchunk = 1024;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    dim3 grid(blocks_for(co, BM), blocks_for(K, BN), blocks_for(M, mchunk));
+    // positions split into chunks of at least 1024 (fewer when the partial
+    // tiles would not fit the scratch cap); each chunk's partial weight
+    // gradient goes to its own slice, and the slices are added to dwt in
+    // chunk order: no atomics, the same result on every run
+    int nchunk = int(blocks_for(M, 1024));
+    while (nchunk > 1 && int64_t(nchunk) * co * K > kConvWsFloats) nchunk = (nchunk + 1) / 2;
+    const int mchunk = int(blocks_for(M, nchunk));
+    nchunk = int(blocks_for(M, mchunk));
+    const int bchunk = 4096, nbc = dbias ? int(blocks_for(M, bchunk)) : 0;
+    const size_t wfl = nchunk > 1 ? size_t(nchunk) * co * K : 0, bfl = size_t(nbc) * co;
+    float* ws = nullptr;
+    if (wfl + bfl > 0) {
+        const cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), (wfl + bfl) * sizeof(float), s);
+        if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("conv_wgrad: workspace: ") + cudaGetErrorString(e));
+    }
+    dim3 grid(blocks_for(co, BM), blocks_for(K, BN), nchunk);
     k_conv_wgrad<<<grid, 128, 0, s>>>(static_cast<const bf16*>(x), x_stride, ci, taps, static_cast<const bf16*>(dz),
-                                      dz_stride, co, dwt, M, h, w, mchunk);
+                                      dz_stride, co, dwt, M, h, w, mchunk, nchunk > 1 ? ws : nullptr);
+    if (nchunk > 1)
+        k_sum_slices<<<blocks_for(int64_t(co) * K, 256), 256, 0, s>>>(ws, nchunk, int64_t(co) * K, dwt);
     if (dbias) {
-        dim3 gb(blocks_for(co, 64), blocks_for(M, 4096));
-        k_bias_grad<<<gb, 64, 0, s>>>(static_cast<const bf16*>(dz), dz_stride, co, M, 4096, dbias);
+        dim3 gb(blocks_for(co, 64), nbc);
+        k_bias_grad<<<gb, 64, 0, s>>>(static_cast<const bf16*>(dz), dz_stride, co, M, bchunk, ws + wfl);
+        k_sum_slices<<<blocks_for(co, 256), 256, 0, s>>>(ws + wfl, nbc, co, dbias);
+    }
+    if (ws) {
+        const cudaError_t e = cudaFreeAsync(ws, s);
+        if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("conv_wgrad: workspace: ") + cudaGetErrorString(e));
     }
     return nn_launch_status("conv_wgrad");
 }
@@ -757,10 +818,15 @@ int lbm_nn_mass_project(float* phi, int64_t n, double target, double* sums, void
 {
     if (!phi || !sums || n < 1) return nn_fail(LBM_NN_ERR_ARG, "mass_project: bad arguments");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), s);
+    const int nb = int(blocks_for(n, kMassPer));
+    double2* part = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&part), size_t(nb) * sizeof(double2), s);
     if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("mass_project: ") + cudaGetErrorString(e));
-    k_mass_sums<<<blocks_for(n, 256), 256, 0, s>>>(phi, n, sums);
+    k_mass_sums<<<nb, 256, 0, s>>>(phi, n, part);
+    k_mass_final<<<1, 1, 0, s>>>(part, nb, sums);
     k_mass_apply<<<blocks_for(n, 256), 256, 0, s>>>(phi, n, target, sums);
+    e = cudaFreeAsync(part, s);
+    if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("mass_project: ") + cudaGetErrorString(e));
     return nn_launch_status("mass_project");
 }
 

@@ -165,3 +165,27 @@ def test_adam_steps_reduce_the_loss(env):
         net.backward(xd, B, H, W)
         net.adam_step(lr=3e-3)
     assert losses[-1] < 0.5 * losses[0]
+
+
+def test_training_step_is_reproducible(env):
+    """Two identical training steps give bit-identical weights: the weight
+    and bias gradients are reduced in a fixed order, not with atomics."""
+    torch, nn, O = env
+    ch, cin, head = [8, 16, 24, 32], 8, 8
+    B, H, W = 2, 32, 64
+    r = np.random.Generator(np.random.PCG64(51))
+    x = r.standard_normal((B * H * W, cin)).astype(np.float32)
+    xd = to_dev(torch, x, torch.bfloat16)
+    td = to_dev(torch, np.sin(x[:, :3]), torch.float32)
+    out = []
+    for _ in range(2):
+        net = nn.UNet(cin=cin, ch=ch, head=head)
+        net.set_params(O.init_params(cin, ch, head, seed=52))
+        for _ in range(3):
+            net.forward(xd, B, H, W, target=td)
+            net.backward(xd, B, H, W)
+            net.adam_step(lr=1e-3)
+        torch.cuda.synchronize()
+        out.append(net.get_params())
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
