@@ -482,23 +482,6 @@ __device__ __forceinline__ int map_phi(int v, int n, int bclo, int bchi, bool& i
     return v;
 }
 
-// Push target along one axis: kind 0 = inside (maybe wrapped), 1 = wall,
-// 2 = open face (population leaves the domain).
-__device__ __forceinline__ int map_push(int v, int n, int bclo, int bchi, int& kind)
-{
-    if (v < 0) {
-        if (bclo == BC_PERIODIC) return v + n;
-        kind = max(kind, bclo == BC_WALL ? 2 : 1);
-        return 0;
-    }
-    if (v >= n) {
-        if (bchi == BC_PERIODIC) return v - n;
-        kind = max(kind, bchi == BC_WALL ? 2 : 1);
-        return n - 1;
-    }
-    return v;
-}
-
 // ---------------------------------------------------------------- kernels
 
 // phi = sum_a g_a of every node into phi[node] (unpadded node order).
