@@ -61,7 +61,7 @@ typedef enum {
     LBM_ERR_CUDA = -2,     /* a CUDA runtime call failed */
     LBM_ERR_OOM = -3,      /* device allocation failed */
     LBM_ERR_DIVERGED = -4, /* non-finite populations found by lbm_diag */
-    LBM_ERR_TIMEOUT = -5,  /* reserved: a bounded wait on the device gave up */
+    LBM_ERR_TIMEOUT = -5,  /* a bounded iteration gave up (lbm_jet_stats) */
     LBM_ERR_STATE = -6     /* call out of order (e.g. step before init) */
 } lbm_status;
 
@@ -122,8 +122,9 @@ typedef struct {
     int32_t reserved;
 } lbm_diag_out;
 
-/* Create a context: validate p, allocate the double-buffered population
- * planes (2 sets x 2 buffers x Q x nx*ny*nz float32) on the current CUDA
+/* Create a context: validate p, allocate the double-buffered populations
+ * (2 sets x 2 buffers x Q values per node, rows padded to a multiple of 32
+ * nodes, 4 or 2 bytes per value by `storage`) on the current CUDA
  * device and bind the CUDA stream `stream` (a cudaStream_t; NULL = the legacy
  * default stream).  Errors: LBM_ERR_ARG (out == NULL, a parameter out of
  * range, unpaired periodic faces, inlet/outlet on another face, last axis
