@@ -60,7 +60,8 @@ typedef enum {
     LBM_ERR_ARG = -1,      /* invalid argument or parameter */
     LBM_ERR_CUDA = -2,     /* a CUDA runtime call failed */
     LBM_ERR_OOM = -3,      /* device allocation failed */
-    LBM_ERR_DIVERGED = -4, /* non-finite populations found by lbm_diag */
+    LBM_ERR_DIVERGED = -4, /* non-finite populations found by lbm_diag or by
+                              the in-step check of lbm_step (diag_every) */
     LBM_ERR_TIMEOUT = -5,  /* a bounded iteration gave up (lbm_jet_stats) */
     LBM_ERR_STATE = -6     /* call out of order (e.g. step before init) */
 } lbm_status;
@@ -78,8 +79,13 @@ typedef enum {
  *               0 = float32; 1 = float16 and 2 = bfloat16, both storing
  *               each population normalised by its weight: f as
  *               (f_a / w_a) * storage_scale, g as g_a / w_a - 1/2
+ *  diag_every   steps between the in-step diagnostics of lbm_step (FP64
+ *               sum of phi, finite check, Laplace pressure sums; Sec. 5.2,
+ *               5.4); 0 = off
  *  rho_L, rho_H densities (eq:density_interpolation)
  *  tau_L, tau_H relaxation times, nu = tau c_s^2 (eq:kinematic_viscosity)
+ *  mu_ratio     viscosity ratio mu_H / mu_L; when > 0 it replaces tau_L:
+ *               tau_L = tau_H (rho_H / rho_L) / mu_ratio (mu_X = rho_X tau_X c_s^2)
  *  sigma, W     surface tension and interface width xi
  *               (eq:beta_kappa_relation)
  *  mobility     M = tau_phi c_s^2 (eq:mobility_relation)
@@ -98,8 +104,9 @@ typedef struct {
     int32_t visc_model;
     int32_t storage;
     int32_t outlet_scheme;
-    int32_t reserved;       /* 0 */
+    int32_t diag_every;
     double rho_L, rho_H, tau_L, tau_H;
+    double mu_ratio;
     double sigma, W, mobility;
     double force[3];
     double rho_ref;
@@ -120,6 +127,8 @@ typedef struct {
     int64_t n_in, n_out;
     int32_t finite;    /* 1 if every population is finite */
     int32_t reserved;
+    double dp_laplace; /* sum_p_in / n_in - sum_p_out / n_out (eq:laplace_law);
+                          0 when either set is empty */
 } lbm_diag_out;
 
 /* Create a context: validate p, allocate the double-buffered populations
@@ -128,8 +137,9 @@ typedef struct {
  * device and bind the CUDA stream `stream` (a cudaStream_t; NULL = the legacy
  * default stream).  Errors: LBM_ERR_ARG (out == NULL, a parameter out of
  * range, unpaired periodic faces, inlet/outlet on another face, last axis
- * shorter than 4 with open faces), LBM_ERR_CUDA (no device), LBM_ERR_OOM.
- * On failure *out is NULL. */
+ * shorter than 4 with open faces, an inlet without the outlet on the
+ * opposite face, W < 2, a negative diag_every), LBM_ERR_CUDA (no device),
+ * LBM_ERR_OOM.  On failure *out is NULL. */
 int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out);
 
 /* Set the state to the equilibria of the given fields (eq:equilibrium,
@@ -145,9 +155,19 @@ int lbm_init_fields(lbm_ctx* ctx, const float* phi, const float* u, const float*
  * lbm_destroy; not while kernel timing is on, nor after a capture was
  * refused, e.g. inside the caller's own global-mode stream capture), the rest
  * launched one by one; the results are the same either way.
+ * With diag_every = k > 0, after every k-th step (counted from the last
+ * lbm_init_fields / lbm_set_populations) the FP64 diagnostics of lbm_diag
+ * (phase threshold 1e-3) run on the stream and lbm_step waits for them: when
+ * a population is not finite it stops there and returns LBM_ERR_DIVERGED
+ * (the state of that step stays readable; lbm_diag_last gives the record).
  * Errors: LBM_ERR_STATE before lbm_init_fields / lbm_set_populations;
- * LBM_ERR_CUDA when a launch or the graph capture fails. */
+ * LBM_ERR_CUDA when a launch or the graph capture fails; LBM_ERR_DIVERGED. */
 int lbm_step(lbm_ctx* ctx, int64_t nsteps);
+
+/* The record of the last in-step diagnostic of lbm_step (diag_every) and the
+ * step count it was taken at (*step = -1 and *out zeroed if none yet).  Does
+ * not touch the device. */
+int lbm_diag_last(const lbm_ctx* ctx, lbm_diag_out* out, int64_t* step);
 
 /* Macroscopic fields of the current state, computed with the same device
  * code as the step: phi [N], u [D][N] (eq:velocity_update), p [N]
@@ -184,15 +204,18 @@ int lbm_get_timing(lbm_ctx* ctx, double* ms, int64_t* nsteps);
  * or would bypass an allocator that must own every byte, e.g. a host
  * framework's caching allocator, a real-time loop, a plug-in that is only
  * handed buffers).  The paper has no counterpart; this is a library service.
- * p describes the grid and physics as for lbm_create; f and g are device
- * pointers to post-streaming populations [Q][N] (the layout of
- * lbm_get_populations); out is a host pointer.  The same kernels as lbm_diag
- * run on `stream` with their scratch (phi, the inlet profile, the reduction
- * partials) in one static device array of the library: at most 2,097,152
- * nodes and 65,536 inlet-plane nodes (LBM_ERR_ARG beyond that).  The array
- * (about 8.6 MB) stays on every device that loads the library until exit.
- * The first call on a device looks up the array's device address; make that
- * call before any stream capture.  All calls share the array and rewrite
+ * p describes the grid and physics as for lbm_create (its storage field is
+ * ignored); f and g are device pointers to float32 post-streaming populations
+ * [Q][N] each (the layout of lbm_get_populations); out is a host pointer.
+ * The same kernels as lbm_diag run on `stream` with their scratch (phi, the
+ * inlet profile, the reduction partials) in one static device array of the
+ * library: at most 2,097,152 nodes and, with an inlet face, 65,536
+ * inlet-plane nodes (LBM_ERR_ARG beyond that).  The array (about 8.6 MB)
+ * stays on every device that loads the library until exit.  The first call
+ * on a device looks up the array's device address and keeps it for that
+ * device's primary context (not valid after cudaDeviceReset or under another
+ * driver context); make that call before any stream capture.  All calls
+ * share the array and rewrite
  * everything they read, so results do not depend on earlier calls, but calls
  * that overlap on the GPU race.  Synchronises `stream`.  Errors as lbm_diag;
  * their text is returned by lbm_last_error(NULL). */

@@ -46,8 +46,11 @@
  *   R8  inlet: derivatives of phi are not evaluated at inlet nodes (the
  *       paper treats the inlet as single phase and skips the derivatives of
  *       the macroscopic variables there): grad phi = lap phi = 0, so the
- *       interfacial forces F_s, F_p, F_mu and F^phi vanish at inlet nodes,
- *       and the force shift f' = f + F/2 of the velocity rule is omitted;
+ *       interfacial forces F_s, F_p, F_mu and F^phi vanish at inlet nodes;
+ *       the velocity rule is applied to f' = f + F/2 with the force that
+ *       remains, the body force F_b = (rho(phi_in) - rho_ref) g, so that
+ *       sum f' e = u_in (eq:velocity_boundary_u) and the velocity of the next
+ *       macroscopic update is u_in;
  *       p* cancels from eq:velocity_boundary_distribution; the tangential
  *       excess momentum is shared by the 2 unknown populations that carry each
  *       tangential component (factor 1/2, which makes
@@ -85,6 +88,7 @@ typedef struct {
     int32_t visc_model;      /* 0: mu linear in phi, 1: tau linear in phi */
     int32_t outlet_scheme;   /* outlet speed U of eq:velocity_options: 0 local, 1 max, 2 average */
     double rho_L, rho_H, tau_L, tau_H;
+    double mu_ratio;         /* mu_H / mu_L; when > 0 it sets tau_L (Reading R3) */
     double sigma, W, mobility;
     double force[3];         /* body-force acceleration g */
     double rho_ref;          /* F_b = (rho - rho_ref) g */
@@ -466,8 +470,11 @@ int orc_validate(const orc_params* p)
     if (p->lattice != ORC_D2Q9 && p->lattice != ORC_D3Q19) return -1;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return -1;
     if (p->lattice == ORC_D2Q9 && p->nz != 1) return -1;
-    if (!(p->rho_L > 0 && p->rho_H > 0 && p->tau_L > 0 && p->tau_H > 0)) return -1;
-    if (!(p->W > 0 && p->mobility > 0 && p->sigma >= 0)) return -1;
+    if (!(p->rho_L > 0 && p->rho_H > 0 && p->tau_H > 0 && p->mu_ratio >= 0)) return -1;
+    if (!(p->mu_ratio > 0 || p->tau_L > 0)) return -1;
+    /* an interface narrower than two lattice units is not resolved by the
+     * isotropic stencils of eq:gradient_phi / eq:laplacian_phi */
+    if (!(p->W >= 2 && p->mobility > 0 && p->sigma >= 0)) return -1;
     if (p->visc_model != 0 && p->visc_model != 1) return -1;
     int D = p->lattice == ORC_D2Q9 ? 2 : 3, L = D - 1;
     if (p->outlet_scheme < 0 || p->outlet_scheme > 2) return -1;
@@ -482,6 +489,9 @@ int orc_validate(const orc_params* p)
     int n[3] = {p->nx, p->ny, p->nz};
     int lo = p->bc[2 * L], hi = p->bc[2 * L + 1];
     if ((lo == BC_INLET || hi == BC_OUTFLOW) && n[L] < 4) return -1;
+    /* what enters through the inlet must be able to leave: an inlet needs the
+     * convective outlet on the opposite face (the paper's jet set-up, Sec. 6) */
+    if (lo == BC_INLET && hi != BC_OUTFLOW) return -1;
     return 0;
 }
 
@@ -491,6 +501,9 @@ orc_ctx* orc_create(const orc_params* p)
     orc_ctx* c = (orc_ctx*)calloc(1, sizeof(orc_ctx));
     if (!c) return NULL;
     c->p = *p;
+    /* Reading R3: mu_X = rho_X tau_X c_s^2, so mu_H / mu_L = ratio gives
+     * tau_L = tau_H (rho_H / rho_L) / ratio */
+    if (p->mu_ratio > 0) c->p.tau_L = p->tau_H * (p->rho_H / p->rho_L) / p->mu_ratio;
     if (p->lattice == ORC_D2Q9) {      /* 2D: no z faces, no z force */
         c->p.bc[4] = c->p.bc[5] = BC_PERIODIC;
         c->p.force[2] = 0.0;
@@ -550,6 +563,118 @@ static void compute_phi(orc_ctx* c, const double* g)
     }
 }
 
+/* Outlet speed U at column (t0, t1) of the outlet: the first moment of f
+ * along the outward normal at layer N-1 after streaming (Reading R9). */
+static double outlet_speed(const orc_ctx* c, const double* fB, int t0, int t1)
+{
+    int L = c->L, Q = c->Q, nL = c->n[L];
+    int64_t iM = (c->D == 2) ? nid(c, t0, nL - 2, 0) : nid(c, t0, t1, nL - 2);
+    double U = 0.0;
+    for (int a = 0; a < Q; ++a) U += fB[iM * Q + a] * c->e[a][L];
+    return U;
+}
+
+/* Open-face rules of App. B applied to the post-streaming state B, given the
+ * state A of the previous time level (the outlet reads chi(N, t) from A).
+ *
+ * Velocity inlet (f) and phase-field inlet (g), Reading R8.  The velocity
+ * rule holds for f' = f + F/2 (eq:velocity_boundary_u,
+ * eq:velocity_boundary_distribution with eq:force_term), with F the force
+ * the next macroscopic update finds at the node: the interfacial forces
+ * F_s, F_p, F_mu need derivatives of phi, which are not evaluated at the
+ * inlet, so F = F_b = (rho - rho_ref) g (eq:gravity_force) with rho from
+ * phi_in (eq:mass_conservation makes sum g = phi_in).  The known populations
+ * are shifted to f', the unknown ones are formed in f' and shifted back.
+ *
+ * Convective outlet, eq:implicit_convective / eq:convective_f/g:
+ * chi(N, t+1) = [chi(N, t) + lambda chi(N-1, t+1)] / (1 + lambda) for every
+ * population of both sets, lambda = U dt/dy clamped to [0, 1]; U of
+ * eq:velocity_options: local (outlet_speed), or its maximum or average over
+ * the layer. */
+static void apply_faces(const orc_ctx* c, const double* fA, const double* gA, double* fB, double* gB)
+{
+    int Q = c->Q, L = c->L;
+    int nt0 = c->n[0], nt1 = (c->D == 3) ? c->n[1] : 1;
+    if (c->p.bc[2 * L] == BC_INLET) {
+        for (int t1 = 0; t1 < nt1; ++t1)
+            for (int t0 = 0; t0 < nt0; ++t0) {
+                int64_t i = (c->D == 2) ? nid(c, t0, 0, 0) : nid(c, t0, t1, 0);
+                double* f = fB + i * Q;
+                double* g = gB + i * Q;
+                double phi_in, un;
+                inlet_profile(c, t0, t1, &phi_in, &un);
+                double uin[3] = {0, 0, 0};
+                uin[L] = un;
+                /* eq:density_interpolation (Reading R4), eq:gravity_force */
+                double ph = phi_in < 0.0 ? 0.0 : (phi_in > 1.0 ? 1.0 : phi_in);
+                double rho = c->p.rho_L + ph * (c->p.rho_H - c->p.rho_L);
+                double F[3];
+                for (int d = 0; d < 3; ++d) F[d] = (rho - c->p.rho_ref) * c->p.force[d];
+                double half[QMAX], fp[QMAX];
+                for (int a = 0; a < Q; ++a) {
+                    double eF = 0.0;
+                    for (int d = 0; d < 3; ++d) eF += c->e[a][d] * F[d];
+                    half[a] = 0.5 * c->w[a] * eF / (rho * CS2);   /* F_a / 2, eq:force_term */
+                    fp[a] = f[a] + half[a];
+                }
+                double Mt[3] = {0, 0, 0}, theta = 0.0;
+                int ndiag = 0;
+                for (int b = 0; b < Q; ++b) {
+                    if (c->e[b][L] != 0) continue;          /* Lambda = {e.n = 0} */
+                    double Gb = Gamma(c, b, uin);
+                    /* f^eq_b = p* w_b + Gamma_b - w_b; the p* part sums to 0 over Lambda */
+                    for (int d = 0; d < 3; ++d) Mt[d] += c->e[b][d] * (fp[b] - (Gb - c->w[b]));
+                    theta += g[b] - phi_in * Gb;            /* eq:excess_density */
+                }
+                for (int a = 0; a < Q; ++a) {
+                    if (c->e[a][L] <= 0) continue;
+                    int tang = 0;
+                    for (int d = 0; d < 3; ++d) if (d != L && c->e[a][d] != 0) tang = 1;
+                    ndiag += tang;
+                }
+                for (int a = 0; a < Q; ++a) {
+                    if (c->e[a][L] <= 0) continue;          /* unknown: e_a . n > 0 */
+                    int ab = c->opp[a];
+                    double Ga = Gamma(c, a, uin), Gab = Gamma(c, ab, uin);
+                    double eM = 0.0;
+                    int tang = 0;
+                    for (int d = 0; d < 3; ++d) {
+                        if (d == L) continue;
+                        eM += c->e[a][d] * Mt[d];
+                        if (c->e[a][d] != 0) tang = 1;
+                    }
+                    /* eq:velocity_boundary_distribution (p* cancels; tangential factor 1/2, R8) */
+                    double fpa = fp[ab] + (Ga - Gab) - 0.5 * eM;
+                    f[a] = fpa - half[a];
+                    g[a] = phi_in * Ga - (g[ab] - phi_in * Gab) - (tang ? theta / ndiag : 0.0);
+                }
+            }
+    }
+    if (c->p.bc[2 * L + 1] == BC_OUTFLOW) {
+        int nL = c->n[L];
+        double Umax = -1e300, Usum = 0.0;
+        for (int t1 = 0; t1 < nt1; ++t1)
+            for (int t0 = 0; t0 < nt0; ++t0) {
+                double U = outlet_speed(c, fB, t0, t1);
+                if (U > Umax) Umax = U;
+                Usum += U;
+            }
+        const double Uglob = c->p.outlet_scheme == 1 ? Umax : Usum / ((double)nt0 * nt1);
+        for (int t1 = 0; t1 < nt1; ++t1)
+            for (int t0 = 0; t0 < nt0; ++t0) {
+                int64_t iN, iM;
+                if (c->D == 2) { iN = nid(c, t0, nL - 1, 0); iM = nid(c, t0, nL - 2, 0); }
+                else { iN = nid(c, t0, t1, nL - 1); iM = nid(c, t0, t1, nL - 2); }
+                double U = c->p.outlet_scheme == 0 ? outlet_speed(c, fB, t0, t1) : Uglob;
+                double lam = U < 0.0 ? 0.0 : (U > 1.0 ? 1.0 : U);
+                for (int a = 0; a < Q; ++a) {
+                    fB[iN * Q + a] = (fA[iN * Q + a] + lam * fB[iM * Q + a]) / (1.0 + lam);
+                    gB[iN * Q + a] = (gA[iN * Q + a] + lam * gB[iM * Q + a]) / (1.0 + lam);
+                }
+            }
+    }
+}
+
 /* One time step: macroscopic update + collision on the current state A,
  * pull streaming into B, inlet/outlet fix-ups on B, swap. */
 static void step_once(orc_ctx* c)
@@ -587,79 +712,7 @@ static void step_once(orc_ctx* c)
         }
     }
 
-    int L = c->L;
-    int nt0 = c->n[0], nt1 = (c->D == 3) ? c->n[1] : 1;
-    /* Velocity inlet (f) and phase-field inlet (g), App. B, Reading R8. */
-    if (c->p.bc[2 * L] == BC_INLET) {
-        for (int t1 = 0; t1 < nt1; ++t1)
-            for (int t0 = 0; t0 < nt0; ++t0) {
-                int64_t i = (c->D == 2) ? nid(c, t0, 0, 0) : nid(c, t0, t1, 0);
-                double* f = c->fB + i * Q;
-                double* g = c->gB + i * Q;
-                double phi_in, un;
-                inlet_profile(c, t0, t1, &phi_in, &un);
-                double uin[3] = {0, 0, 0};
-                uin[L] = un;
-                double Mt[3] = {0, 0, 0}, theta = 0.0;
-                int ndiag = 0;
-                for (int b = 0; b < Q; ++b) {
-                    if (c->e[b][L] != 0) continue;          /* Lambda = {e.n = 0} */
-                    double Gb = Gamma(c, b, uin);
-                    for (int d = 0; d < 3; ++d) Mt[d] += c->e[b][d] * (f[b] - (Gb - c->w[b]));
-                    theta += g[b] - phi_in * Gb;            /* eq:excess_density */
-                }
-                for (int a = 0; a < Q; ++a) {
-                    if (c->e[a][L] <= 0) continue;
-                    int tang = 0;
-                    for (int d = 0; d < 3; ++d) if (d != L && c->e[a][d] != 0) tang = 1;
-                    ndiag += tang;
-                }
-                for (int a = 0; a < Q; ++a) {
-                    if (c->e[a][L] <= 0) continue;          /* unknown: e_a . n > 0 */
-                    int ab = c->opp[a];
-                    double Ga = Gamma(c, a, uin), Gab = Gamma(c, ab, uin);
-                    double eM = 0.0;
-                    int tang = 0;
-                    for (int d = 0; d < 3; ++d) {
-                        if (d == L) continue;
-                        eM += c->e[a][d] * Mt[d];
-                        if (c->e[a][d] != 0) tang = 1;
-                    }
-                    f[a] = f[ab] + (Ga - Gab) - 0.5 * eM;   /* eq:velocity_boundary_distribution */
-                    g[a] = phi_in * Ga - (g[ab] - phi_in * Gab) - (tang ? theta / ndiag : 0.0);
-                }
-            }
-    }
-    /* Convective outlet, eq:implicit_convective, Reading R9; the outlet
-     * speed U of eq:velocity_options: local (the bare first moment at layer
-     * N-1 after streaming), or its maximum or average over the layer. */
-    if (c->p.bc[2 * L + 1] == BC_OUTFLOW) {
-        int nL = c->n[L];
-        double Umax = -1e300, Usum = 0.0;
-        for (int t1 = 0; t1 < nt1; ++t1)
-            for (int t0 = 0; t0 < nt0; ++t0) {
-                int64_t iM = (c->D == 2) ? nid(c, t0, nL - 2, 0) : nid(c, t0, t1, nL - 2);
-                double U = 0.0;
-                for (int a = 0; a < Q; ++a) U += c->fB[iM * Q + a] * c->e[a][L];
-                if (U > Umax) Umax = U;
-                Usum += U;
-            }
-        const double Uglob = c->p.outlet_scheme == 1 ? Umax : Usum / ((double)nt0 * nt1);
-        for (int t1 = 0; t1 < nt1; ++t1)
-            for (int t0 = 0; t0 < nt0; ++t0) {
-                int64_t iN, iM;
-                if (c->D == 2) { iN = nid(c, t0, nL - 1, 0); iM = nid(c, t0, nL - 2, 0); }
-                else { iN = nid(c, t0, t1, nL - 1); iM = nid(c, t0, t1, nL - 2); }
-                double U = 0.0;
-                for (int a = 0; a < Q; ++a) U += c->fB[iM * Q + a] * c->e[a][L];
-                if (c->p.outlet_scheme != 0) U = Uglob;
-                double lam = U < 0.0 ? 0.0 : (U > 1.0 ? 1.0 : U);
-                for (int a = 0; a < Q; ++a) {
-                    c->fB[iN * Q + a] = (c->fA[iN * Q + a] + lam * c->fB[iM * Q + a]) / (1.0 + lam);
-                    c->gB[iN * Q + a] = (c->gA[iN * Q + a] + lam * c->gB[iM * Q + a]) / (1.0 + lam);
-                }
-            }
-    }
+    apply_faces(c, c->fA, c->gA, c->fB, c->gB);
     (void)nz;
     double* t;
     t = c->fA; c->fA = c->fB; c->fB = t;
@@ -760,6 +813,26 @@ void orc_set_pops(orc_ctx* c, const double* f, const double* g)
         for (int64_t i = 0; i < c->N; ++i) {
             c->fA[i * c->Q + a] = f[(int64_t)a * c->N + i];
             c->gA[i * c->Q + a] = g[(int64_t)a * c->N + i];
+        }
+}
+
+/* The open-face rules alone (test hook for the pins of App. B): fB, gB are
+ * a post-streaming state [a][node] (population-major); the context's current
+ * state plays chi(N, t) of the outlet rule.  fB and gB are overwritten with
+ * the state after the inlet and outlet rules. */
+void orc_apply_faces(orc_ctx* c, double* fB, double* gB)
+{
+    int Q = c->Q;
+    for (int a = 0; a < Q; ++a)
+        for (int64_t i = 0; i < c->N; ++i) {
+            c->fB[i * Q + a] = fB[(int64_t)a * c->N + i];
+            c->gB[i * Q + a] = gB[(int64_t)a * c->N + i];
+        }
+    apply_faces(c, c->fA, c->gA, c->fB, c->gB);
+    for (int a = 0; a < Q; ++a)
+        for (int64_t i = 0; i < c->N; ++i) {
+            fB[(int64_t)a * c->N + i] = c->fB[i * Q + a];
+            gB[(int64_t)a * c->N + i] = c->gB[i * Q + a];
         }
 }
 

@@ -58,6 +58,7 @@ class OrcParams(ctypes.Structure):
         ("visc_model", ctypes.c_int32), ("outlet_scheme", ctypes.c_int32),
         ("rho_L", ctypes.c_double), ("rho_H", ctypes.c_double),
         ("tau_L", ctypes.c_double), ("tau_H", ctypes.c_double),
+        ("mu_ratio", ctypes.c_double),
         ("sigma", ctypes.c_double), ("W", ctypes.c_double),
         ("mobility", ctypes.c_double),
         ("force", ctypes.c_double * 3), ("rho_ref", ctypes.c_double),
@@ -92,6 +93,7 @@ def lib():
         _lib.orc_collide_node.argtypes = [ctypes.c_void_p, d, d, d, d, d, d, d]
         _lib.orc_advect.argtypes = [ctypes.c_void_p, d, ctypes.c_double, ctypes.c_int64]
         _lib.orc_advect.restype = ctypes.c_int
+        _lib.orc_apply_faces.argtypes = [ctypes.c_void_p, d, d]
     return _lib
 
 
@@ -137,7 +139,8 @@ def make_params(p: dict) -> OrcParams:
     s.visc_model = int(p.get("visc_model", 0))
     s.outlet_scheme = int(p.get("outlet_scheme", 0))
     s.rho_L, s.rho_H = float(p["rho_L"]), float(p["rho_H"])
-    s.tau_L, s.tau_H = float(p["tau_L"]), float(p["tau_H"])
+    s.tau_L, s.tau_H = float(p.get("tau_L", 0.0)), float(p["tau_H"])
+    s.mu_ratio = float(p.get("mu_ratio", 0.0))
     s.sigma, s.W, s.mobility = float(p["sigma"]), float(p["W"]), float(p["mobility"])
     g = list(p.get("force", (0.0, 0.0, 0.0))) + [0.0] * 3
     for i in range(3):
@@ -217,6 +220,16 @@ class Oracle:
         ua = np.ascontiguousarray(u, np.float64).reshape(-1)
         if lib().orc_advect(self._h, _dp(ua), float(scale), int(nsteps)) != 0:
             raise ValueError("advection needs periodic or wall faces")
+
+    def apply_faces(self, fB, gB):
+        """The inlet and outlet rules of App. B applied to the post-streaming
+        state (fB, gB) [Q][nz][ny][nx], with the current state as chi(N, t) of
+        the outlet; returns the new arrays (see orc_apply_faces)."""
+        fo = np.ascontiguousarray(fB, np.float64).reshape(-1).copy()
+        go = np.ascontiguousarray(gB, np.float64).reshape(-1).copy()
+        assert fo.size == self.Q * self.N and go.size == self.Q * self.N
+        lib().orc_apply_faces(self._h, _dp(fo), _dp(go))
+        return fo.reshape((self.Q,) + self.shape), go.reshape((self.Q,) + self.shape)
 
     def collide_node(self, f, g, phin):
         f = np.ascontiguousarray(f, np.float64)

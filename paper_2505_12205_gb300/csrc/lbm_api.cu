@@ -1,6 +1,7 @@
 // C ABI of the phase-field WMRT lattice Boltzmann library (declared in
 // include/lbm.h): parameter validation, device memory, stream binding and
 // dispatch to the per-lattice kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -76,6 +77,11 @@ struct lbm_ctx {
     void* g0 = nullptr;
     cudaStream_t cap = nullptr;
     bool no_graphs = false;         // a capture was refused: launch step by step
+    // in-step diagnostics (diag_every): steps since the state was set, and
+    // the last record
+    int64_t step_count = 0;
+    int64_t last_diag_step = -1;
+    lbm_diag_out last_diag{};
     std::string err;
 };
 
@@ -115,8 +121,14 @@ static int validate(const lbm_params* p, std::string& why)
             return -1;
         }
     }
-    if (!(p->rho_L > 0 && p->rho_H > 0 && p->tau_L > 0 && p->tau_H > 0)) { why = "rho_L, rho_H, tau_L, tau_H must be > 0"; return -1; }
-    if (!(p->W > 0 && p->mobility > 0 && p->sigma >= 0)) { why = "W, mobility must be > 0 and sigma >= 0"; return -1; }
+    if (!(p->rho_L > 0 && p->rho_H > 0 && p->tau_H > 0)) { why = "rho_L, rho_H, tau_H must be > 0"; return -1; }
+    if (!(p->mu_ratio >= 0)) { why = "mu_ratio must be >= 0 (0: tau_L as given)"; return -1; }
+    if (!(p->mu_ratio > 0 || p->tau_L > 0)) { why = "tau_L must be > 0 when mu_ratio is 0"; return -1; }
+    // an interface narrower than two lattice units is not resolved by the
+    // isotropic stencils of eq:gradient_phi / eq:laplacian_phi
+    if (!(p->W >= 2)) { why = "W (interface width) must be >= 2 lattice units"; return -1; }
+    if (!(p->mobility > 0 && p->sigma >= 0)) { why = "mobility must be > 0 and sigma >= 0"; return -1; }
+    if (p->diag_every < 0) { why = "diag_every must be >= 0"; return -1; }
     if (p->visc_model != 0 && p->visc_model != 1) { why = "visc_model must be 0 or 1"; return -1; }
     if (p->storage < 0 || p->storage > 2) { why = "storage must be 0 (float32), 1 (float16) or 2 (bfloat16)"; return -1; }
     if (!(p->storage_scale >= 0)) { why = "storage_scale must be >= 0"; return -1; }
@@ -136,7 +148,19 @@ static int validate(const lbm_params* p, std::string& why)
         return -1;
     }
     if (p->bc[2 * L] == LBM_BC_INLET && !(p->inlet_radius >= 0)) { why = "inlet_radius must be >= 0"; return -1; }
+    // what enters through the inlet must be able to leave (Sec. 6 jet set-up)
+    if (p->bc[2 * L] == LBM_BC_INLET && p->bc[2 * L + 1] != LBM_BC_OUTFLOW) {
+        why = "an inlet needs the convective outlet on the opposite face";
+        return -1;
+    }
     return 0;
+}
+
+// tau_L as given, or from the viscosity ratio: mu_X = rho_X tau_X c_s^2, so
+// mu_H / mu_L = mu_ratio gives tau_L = tau_H (rho_H / rho_L) / mu_ratio
+static double tau_L_of(const lbm_params* p)
+{
+    return p->mu_ratio > 0 ? p->tau_H * (p->rho_H / p->rho_L) / p->mu_ratio : p->tau_L;
 }
 
 static DevParams make_dev(const lbm_params* p, int64_t N)
@@ -155,8 +179,9 @@ static DevParams make_dev(const lbm_params* p, int64_t N)
         if (p->bc[f] == LBM_BC_FREESLIP) d.has_slip = 1;
     d.N = N;
     d.rho_L = float(p->rho_L); d.rho_H = float(p->rho_H);
-    d.tau_L = float(p->tau_L); d.tau_H = float(p->tau_H);
-    d.mu_L = float(p->rho_L * p->tau_L / 3.0); d.mu_H = float(p->rho_H * p->tau_H / 3.0);
+    const double tau_L = tau_L_of(p);
+    d.tau_L = float(tau_L); d.tau_H = float(p->tau_H);
+    d.mu_L = float(p->rho_L * tau_L / 3.0); d.mu_H = float(p->rho_H * p->tau_H / 3.0);
     d.beta = float(12.0 * p->sigma / p->W);
     d.kappa = float(1.5 * p->sigma * p->W);
     d.inv_W = float(1.0 / p->W);
@@ -237,12 +262,60 @@ static cudaError_t capture_steps(lbm_ctx* c, int slot)
     return e;
 }
 
+// The diagnostics record of a reduction result.
+static void fill_diag(const DiagPartial& r, lbm_diag_out* out)
+{
+    out->sum_phi = r.sum_phi;
+    out->sum_p_in = r.sum_p_in;
+    out->sum_p_out = r.sum_p_out;
+    out->max_speed = r.max_speed;
+    out->n_in = r.n_in;
+    out->n_out = r.n_out;
+    out->finite = r.nonfinite ? 0 : 1;
+    out->reserved = 0;
+    out->dp_laplace = (r.n_in > 0 && r.n_out > 0) ? r.sum_p_in / double(r.n_in) - r.sum_p_out / double(r.n_out) : 0.0;
+}
+
 // Entry points for the other translation units of the library.
 namespace lbm {
 int api_validate(const lbm_params* p, std::string& why) { return validate(p, why); }
 DevParams api_make_dev(const lbm_params* p, int64_t N) { return make_dev(p, N); }
 void api_set_thread_error(const std::string& msg) { g_create_err = msg; }
+void api_fill_diag(const DiagPartial& r, lbm_diag_out* out) { fill_diag(r, out); }
 }  // namespace lbm
+
+// The FP64 diagnostics of the current state into *r (synchronises).
+static int run_diag(lbm_ctx* c, double phase_eps, DiagPartial* r)
+{
+    cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+        return decltype(l)::diag(c->dp, c->b, phase_eps, c->diag_part, c->diag_nparts, c->diag_res, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "diag kernels");
+    LBM_CUDA(c, cudaMemcpyAsync(r, c->diag_res, sizeof *r, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+// nsteps steps: whole graphs of kStepGraph steps (not while kernel timing is
+// on: its events are recorded between the launches), then single steps.
+static int run_steps(lbm_ctx* c, int64_t nsteps)
+{
+    while (!c->timing && !c->no_graphs && nsteps >= kStepGraph) {
+        const int slot = (c->b.fA == c->f0 ? 0 : 1) | (c->b.gA == c->g0 ? 0 : 2);
+        if (!c->graph[slot] && capture_steps(c, slot) != cudaSuccess) {
+            cudaGetLastError();                 // a refused capture leaves no sticky error
+            c->no_graphs = true;
+            break;
+        }
+        LBM_CUDA(c, cudaGraphLaunch(c->graph[slot], c->stream));
+        nsteps -= kStepGraph;
+    }
+    for (int64_t s = 0; s < nsteps; ++s) {
+        cudaError_t e = dispatch_step(c);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step kernels");
+    }
+    return LBM_OK;
+}
 
 extern "C" {
 
@@ -400,6 +473,7 @@ int lbm_init_fields(lbm_ctx* c, const float* phi, const float* u, const float* p
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = true;
+    c->step_count = 0;
     return LBM_OK;
 }
 
@@ -408,22 +482,32 @@ int lbm_step(lbm_ctx* c, int64_t nsteps)
     if (!c) return LBM_ERR_ARG;
     if (nsteps < 0) return fail(c, LBM_ERR_ARG, "nsteps < 0");
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "lbm_step before lbm_init_fields/lbm_set_populations");
-    // whole graphs of kStepGraph steps (not while kernel timing is on: its
-    // events are recorded between the launches), then single steps
-    while (!c->timing && !c->no_graphs && nsteps >= kStepGraph) {
-        const int slot = (c->b.fA == c->f0 ? 0 : 1) | (c->b.gA == c->g0 ? 0 : 2);
-        if (!c->graph[slot] && capture_steps(c, slot) != cudaSuccess) {
-            cudaGetLastError();                 // a refused capture leaves no sticky error
-            c->no_graphs = true;
-            break;
+    const int64_t k = c->p.diag_every;
+    while (nsteps > 0) {
+        // up to the next in-step diagnostic (a12: every k steps)
+        const int64_t chunk = k > 0 ? std::min(nsteps, k - c->step_count % k) : nsteps;
+        const int r = run_steps(c, chunk);
+        if (r != LBM_OK) return r;
+        c->step_count += chunk;
+        nsteps -= chunk;
+        if (k > 0 && c->step_count % k == 0) {
+            DiagPartial d;
+            const int rd = run_diag(c, 1e-3, &d);
+            if (rd != LBM_OK) return rd;
+            fill_diag(d, &c->last_diag);
+            c->last_diag_step = c->step_count;
+            if (d.nonfinite)
+                return fail(c, LBM_ERR_DIVERGED, "non-finite populations at step " + std::to_string(c->step_count));
         }
-        LBM_CUDA(c, cudaGraphLaunch(c->graph[slot], c->stream));
-        nsteps -= kStepGraph;
     }
-    for (int64_t s = 0; s < nsteps; ++s) {
-        cudaError_t e = dispatch_step(c);
-        if (e != cudaSuccess) return cuda_fail(c, e, "step kernels");
-    }
+    return LBM_OK;
+}
+
+int lbm_diag_last(const lbm_ctx* c, lbm_diag_out* out, int64_t* step)
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    *out = c->last_diag;
+    if (step) *step = c->last_diag_step;
     return LBM_OK;
 }
 
@@ -495,6 +579,7 @@ int lbm_set_populations(lbm_ctx* c, const float* f, const float* g, int on_devic
     if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = true;
+    c->step_count = 0;
     return LBM_OK;
 }
 
@@ -502,21 +587,10 @@ int lbm_diag(lbm_ctx* c, double phase_eps, lbm_diag_out* out)
 {
     if (!c || !out) return LBM_ERR_ARG;
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
-    cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
-        return decltype(l)::diag(c->dp, c->b, phase_eps, c->diag_part, c->diag_nparts, c->diag_res, c->stream);
-    });
-    if (e != cudaSuccess) return cuda_fail(c, e, "diag kernels");
     DiagPartial r;
-    LBM_CUDA(c, cudaMemcpyAsync(&r, c->diag_res, sizeof r, cudaMemcpyDeviceToHost, c->stream));
-    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    out->sum_phi = r.sum_phi;
-    out->sum_p_in = r.sum_p_in;
-    out->sum_p_out = r.sum_p_out;
-    out->max_speed = r.max_speed;
-    out->n_in = r.n_in;
-    out->n_out = r.n_out;
-    out->finite = r.nonfinite ? 0 : 1;
-    out->reserved = 0;
+    const int rd = run_diag(c, phase_eps, &r);
+    if (rd != LBM_OK) return rd;
+    fill_diag(r, out);
     if (r.nonfinite) return fail(c, LBM_ERR_DIVERGED, "non-finite populations");
     return LBM_OK;
 }

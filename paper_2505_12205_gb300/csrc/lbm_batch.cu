@@ -27,6 +27,7 @@ extern template struct lbm::BatchLaunch<lbm::D3Q19, lbm::StoreF16, 32, 8>;
 namespace lbm {
 int api_validate(const lbm_params* p, std::string& why);
 DevParams api_make_dev(const lbm_params* p, int64_t N);
+void api_fill_diag(const DiagPartial& r, lbm_diag_out* out);
 }  // namespace lbm
 
 using lbm::BatchCase;
@@ -450,14 +451,7 @@ int lbm_batch_diag(lbm_batch* b, int32_t c, double phase_eps, lbm_diag_out* out)
     DiagPartial r;
     BATCH_CUDA(b, cudaMemcpyAsync(&r, b->part + kDiagParts, sizeof r, cudaMemcpyDeviceToHost, b->stream));
     BATCH_CUDA(b, cudaStreamSynchronize(b->stream));
-    out->sum_phi = r.sum_phi;
-    out->sum_p_in = r.sum_p_in;
-    out->sum_p_out = r.sum_p_out;
-    out->max_speed = r.max_speed;
-    out->n_in = r.n_in;
-    out->n_out = r.n_out;
-    out->finite = r.nonfinite ? 0 : 1;
-    out->reserved = 0;
+    lbm::api_fill_diag(r, out);
     if (r.nonfinite) return bfail(b, LBM_ERR_DIVERGED, "non-finite populations");
     return LBM_OK;
 }

@@ -875,10 +875,13 @@ k_step_batch(const BatchCase* __restrict__ cases, const int2* __restrict__ items
 }
 
 // Velocity inlet (f) and phase-field inlet (g) on the low face of the last
-// axis, applied to the post-streaming populations in B (App. B; the force
-// shift is omitted at the inlet, p* cancels, the tangential excess momentum
-// is shared by the two unknowns that carry each tangential component, the
-// phase excess by the unknowns with a tangential component).
+// axis, applied to the post-streaming populations in B (App. B).  The
+// velocity rule holds for f' = f + F/2 (eq:velocity_boundary_u) with the force
+// the next macroscopic update finds at the node: derivatives of phi are not
+// evaluated at the inlet, so F is the body force (rho(phi_in) - rho_ref) g
+// (eq:gravity_force).  p* cancels, the tangential excess momentum is shared
+// by the two unknowns that carry each tangential component, the phase excess
+// by the unknowns with a tangential component.
 template <class L, class S>
 __global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __restrict__ fB, typename S::T* __restrict__ gB)
 {
@@ -893,6 +896,11 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __re
     const float phin = P.phi_in[t], un = P.u_in[t];
     const float ux = 0.0f, uy = (L::D == 2) ? un : 0.0f, uz = (L::D == 3) ? un : 0.0f;
     const float uu = un * un;
+    // F_a / 2 = 1.5 w_a e_a . F / rho with F = (rho - rho_ref) g, rho of phi_in
+    const float rin = fmaf(fminf(fmaxf(phin, 0.0f), 1.0f), P.rho_H - P.rho_L, P.rho_L);
+    const float hs = (rin - P.rho_ref) * (1.5f / rin);
+    const float hx = hs * P.gx, hy = hs * P.gy, hz = hs * P.gz;
+    auto half = [&](int a) { return L::w(a) * (float(L::ex(a)) * hx + float(L::ey(a)) * hy + float(L::ez(a)) * hz); };
     // Gamma_a = w_a + gdev_a; the inlet uses f^eq without p* (it cancels)
     float f[Q], g[Q];
 #pragma unroll
@@ -908,7 +916,7 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __re
         const int t0 = L::ex(a), t1 = (L::D == 2) ? 0 : L::ey(a);
         if (en == 0) {
             const float d = gdev<L>(a, ux, uy, uz, uu);
-            const float fneq = f[a] - d;
+            const float fneq = (f[a] + half(a)) - d;        // f' - feq (p* cancels)
             if (t0) Mx += float(t0) * fneq;
             if (t1) My += float(t1) * fneq;
             theta += g[a] - phin * (L::w(a) + d);     // eq:excess_density
@@ -925,7 +933,8 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __re
         const int ab = L::opp(a);
         const float da = gdev<L>(a, ux, uy, uz, uu), db = gdev<L>(ab, ux, uy, uz, uu);
         const float eM = float(t0) * Mx + float(t1) * My;
-        fn[32 * a] = S::ef(f[ab] + (da - db) - 0.5f * eM, L::w(a), P);   // eq:velocity_boundary_distribution
+        // eq:velocity_boundary_distribution on f' = f + F/2, shifted back
+        fn[32 * a] = S::ef(((f[ab] + half(ab)) + (da - db) - 0.5f * eM) - half(a), L::w(a), P);
         const float corr = (t0 != 0 || t1 != 0) ? th_n : 0.0f;
         // eq:unknown_distribution_*: g_a = geq_a - (g_abar - geq_abar) - corr, w_a = w_abar
         gn[32 * a] = S::eg(phin * (2.0f * L::w(a) + da + db) - g[ab] - corr, L::w(a));

@@ -32,20 +32,24 @@ namespace lbm {
 int api_validate(const lbm_params* p, std::string& why);
 DevParams api_make_dev(const lbm_params* p, int64_t N);
 void api_set_thread_error(const std::string& msg);
+void api_fill_diag(const DiagPartial& r, lbm_diag_out* out);
 }  // namespace lbm
 
 namespace {
 
 constexpr int64_t kMaxNodes = int64_t(1) << 21;     // 2,097,152 nodes
 constexpr int kMaxFace = 1 << 16;                   // 65,536 inlet-plane nodes
-constexpr int kParts = 2 * 152;                     // reduction blocks
-constexpr size_t kPartFloats = (kParts + 1) * sizeof(lbm::DiagPartial) / sizeof(float);
+// Width of the first reduction pass: a fixed number of blocks, each reducing a
+// grid-strided share of the nodes (two per SM of a 152-SM GB300; any value
+// gives the same sums up to FP64 rounding order, which stays fixed).
+constexpr int kReduceBlocks = 2 * 152;
+constexpr size_t kPartFloats = (kReduceBlocks + 1) * sizeof(lbm::DiagPartial) / sizeof(float);
 constexpr size_t kScratchFloats = size_t(kMaxNodes) + 2 * size_t(kMaxFace) + kPartFloats;
 
 static_assert(sizeof(lbm::DiagPartial) % sizeof(double) == 0, "partials must stay 8-byte aligned");
 static_assert((size_t(kMaxNodes) + 2 * size_t(kMaxFace)) % 2 == 0, "partials must start 8-byte aligned");
 
-// layout: phi [kMaxNodes] | phi_in, u_in [2 * kMaxFace] | partials [kParts + 1]
+// layout: phi [kMaxNodes] | phi_in, u_in [2 * kMaxFace] | partials [kReduceBlocks + 1]
 static __device__ __align__(256) float g_scratch[kScratchFloats];
 
 constexpr int kMaxDevices = 64;
@@ -62,7 +66,9 @@ int fail(int code, const std::string& msg)
 // Device address of the static scratch on the current device.  In host code
 // g_scratch names a host-side stand-in, so the address is looked up once per
 // device (the first call on a device does this; make that first call before
-// any stream capture).
+// any stream capture).  The cached address belongs to the device's primary
+// context: it is not valid after cudaDeviceReset or under another driver
+// context bound to the same device.
 int scratch_address(float** out)
 {
     int dev = 0;
@@ -88,15 +94,20 @@ extern "C" int lbm_diag_noalloc(const lbm_params* p, const float* f, const float
 {
     if (!p || !f || !g || !out) return fail(LBM_ERR_ARG, "lbm_diag_noalloc: NULL argument");
     std::string why;
+    // the planes are float32 whatever storage format p names (the layout of
+    // lbm_get_populations, which decodes 16-bit states)
+    lbm_params pf = *p;
+    pf.storage = 0;
+    p = &pf;
     if (lbm::api_validate(p, why) != 0) return fail(LBM_ERR_ARG, "lbm_diag_noalloc: " + why);
-    if (p->storage != 0) return fail(LBM_ERR_ARG, "lbm_diag_noalloc: populations must be float32 (storage 0)");
     const int64_t N = int64_t(p->nx) * p->ny * p->nz;
     const int D = p->lattice == LBM_D2Q9 ? 2 : 3;
     const int64_t nface = D == 2 ? p->nx : int64_t(p->nx) * p->ny;
+    const bool inlet = p->bc[2 * (D - 1)] == LBM_BC_INLET;
     if (N > kMaxNodes)
         return fail(LBM_ERR_ARG, "lbm_diag_noalloc: grid of " + std::to_string(N) +
                                      " nodes exceeds its static scratch of " + std::to_string(kMaxNodes) + " nodes");
-    if (nface > kMaxFace)
+    if (inlet && nface > kMaxFace)
         return fail(LBM_ERR_ARG, "lbm_diag_noalloc: inlet plane of " + std::to_string(nface) +
                                      " nodes exceeds its static scratch of " + std::to_string(kMaxFace) + " nodes");
     float* base = nullptr;
@@ -108,7 +119,7 @@ extern "C" int lbm_diag_noalloc(const lbm_params* p, const float* f, const float
     dp.phi_in = base + kMaxNodes;
     dp.u_in = base + kMaxNodes + kMaxFace;
     lbm::DiagPartial* part = reinterpret_cast<lbm::DiagPartial*>(base + kMaxNodes + 2 * kMaxFace);
-    lbm::DiagPartial* res = part + kParts;
+    lbm::DiagPartial* res = part + kReduceBlocks;
     lbm::Buffers b;
     b.fA = const_cast<float*>(f);
     b.gA = const_cast<float*>(g);
@@ -117,8 +128,7 @@ extern "C" int lbm_diag_noalloc(const lbm_params* p, const float* f, const float
     b.phi = base;
 
     cudaError_t e = cudaSuccess;
-    const int L = D - 1;
-    if (p->bc[2 * L] == LBM_BC_INLET) {
+    if (inlet) {
         e = D == 2 ? lbm::Launch<lbm::D2Q9, lbm::StoreF32>::inlet_profile(dp, p->inlet_center[0], 0.0, p->inlet_radius, p->W,
                                                           p->inlet_u, base + kMaxNodes,
                                                           base + kMaxNodes + kMaxFace, s)
@@ -127,20 +137,13 @@ extern "C" int lbm_diag_noalloc(const lbm_params* p, const float* f, const float
                                                            base + kMaxNodes + kMaxFace, s);
     }
     if (e == cudaSuccess)
-        e = D == 2 ? lbm::Launch<lbm::D2Q9, lbm::StoreF32>::diag_planar(dp, b, phase_eps, part, kParts, res, s)
-                   : lbm::Launch<lbm::D3Q19, lbm::StoreF32>::diag_planar(dp, b, phase_eps, part, kParts, res, s);
+        e = D == 2 ? lbm::Launch<lbm::D2Q9, lbm::StoreF32>::diag_planar(dp, b, phase_eps, part, kReduceBlocks, res, s)
+                   : lbm::Launch<lbm::D3Q19, lbm::StoreF32>::diag_planar(dp, b, phase_eps, part, kReduceBlocks, res, s);
     lbm::DiagPartial h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, res, sizeof h, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("lbm_diag_noalloc: ") + cudaGetErrorString(e));
-    out->sum_phi = h.sum_phi;
-    out->sum_p_in = h.sum_p_in;
-    out->sum_p_out = h.sum_p_out;
-    out->max_speed = h.max_speed;
-    out->n_in = h.n_in;
-    out->n_out = h.n_out;
-    out->finite = h.nonfinite ? 0 : 1;
-    out->reserved = 0;
+    lbm::api_fill_diag(h, out);
     if (h.nonfinite) return fail(LBM_ERR_DIVERGED, "lbm_diag_noalloc: non-finite populations");
     return LBM_OK;
 }

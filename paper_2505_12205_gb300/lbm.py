@@ -27,7 +27,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOU
 EXPORTS = ["lbm_create", "lbm_init_fields", "lbm_step", "lbm_get_fields", "lbm_get_populations",
            "lbm_set_populations", "lbm_diag", "lbm_sync", "lbm_shape", "lbm_last_error",
            "lbm_destroy", "lbm_collide_cells", "lbm_set_timing", "lbm_get_timing",
-           "lbm_diag_noalloc", "lbm_advect_phase", "lbm_jet_stats", "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step",
+           "lbm_diag_noalloc", "lbm_diag_last", "lbm_advect_phase", "lbm_jet_stats", "lbm_batch_create", "lbm_batch_init_fields", "lbm_batch_step",
            "lbm_batch_get_fields", "lbm_batch_diag", "lbm_batch_get_plan", "lbm_batch_set_plan",
            "lbm_batch_tune", "lbm_batch_sync", "lbm_batch_last_error", "lbm_batch_destroy"]
 
@@ -40,9 +40,10 @@ class LbmParams(ctypes.Structure):
         ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
         ("bc", ctypes.c_int32 * 6),
         ("visc_model", ctypes.c_int32), ("storage", ctypes.c_int32),
-        ("outlet_scheme", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("outlet_scheme", ctypes.c_int32), ("diag_every", ctypes.c_int32),
         ("rho_L", ctypes.c_double), ("rho_H", ctypes.c_double),
         ("tau_L", ctypes.c_double), ("tau_H", ctypes.c_double),
+        ("mu_ratio", ctypes.c_double),
         ("sigma", ctypes.c_double), ("W", ctypes.c_double),
         ("mobility", ctypes.c_double),
         ("force", ctypes.c_double * 3), ("rho_ref", ctypes.c_double),
@@ -59,6 +60,7 @@ class LbmDiagOut(ctypes.Structure):
         ("sum_p_out", ctypes.c_double), ("max_speed", ctypes.c_double),
         ("n_in", ctypes.c_int64), ("n_out", ctypes.c_int64),
         ("finite", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("dp_laplace", ctypes.c_double),
     ]
 
 
@@ -116,6 +118,7 @@ def load(path: str = LIB_PATH):
     lib.lbm_destroy.argtypes = [vp]
     lib.lbm_collide_cells.argtypes = [P, i64, f32p, f32p, f32p, f32p, f32p, f32p, vp]
     lib.lbm_diag_noalloc.argtypes = [P, f32p, f32p, ctypes.c_double, ctypes.POINTER(LbmDiagOut), vp]
+    lib.lbm_diag_last.argtypes = [vp, ctypes.POINTER(LbmDiagOut), ctypes.POINTER(ctypes.c_int64)]
     lib.lbm_set_timing.argtypes = [vp, ctypes.c_int]
     lib.lbm_advect_phase.argtypes = [vp, f32p, ctypes.c_double, i64, ctypes.c_int]
     lib.lbm_jet_stats.argtypes = [vp, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(LbmJetStats)]
@@ -148,8 +151,10 @@ def make_params(p: dict) -> LbmParams:
     s.visc_model = int(p.get("visc_model", 0))
     s.storage = int(p.get("storage", 0))
     s.outlet_scheme = int(p.get("outlet_scheme", 0))
+    s.diag_every = int(p.get("diag_every", 0))
     s.rho_L, s.rho_H = float(p["rho_L"]), float(p["rho_H"])
-    s.tau_L, s.tau_H = float(p["tau_L"]), float(p["tau_H"])
+    s.tau_L, s.tau_H = float(p.get("tau_L", 0.0)), float(p["tau_H"])
+    s.mu_ratio = float(p.get("mu_ratio", 0.0))
     s.sigma, s.W, s.mobility = float(p["sigma"]), float(p["W"]), float(p["mobility"])
     g = list(p.get("force", (0.0, 0.0, 0.0))) + [0.0] * 3
     for i in range(3):
@@ -221,25 +226,34 @@ def lbm_step(ctx, nsteps: int):
     _check(lib, lib.lbm_step(ctx, int(nsteps)), ctx)
 
 
+def _dims(ctx):
+    """(N, Q, D) of a context."""
+    n, q = lbm_shape(ctx)
+    return n, q, 2 if q == 9 else 3
+
+
 def lbm_get_fields(ctx, phi=None, u=None, p=None):
     lib = load()
-    a, k1 = _ptr(phi)
-    b, k2 = _ptr(u)
-    c, k3 = _ptr(p)
+    n, _, d = _dims(ctx)
+    a, k1 = _ptr(phi, n)
+    b, k2 = _ptr(u, n * d)
+    c, k3 = _ptr(p, n)
     _check(lib, lib.lbm_get_fields(ctx, a, b, c, _one_kind(k1, k2, k3)), ctx)
 
 
 def lbm_get_populations(ctx, f=None, g=None):
     lib = load()
-    a, k1 = _ptr(f)
-    b, k2 = _ptr(g)
+    n, q, _ = _dims(ctx)
+    a, k1 = _ptr(f, n * q)
+    b, k2 = _ptr(g, n * q)
     _check(lib, lib.lbm_get_populations(ctx, a, b, _one_kind(k1, k2)), ctx)
 
 
 def lbm_set_populations(ctx, f, g):
     lib = load()
-    a, k1 = _ptr(f)
-    b, k2 = _ptr(g)
+    n, q, _ = _dims(ctx)
+    a, k1 = _ptr(f, n * q)
+    b, k2 = _ptr(g, n * q)
     _check(lib, lib.lbm_set_populations(ctx, a, b, _one_kind(k1, k2)), ctx)
 
 
@@ -250,6 +264,15 @@ def lbm_diag(ctx, phase_eps: float = 1e-3) -> dict:
     if code not in (LBM_OK, LBM_ERR_DIVERGED):
         _check(lib, code, ctx)
     return {k: getattr(out, k) for k, _ in LbmDiagOut._fields_ if k != "reserved"}
+
+
+def lbm_diag_last(ctx):
+    """(record, step) of the last in-step diagnostic of lbm_step (step -1 if none)."""
+    lib = load()
+    out = LbmDiagOut()
+    step = ctypes.c_int64()
+    _check(lib, lib.lbm_diag_last(ctx, ctypes.byref(out), ctypes.byref(step)), ctx)
+    return {k: getattr(out, k) for k, _ in LbmDiagOut._fields_ if k != "reserved"}, step.value
 
 
 def lbm_sync(ctx):
@@ -276,7 +299,8 @@ def lbm_destroy(ctx):
 
 def lbm_advect_phase(ctx, u, scale: float = 1.0, nsteps: int = 1):
     lib = load()
-    a, k = _ptr(u)
+    n, _, d = _dims(ctx)
+    a, k = _ptr(u, n * d)
     _check(lib, lib.lbm_advect_phase(ctx, a, float(scale), int(nsteps), k), ctx)
 
 
@@ -310,8 +334,14 @@ def lbm_diag_noalloc(params: dict, f, g, phase_eps: float = 1e-3, stream=None) -
     without a context and without any device allocation (see include/lbm.h)."""
     lib = load()
     s = make_params(params)
+    q = 9 if s.lattice == LBM_D2Q9 else 19
+    n = q * s.nx * s.ny * s.nz
+    pf, kf = _ptr(f, n)
+    pg, kg = _ptr(g, n)
+    if kf != 1 or kg != 1 or not (f.is_cuda and g.is_cuda):
+        raise ValueError("lbm_diag_noalloc takes CUDA float32 tensors of Q * nx * ny * nz elements")
     out = LbmDiagOut()
-    code = lib.lbm_diag_noalloc(ctypes.byref(s), _ptr(f)[0], _ptr(g)[0], float(phase_eps),
+    code = lib.lbm_diag_noalloc(ctypes.byref(s), pf, pg, float(phase_eps),
                                 ctypes.byref(out), ctypes.c_void_p(_stream_handle(stream)))
     if code not in (LBM_OK, LBM_ERR_DIVERGED):
         _check(lib, code)
@@ -374,6 +404,9 @@ class LBM:
 
     def sync(self):
         lbm_sync(self._h)
+
+    def diag_last(self):
+        return lbm_diag_last(self._h)
 
     def fields(self):
         phi = np.empty(self.shape, np.float32)

@@ -174,19 +174,70 @@ def test_drop2d_128_parity_1000_steps(lib, orc, report):
 
 
 def test_rt2d_parity_full_size(lib, orc, report):
-    """256 x 1024 Rayleigh-Taylor (At = 0.5, Re = 3000, W = 5), 200 steps."""
+    """256 x 1024 Rayleigh-Taylor (At = 0.5, Re = 3000, W = 5), 1000 steps:
+    relative L2 of phi and u <= 1e-5 (the float32 bound)."""
     p, phi, u, ps = C.rayleigh_taylor2d()
     sim = lib.LBM(p)
     sim.init_fields(phi, u, ps)
-    sim.step(200)
+    sim.step(1000)
     g_phi, g_u, _ = sim.fields()
     o = orc.Oracle(p)
     o.init_fields(phi, u, ps)
-    o.step(200)
+    o.step(1000)
     r_phi, r_u, _ = o.fields()
-    report("rt2d_200", phi_l2=rel_l2(g_phi, r_phi), u_l2=rel_l2(g_u, r_u))
+    report("rt2d_1000", phi_l2=rel_l2(g_phi, r_phi), u_l2=rel_l2(g_u, r_u))
     assert rel_l2(g_phi, r_phi) <= 1e-5
     assert rel_l2(g_u, r_u) <= 1e-5
+
+
+def test_jet3d_quarter_scale_parity_500_steps(lib, orc, report):
+    """The 3D jet at a quarter of the 256 x 256 x 1024 workload's size
+    (64 x 64 x 256, nozzle radius 4, same faces and physics), 500 steps:
+    relative L2 of phi and u <= 1e-5."""
+    p, phi, u, ps = C.jet3d(nx=64, ny=64, nz=256, Rn=4.0)
+    sim = lib.LBM(p)
+    sim.init_fields(phi, u, ps)
+    sim.step(500)
+    g_phi, g_u, _ = sim.fields()
+    o = orc.Oracle(p)
+    o.init_fields(phi, u, ps)
+    o.step(500)
+    r_phi, r_u, _ = o.fields()
+    report("jet3d_quarter_500", phi_l2=rel_l2(g_phi, r_phi), u_l2=rel_l2(g_u, r_u))
+    assert rel_l2(g_phi, r_phi) <= 1e-5
+    assert rel_l2(g_u, r_u) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["d2q9_jet", "d3q19_jet", "d3q19_aligned_jet"])
+def test_inlet_force_shift_matches_the_oracle(lib, orc, report, name):
+    """A body force with normal and tangential components (3e-4, far above
+    the jets' gravity): the inlet's velocity rule acts on f' = f + F/2
+    (eq:velocity_boundary_u), populations after one and three steps equal the
+    oracle's, and the velocity the GPU reports at inlet nodes is u_in."""
+    lat, (nz, ny, nx), bc = STEP_CASES[name]
+    p = C.base_params(lat, nx, ny, nz, rho_L=0.05, tau_L=0.3, tau_H=0.1, sigma=2e-3, W=4.0,
+                      force=[3e-4, -2e-4, 3e-4], rho_ref=0.05, inlet_u=0.04,
+                      inlet_center=[nx / 2.0 - 0.3, ny / 2.0 + 0.2], inlet_radius=3.5)
+    p["bc"] = bc
+    f, g = C.random_state(p, seed_offset=77)
+    o = orc.Oracle(p)
+    o.set_populations(f, g)
+    sim = lib.LBM(p)
+    sim.set_populations(f.astype(np.float32), g.astype(np.float32))
+    for n in (1, 2):
+        o.step(n)
+        sim.step(n)
+        gf, gg = sim.populations()
+        rf, rg = o.populations()
+        assert close(gg, rg) and close(gf, rf), (np.abs(gf - rf).max(), np.abs(gg - rg).max())
+    D = 2 if lat == 0 else 3
+    u = sim.fields()[1]
+    ui = u[:, 0, 0, :] if lat == 0 else u[:, 0].reshape(D, -1)
+    r_u = o.fields()[1]
+    ri = r_u[:, 0, 0, :] if lat == 0 else r_u[:, 0].reshape(D, -1)
+    report("inlet_force_" + name, u_inlet_max=np.abs(ui - ri).max())
+    assert np.abs(ui - ri).max() < 1e-6
+    assert np.abs(ri[:D - 1]).max() < 1e-12           # tangential u_in = 0
 
 
 def test_jet3d_aligned_parity(lib, orc, report):
@@ -271,6 +322,52 @@ def test_invalid_parameters_rejected(lib):
     with pytest.raises(lib.LbmError) as e:
         sim.step(1)                      # no state yet
     assert e.value.code == lib.LBM_ERR_STATE
+
+
+def test_in_step_divergence_check(lib):
+    """diag_every = k: lbm_step runs the FP64 diagnostics after every k-th
+    step and stops with LBM_ERR_DIVERGED at the first one that finds a
+    non-finite population (planted on the host through
+    lbm_set_populations); the record says where."""
+    p, phi, u, ps = C.drop2d(n=32, R=8.0)
+    p["diag_every"] = 4
+    sim = lib.LBM(p)
+    sim.init_fields(phi, u, ps)
+    sim.step(9)                          # records at steps 4 and 8
+    rec, step = sim.diag_last()
+    assert step == 8 and rec["finite"] == 1
+    d = sim.diag()
+    sim.step(3)                          # 12: a record, still finite
+    rec, step = sim.diag_last()
+    assert step == 12 and abs(rec["sum_phi"] / d["sum_phi"] - 1) < 1e-6
+    f, g = sim.populations()
+    f[3, 0, 5, 7] = np.nan
+    sim.set_populations(f, g)            # the step count restarts at 0
+    with pytest.raises(lib.LbmError) as e:
+        sim.step(10)
+    assert e.value.code == lib.LBM_ERR_DIVERGED
+    assert "step 4" in lib.lbm_last_error(sim._h)
+    rec, step = sim.diag_last()
+    assert step == 4 and rec["finite"] == 0
+    assert sim.diag()["finite"] == 0     # the state stays readable
+
+
+def test_mu_ratio_sets_tau_L(lib):
+    """mu_ratio > 0 replaces tau_L by tau_H (rho_H / rho_L) / mu_ratio: the
+    same run as with that tau_L given, bit for bit."""
+    p, phi, u, ps = C.drop2d(n=48, R=12.0)
+    q = dict(p)
+    q["tau_L"] = 0.0
+    q["mu_ratio"] = 100.0
+    assert abs(p["tau_L"] - p["tau_H"] * (p["rho_H"] / p["rho_L"]) / 100.0) < 1e-12
+    a, b = lib.LBM(p), lib.LBM(q)
+    a.init_fields(phi, u, ps)
+    b.init_fields(phi, u, ps)
+    a.step(30)
+    b.step(30)
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
 
 
 def test_diag_detects_non_finite(lib):

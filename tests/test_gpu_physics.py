@@ -68,16 +68,20 @@ def test_capillary_wave_vs_prosperetti(lib, report):
 
 
 def test_laplace_3d_drop(lib, report):
+    """tab:laplace_errors: 100^3, R = 25, sigma = 1e-3, 50,000 iterations, the
+    paper reports 0.62 %.  eq:laplace_law takes R as the radius of the drop in
+    its equilibrium state: here the radius of the sphere holding the drop's
+    phase volume, (3 sum(phi) / (4 pi))^(1/3)."""
     R, sigma = 25.0, 1e-3
     p, phi, u, ps = C.drop3d(n=100, R=R, sigma=sigma, W=4.0, tau_H=0.5)
     sim = lib.LBM(p)
     sim.init_fields(phi, u, ps)
-    sim.step(20000)
+    sim.step(50000)
     d = sim.diag(1e-3)
-    dp = d["sum_p_in"] / d["n_in"] - d["sum_p_out"] / d["n_out"]
-    err = dp / (2 * sigma / R) - 1
-    report("laplace_3d_R25", rel_err=err, dp=dp, mass=d["sum_phi"])
+    dp = d["dp_laplace"]
+    r_eq = (3.0 * d["sum_phi"] / (4.0 * np.pi)) ** (1.0 / 3.0)
+    err = dp / (2 * sigma / r_eq) - 1
+    err_r0 = dp / (2 * sigma / R) - 1
+    report("laplace_3d_R25", rel_err=err, rel_err_initial_radius=err_r0, r_eq=r_eq, dp=dp, mass=d["sum_phi"])
     assert d["finite"] == 1
-    # the paper reports 0.62 % for R = 25, sigma = 1e-3 after 50,000 iterations;
-    # after 20,000 steps the pressure jump is still about 3 % below sigma / R
-    assert abs(err) < 0.04
+    assert abs(err) < 0.015

@@ -37,10 +37,33 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_params_struct_layout(lib):
-    # natural alignment of the C struct: 14 int32 then 16 doubles
-    assert ctypes.sizeof(lib.LbmParams) == 14 * 4 + 16 * 8
+    # natural alignment of the C struct: 14 int32 then 17 doubles
+    assert ctypes.sizeof(lib.LbmParams) == 14 * 4 + 17 * 8
     assert lib.LbmParams.rho_L.offset == 56
-    assert ctypes.sizeof(lib.LbmDiagOut) == 4 * 8 + 2 * 8 + 2 * 4
+    assert lib.LbmParams.mu_ratio.offset == 88
+    assert ctypes.sizeof(lib.LbmDiagOut) == 4 * 8 + 2 * 8 + 2 * 4 + 8
+
+
+@pytest.mark.parametrize("change", ["W", "inlet_without_outlet", "diag_every", "mu_ratio", "tau_L"])
+def test_create_rejects_invalid_parameters_before_touching_a_device(lib, change):
+    """Parameter validation of lbm_create (W >= 2, an inlet needs the outlet
+    opposite, diag_every >= 0, mu_ratio >= 0, tau_L > 0 unless mu_ratio sets
+    it) runs before any CUDA call, so it is checked here without a GPU."""
+    import lbm_cases as C
+    p = C.jet2d(nx=16, ny=16, half_width=3.0, W=4.0)[0]
+    if change == "W":
+        p["W"] = 1.5
+    elif change == "inlet_without_outlet":
+        p["bc"] = [0, 0, 2, 1, 0, 0]
+    elif change == "diag_every":
+        p["diag_every"] = -1
+    elif change == "mu_ratio":
+        p["mu_ratio"] = -2.0
+    else:
+        p["tau_L"] = 0.0
+    with pytest.raises(lib.LbmError) as e:
+        lib.LBM(p)
+    assert e.value.code == lib.LBM_ERR_ARG, lib.lbm_last_error()
 
 
 def test_no_gpu_means_an_error_not_a_fallback(lib):

@@ -7,8 +7,12 @@ eq:chemical_potential, a c_s^2 slip in eq:gradient_phi, a transposed velocity
 component, a missing 1/c_s^2 in eq:force_term, a flipped pressure force
 (eq:pressure_force), a flipped viscous force (eq:viscous_force_wmrt), the
 wrong stress row relaxed at s_nu, bounce-back into the wrong slot
-(eq:no_slip_f), the inlet's tangential factor N = 4 as printed, and a missing
-1/2 in the g equilibrium shift (eq:equilibrium_with_force).
+(eq:no_slip_f), the inlet's tangential factor N = 4 as printed, a missing
+1/2 in the g equilibrium shift (eq:equilibrium_with_force), the velocity
+inlet applied to f instead of f' = f + F/2 (eq:velocity_boundary_u), and three
+outlet mistakes (eq:implicit_convective): the old and new layers swapped, the
+outlet speed not clamped to [0, 1], and the speed taken on layer N instead of
+N-1.
 """
 import os
 import subprocess
@@ -19,8 +23,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "lbm_oracle.c")
 
-FAST = ["tests/test_oracle_lattice.py", "tests/test_oracle_physics.py", "-m", "not slow"]
-ALL = ["tests/test_oracle_lattice.py", "tests/test_oracle_physics.py"]
+FAST = ["tests/test_oracle_lattice.py", "tests/test_oracle_faces.py", "tests/test_oracle_physics.py",
+        "-m", "not slow"]
+ALL = ["tests/test_oracle_lattice.py", "tests/test_oracle_faces.py", "tests/test_oracle_physics.py"]
 
 MUTANTS = {
     "mu_phi_printed_sign": (
@@ -48,8 +53,20 @@ MUTANTS = {
         "c->fB[i * Q + a] = c->fs[i * Q + c->opp[a]];",
         "c->fB[i * Q + a] = c->fs[i * Q + a];", ALL),
     "inlet_factor_quarter": (
-        "f[a] = f[ab] + (Ga - Gab) - 0.5 * eM;",
-        "f[a] = f[ab] + (Ga - Gab) - 0.25 * eM;", FAST),
+        "double fpa = fp[ab] + (Ga - Gab) - 0.5 * eM;",
+        "double fpa = fp[ab] + (Ga - Gab) - 0.25 * eM;", FAST),
+    "inlet_missing_force_shift": (
+        "half[a] = 0.5 * c->w[a] * eF / (rho * CS2);",
+        "half[a] = 0.0;", FAST),
+    "outlet_swapped_layers": (
+        "fB[iN * Q + a] = (fA[iN * Q + a] + lam * fB[iM * Q + a]) / (1.0 + lam);",
+        "fB[iN * Q + a] = (fB[iM * Q + a] + lam * fA[iN * Q + a]) / (1.0 + lam);", FAST),
+    "outlet_unclamped": (
+        "double lam = U < 0.0 ? 0.0 : (U > 1.0 ? 1.0 : U);",
+        "double lam = U;", FAST),
+    "outlet_speed_wrong_layer": (
+        "int64_t iM = (c->D == 2) ? nid(c, t0, nL - 2, 0) : nid(c, t0, t1, nL - 2);",
+        "int64_t iM = (c->D == 2) ? nid(c, t0, nL - 1, 0) : nid(c, t0, t1, nL - 1);", FAST),
     "g_shift_missing_half": (
         "double gbar = geq - 0.5 * Fphi;",
         "double gbar = geq - Fphi;", ALL),

@@ -44,10 +44,19 @@ def _agree(a, b):
         assert a[k] == b[k], (k, a[k], b[k])
 
 
+def _planar_jet_walls():
+    """A small planar jet (D2Q9 inlet on y = 0, outlet on top) with walled
+    x faces: the 2D inlet profile and the clamped ghost phi of walls."""
+    p, phi, u, ps = C.jet2d(nx=40, ny=64, half_width=5.0, W=4.0, stub=8.0)
+    p["bc"] = [1, 1, 2, 3, 0, 0]
+    return p, phi, u, ps
+
+
 def test_noalloc_diag_matches_context_diag_twice(lib):
     import torch
-    # a periodic 2D drop and a small 3D jet (inlet profile in the scratch too)
-    cases = [C.drop2d(n=64, R=16.0), C.jet3d(nx=24, ny=24, nz=48, Rn=4.0)]
+    # a periodic 2D drop, a small 3D jet (3D inlet profile in the scratch) and
+    # a walled planar jet (2D inlet profile, wall ghosts)
+    cases = [C.drop2d(n=64, R=16.0), C.jet3d(nx=24, ny=24, nz=48, Rn=4.0), _planar_jet_walls()]
     states = [_device_state(lib, c, 30) for c in cases]
     for _ in range(2):                          # two calls in a row per state
         for p, sim, f, g in states:
@@ -59,11 +68,33 @@ def test_noalloc_diag_matches_context_diag_twice(lib):
     assert states[0][1].diag(1e-2)["n_in"] > 0
 
 
+def test_noalloc_ignores_the_storage_format(lib):
+    """The planes are float32 whatever storage p names: parameters copied from
+    a float16 context give that context's reductions of the decoded state."""
+    import torch
+    p, phi, u, ps = C.drop2d(n=48, R=12.0)
+    p = dict(p, storage=1)
+    p_, sim, f, g = _device_state(lib, (p, phi, u, ps), 20)
+    ref = sim.diag(1e-2)
+    got = lib.lbm_diag_noalloc(p, f, g, 1e-2)
+    torch.cuda.synchronize()
+    assert abs(got["sum_phi"] - ref["sum_phi"]) <= 1e-9 * abs(ref["sum_phi"])
+    assert got["n_in"] == ref["n_in"] and got["n_out"] == ref["n_out"]
+
+
 def test_noalloc_rejects_grids_beyond_its_scratch(lib):
     import torch
     p = C.base_params(0, 2048, 2048, 1)        # 4.2 M nodes > 2,097,152
-    f = torch.zeros(9, dtype=torch.float32, device="cuda")
+    # the wrapper checks the buffer sizes itself
+    small = torch.zeros(9, dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        lib.lbm_diag_noalloc(p, small, small)
+    # correctly sized buffers reach the C entry point, which refuses the grid
+    # before any launch
+    f = torch.zeros(9 * 2048 * 2048, dtype=torch.float32, device="cuda")
     with pytest.raises(lib.LbmError) as e:
         lib.lbm_diag_noalloc(p, f, f)
     assert e.value.code == lib.LBM_ERR_ARG
     assert "exceeds" in lib.lbm_last_error()
+    del f
+    torch.cuda.empty_cache()
