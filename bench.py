@@ -307,6 +307,13 @@ def run_gpu(args):
         kname = "k_step_fused<D3Q19,32,6> (phi + collide + push-stream, one pass)"
         extra = {"We": WORKLOAD["We"]}
     p["storage"] = {"fp32": 0, "fp16": 1, "bf16": 2}[args.storage]
+    inplace = args.layout == "inplace"
+    p["layout"] = 1 if inplace else 0
+    p["diag_every"] = args.diag_every
+    if inplace:
+        name += " (in-place layout)"
+        kname = kname.replace("k_step_fused", "k_step_inplace").replace(
+            "(phi + collide + push-stream, one pass)", "(collide + in-place stream, even/odd forms; phi by a pre-pass)")
     elem = 4 if args.storage == "fp32" else 2
     N = p["nx"] * p["ny"] * p["nz"]
     stream = torch.cuda.current_stream()
@@ -349,8 +356,9 @@ def run_gpu(args):
     achieved = bytes_per_lu * N / (step_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS,
-            "traffic": ncu_traffic(args.workload) if (args.storage == "fp32" and not args.grid) else None,
+            "traffic": ncu_traffic(args.workload) if (args.storage == "fp32" and not args.grid and not inplace) else None,
             "kernel": kname,
+            "phi_prepass_ms_per_step": ms_phi / max(nrec, 1),
             "algorithmic_bytes_per_lu": bytes_per_lu, "peak_source": peak_kind + " hbm_gbs",
             "kernel_share_of_step": ms_step / max(ms_phi + ms_step + ms_face, 1e-9)}
 
@@ -392,13 +400,18 @@ def run_gpu(args):
             "config": dict({"workload": name, "lattice": lat,
                             "grid": [p["nx"], p["ny"], p["nz"]], "nodes_per_gpu": N,
                             "storage": args.storage,
+                            "layout": "in place (one copy)" if inplace else "A/B (two copies)",
+                            "diag_every": args.diag_every,
                             "l2": "inputs larger than L2: %.1f GB of populations per GPU vs 129 MB L2"
-                                  % (4 * Q * elem * N / 1e9),
+                                  % ((2 if inplace else 4) * Q * elem * N / 1e9),
                             "parallelism": "replicas" if ws > 1 else "single"}, **extra),
             "hbm_gbs_algorithmic": value / ws * 1e6 * bytes_per_lu / 1e9 if ws == 1 else None,
             "roofline": roof,
             "e2e": e2e,
-            "gpu_launches": (1 + faces) * args.steps,
+            # per step: the fused kernel (+ the phi pre-pass in place) and the
+            # face kernels; per in-step diagnostic: k_phi, k_diag, k_diag_final
+            "gpu_launches": (1 + (1 if inplace else 0) + faces) * args.steps
+                            + (3 * (args.steps // args.diag_every) if args.diag_every else 0),
             "clocks": clk,
             "cpu_baseline": cpu,
         }
@@ -740,6 +753,10 @@ def main():
                     help="population storage format (arithmetic is float32); default fp32 for the "
                          "jet, fp16 for the sweep")
     ap.add_argument("--workload", default="jet", choices=["jet", "rt2d", "sweep", "learned", "jet-sweep", "nn"])
+    ap.add_argument("--layout", default="ab", choices=["ab", "inplace"],
+                    help="population layout of the jet / rt2d workloads: two copies (A/B) or one (in place)")
+    ap.add_argument("--diag-every", type=int, default=100,
+                    help="steps between the in-step FP64 diagnostics (sum phi, finite check) of lbm_step")
     ap.add_argument("--epochs", type=int, default=24, help="training epochs of the learned workload")
     ap.add_argument("--skip", type=int, default=1, help="windows predicted after each passing check (learned)")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,

@@ -82,6 +82,14 @@ typedef enum {
  *  diag_every   steps between the in-step diagnostics of lbm_step (FP64
  *               sum of phi, finite check, Laplace pressure sums; Sec. 5.2,
  *               5.4); 0 = off
+ *  layout       0: two copies of each population set (A/B: the step reads
+ *               one and writes the other; the fastest step); 1: one copy,
+ *               updated in place (AA pattern: steps alternate between writing
+ *               each node's post-collision populations into its own opposite
+ *               slots and reading/writing them at the neighbours), half the
+ *               population memory; each step then forms phi in a separate
+ *               pass first.  Both give the same results, bit for bit.
+ *               lbm_advect_phase needs layout 0.
  *  rho_L, rho_H densities (eq:density_interpolation)
  *  tau_L, tau_H relaxation times, nu = tau c_s^2 (eq:kinematic_viscosity)
  *  mu_ratio     viscosity ratio mu_H / mu_L; when > 0 it replaces tau_L:
@@ -105,6 +113,8 @@ typedef struct {
     int32_t storage;
     int32_t outlet_scheme;
     int32_t diag_every;
+    int32_t layout;
+    int32_t reserved;       /* 0 */
     double rho_L, rho_H, tau_L, tau_H;
     double mu_ratio;
     double sigma, W, mobility;
@@ -131,14 +141,15 @@ typedef struct {
                           0 when either set is empty */
 } lbm_diag_out;
 
-/* Create a context: validate p, allocate the double-buffered populations
- * (2 sets x 2 buffers x Q values per node, rows padded to a multiple of 32
- * nodes, 4 or 2 bytes per value by `storage`) on the current CUDA
+/* Create a context: validate p, allocate the populations (2 sets x 2
+ * buffers, or 1 buffer with layout 1, x Q values per node, rows padded to a
+ * multiple of 32 nodes, 4 or 2 bytes per value by `storage`) on the current CUDA
  * device and bind the CUDA stream `stream` (a cudaStream_t; NULL = the legacy
  * default stream).  Errors: LBM_ERR_ARG (out == NULL, a parameter out of
  * range, unpaired periodic faces, inlet/outlet on another face, last axis
  * shorter than 4 with open faces, an inlet without the outlet on the
- * opposite face, W < 2, a negative diag_every), LBM_ERR_CUDA (no device),
+ * opposite face, W < 2, a negative diag_every, layout not 0 or 1),
+ * LBM_ERR_CUDA (no device),
  * LBM_ERR_OOM.  On failure *out is NULL. */
 int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out);
 
@@ -176,9 +187,12 @@ int lbm_diag_last(const lbm_ctx* ctx, lbm_diag_out* out, int64_t* step);
 int lbm_get_fields(lbm_ctx* ctx, float* phi, float* u, float* p, int on_device);
 
 /* Raw state (checkpoint): the post-streaming populations f and g, each
- * [Q][N] float32.  With float32 storage lbm_set_populations restores it
- * exactly; with 16-bit storage the values are decoded to float32 and
- * encoded again on restore (exact up to that rounding).  Synchronises. */
+ * [Q][N] float32 (either may be NULL in lbm_get_populations), in the same
+ * order whatever the layout.  With float32 storage lbm_set_populations
+ * restores it exactly; with 16-bit storage the values are decoded to float32
+ * and encoded again on restore (exact up to that rounding).  The conversion
+ * goes through a staging buffer of 4 N floats (allocated on first use).
+ * Synchronises. */
 int lbm_get_populations(lbm_ctx* ctx, float* f, float* g, int on_device);
 int lbm_set_populations(lbm_ctx* ctx, const float* f, const float* g, int on_device);
 
@@ -241,8 +255,8 @@ int lbm_destroy(lbm_ctx* ctx);
  * eq:forcing_term and g^eq = phi Gamma(u), then streaming of g with the face
  * rules; f is left as it is.  This is the frozen-velocity mode of the
  * paper's circular interface in a shear flow (Sec. 5.3, eq:velocity_u,
- * eq:velocity_v).  Faces must be periodic, walls or free slip (LBM_ERR_ARG
- * otherwise).
+ * eq:velocity_v).  Faces must be periodic, walls or free slip, and the
+ * layout 0 (LBM_ERR_ARG otherwise).
  * With host u the call synchronises the stream. */
 int lbm_advect_phase(lbm_ctx* ctx, const float* u, double scale, int64_t nsteps, int on_device);
 
@@ -313,7 +327,7 @@ typedef struct {
 
 /* Create a batch of ncases cases from params[0 .. ncases-1] (each validated
  * like lbm_create; all with the same lattice and storage, storage 0 or 1,
- * faces periodic or wall).  Allocates the populations of every case (two
+ * faces periodic or wall, layout 0; diag_every is not used).  Allocates the populations of every case (two
  * buffers per set).  Returns LBM_ERR_ARG, LBM_ERR_CUDA or LBM_ERR_OOM on
  * failure (*out = NULL; text from lbm_batch_last_error(NULL)). */
 int lbm_batch_create(const lbm_params* params, int32_t ncases, void* stream, lbm_batch** out);

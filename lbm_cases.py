@@ -20,8 +20,9 @@ workload sizes used by the benchmark:
     at ((nx-1)/2, (ny-1)/2), periodic box, zero velocity;
   * Rayleigh-Taylor (Sec. 5.5, table tab:rayleigh_spec case a): heavy fluid
     above light, interface y0 = ny/2 + 0.1 L cos(2 pi x / L), walls top and
-    bottom, periodic in x; U0 = sqrt(g L) = 0.04 sets g, the Reynolds,
-    Peclet and capillary numbers set tau_H, M and sigma;
+    bottom, periodic in x, at rest with the hydrostatic pressure of the body
+    force; U0 = sqrt(g L) = 0.04 sets g, the Reynolds, Peclet and capillary
+    numbers set tau_H, M and sigma;
   * liquid jet (Sec. 6): circular plug inlet on the z = 0 face, convective
     outlet on the top z face, periodic sides, gravity along the jet;
   * two-phase Poiseuille (Sec. 5.3), flat interface, single-phase shear wave
@@ -123,10 +124,31 @@ def rayleigh_taylor2d(L=256, height=None, W=5.0, At=0.5, Re=3000.0, Pe=1000.0,
     x = np.arange(nx, dtype=np.float64)
     y0 = ny / 2.0 + 0.1 * L * np.cos(2.0 * np.pi * x / L)
     phi = np.empty((1, ny, nx), np.float32)                  # heavy on top
-    for r0 in range(0, ny, 1024):                            # row blocks: bounded temporaries
-        y = np.arange(r0, min(r0 + 1024, ny), dtype=np.float64)[:, None]
-        phi[0, r0:r0 + y.shape[0]] = tanh_profile(y - y0[None, :], W)
-    return p, phi, _zeros_u(2, (1, ny, nx)), None
+    pstar = np.empty((1, ny, nx), np.float32)
+    drho = rho_H - rho_L
+    # Fluid at rest in hydrostatic balance with the body force
+    # F_b = (rho - rho_L) g: p(y) = p(y + 1) + (F_b(y) + F_b(y + 1)) / 2 down
+    # from the top row (trapezoid rule), p* = p / (rho c_s^2); row blocks from
+    # the top carry the running sum.  The level is set by p = 0 at mid-height
+    # of column 0 (near the interface, where p* enters the pressure force).
+    f0 = tanh_profile(np.arange(ny, dtype=np.float64) - y0[0], W) * drho * g
+    p_mid = (0.5 * (f0[:-1] + f0[1:]))[ny // 2:].sum()
+    carry = np.full(nx, -p_mid)
+    fb_above = None
+    for r1 in range(ny, 0, -1024):                           # row blocks: bounded temporaries
+        r0 = max(0, r1 - 1024)
+        y = np.arange(r0, r1, dtype=np.float64)[:, None]
+        ph = tanh_profile(y - y0[None, :], W)
+        phi[0, r0:r1] = ph
+        fb = ph * drho * g                                   # |F_b| (downwards)
+        half = 0.5 * (fb[:-1] + fb[1:])                      # between rows y and y + 1
+        step = np.concatenate([half, (0.5 * (fb[-1] + fb_above))[None] if fb_above is not None
+                               else np.zeros((1, nx))])
+        pr = carry[None, :] + np.cumsum(step[::-1], axis=0)[::-1]
+        carry = pr[0].copy()
+        fb_above = fb[0].copy()
+        pstar[0, r0:r1] = pr / ((rho_L + ph * drho) / 3.0)
+    return p, phi, _zeros_u(2, (1, ny, nx)), pstar
 
 
 # -------------------------------------------------------------- 3D jet

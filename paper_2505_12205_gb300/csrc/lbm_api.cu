@@ -57,7 +57,9 @@ struct lbm_ctx {
     DiagPartial* diag_part = nullptr;
     DiagPartial* diag_res = nullptr;
     int diag_nparts = 0;
-    float* staging = nullptr;       // float32 population-major planes for checkpoints
+    float* staging = nullptr;       // float32 planes of kStageSets populations for checkpoints
+    float* fieldbuf = nullptr;      // in-place layout: (D + 2) N floats staging the fields
+    float* outold = nullptr;        // in-place layout: outlet plane kept for the outlet rule
     float* uadv = nullptr;          // prescribed velocity of lbm_advect_phase (host input copied here)
     int* ccl = nullptr;             // jet post-processing scratch: labels, sizes, lo, hi (4 N ints)
     int* ccl_list = nullptr;        // (size, lo, hi) of the components, count at the end
@@ -85,7 +87,9 @@ struct lbm_ctx {
     std::string err;
 };
 
-constexpr int64_t kStepGraph = 16;  // steps per graph replay (even: A and B end where they began)
+constexpr int64_t kStepGraph = 16;  // steps per graph replay (even: A and B, or the in-place
+                                    // layout's parity, end where they began)
+constexpr int kStagePops = 4;       // populations converted per pass of a checkpoint
 
 static thread_local std::string g_create_err;
 
@@ -129,6 +133,7 @@ static int validate(const lbm_params* p, std::string& why)
     if (!(p->W >= 2)) { why = "W (interface width) must be >= 2 lattice units"; return -1; }
     if (!(p->mobility > 0 && p->sigma >= 0)) { why = "mobility must be > 0 and sigma >= 0"; return -1; }
     if (p->diag_every < 0) { why = "diag_every must be >= 0"; return -1; }
+    if (p->layout != 0 && p->layout != 1) { why = "layout must be 0 (A/B) or 1 (in place)"; return -1; }
     if (p->visc_model != 0 && p->visc_model != 1) { why = "visc_model must be 0 or 1"; return -1; }
     if (p->storage < 0 || p->storage > 2) { why = "storage must be 0 (float32), 1 (float16) or 2 (bfloat16)"; return -1; }
     if (!(p->storage_scale >= 0)) { why = "storage_scale must be >= 0"; return -1; }
@@ -225,8 +230,12 @@ static cudaError_t dispatch_step(lbm_ctx* c)
         }
         return Ln::step_fused(c->dp, c->geom, c->fused_blocks, c->b, c->stream);
     });
-    std::swap(c->b.fA, c->b.fB);
-    std::swap(c->b.gA, c->b.gB);
+    if (c->b.inplace) {
+        c->b.par ^= 1;
+    } else {
+        std::swap(c->b.fA, c->b.fB);
+        std::swap(c->b.gA, c->b.gB);
+    }
     return e;
 }
 
@@ -301,7 +310,7 @@ static int run_diag(lbm_ctx* c, double phase_eps, DiagPartial* r)
 static int run_steps(lbm_ctx* c, int64_t nsteps)
 {
     while (!c->timing && !c->no_graphs && nsteps >= kStepGraph) {
-        const int slot = (c->b.fA == c->f0 ? 0 : 1) | (c->b.gA == c->g0 ? 0 : 2);
+        const int slot = c->b.inplace ? c->b.par : (c->b.fA == c->f0 ? 0 : 1) | (c->b.gA == c->g0 ? 0 : 2);
         if (!c->graph[slot] && capture_steps(c, slot) != cudaSuccess) {
             cudaGetLastError();                 // a refused capture leaves no sticky error
             c->no_graphs = true;
@@ -344,8 +353,12 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
 
     c->elem = p->storage == 0 ? 4 : 2;
     const size_t plane = size_t(c->dp.Np) * c->Q * c->elem;
+    c->b.inplace = p->layout == 1 ? 1 : 0;
+    c->b.par = 0;
+    c->b.fB = c->b.gB = nullptr;
     void** bufs[4] = {&c->b.fA, &c->b.gA, &c->b.fB, &c->b.gB};
-    for (void** b : bufs) {
+    for (int k = 0; k < (c->b.inplace ? 2 : 4); ++k) {
+        void** b = bufs[k];
         e = cudaMalloc(b, plane);
         if (e != cudaSuccess) {
             int r = cuda_fail(nullptr, e, "cudaMalloc(populations)");
@@ -365,8 +378,21 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
         lbm_destroy(c);
         return r;
     }
+    if (e == cudaSuccess && c->b.inplace) {
+        e = cudaMalloc(reinterpret_cast<void**>(&c->fieldbuf), size_t(c->N) * (c->D + 2) * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&c->outold), 2 * size_t(c->Q) * nface * sizeof(float));
+    }
+    if (e != cudaSuccess) {
+        int r = cuda_fail(nullptr, e, "cudaMalloc");
+        lbm_destroy(c);
+        return r;
+    }
     c->diag_res = c->diag_part + c->diag_nparts;
-    e = with_launch(c->D, p->storage, [&](auto l) { return decltype(l)::fused_geom(c->dp, &c->geom, &c->fused_blocks); });
+    c->dp.phis = c->b.phi;
+    c->dp.outold = c->outold;
+    e = with_launch(c->D, p->storage, [&](auto l) {
+        return decltype(l)::fused_geom(c->dp, &c->geom, &c->fused_blocks, c->b.inplace != 0);
+    });
     if (e != cudaSuccess) {
         int r = cuda_fail(nullptr, e, "fused step set-up");
         lbm_destroy(c);
@@ -403,6 +429,7 @@ int lbm_destroy(lbm_ctx* c)
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     cudaFree(c->b.fA); cudaFree(c->b.gA); cudaFree(c->b.fB); cudaFree(c->b.gB);
     cudaFree(c->b.phi); cudaFree(c->face); cudaFree(c->diag_part); cudaFree(c->staging); cudaFree(c->uadv);
+    cudaFree(c->fieldbuf); cudaFree(c->outold);
     cudaFree(c->ccl); cudaFree(c->ccl_list);
     delete c;
     return LBM_OK;
@@ -460,15 +487,20 @@ int lbm_init_fields(lbm_ctx* c, const float* phi, const float* u, const float* p
     if (!phi) return fail(c, LBM_ERR_ARG, "phi is NULL");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t nb = size_t(c->N) * sizeof(float);
-    // stage the fields in the f buffer B (Q * elem >= 4 (D + 2) bytes per node)
-    float* s_phi = static_cast<float*>(c->b.fB);
+    // stage the fields in the f buffer B (Q * elem >= 4 (D + 2) bytes per
+    // node), or in the field buffer of the in-place layout
+    float* s_phi = c->b.inplace ? c->fieldbuf : static_cast<float*>(c->b.fB);
     float* s_u = s_phi + c->N;
     float* s_p = s_phi + c->N * (1 + c->D);
     LBM_CUDA(c, cudaMemcpyAsync(s_phi, phi, nb, kind, c->stream));
     if (u) LBM_CUDA(c, cudaMemcpyAsync(s_u, u, nb * c->D, kind, c->stream));
     if (pstar) LBM_CUDA(c, cudaMemcpyAsync(s_p, pstar, nb, kind, c->stream));
+    c->b.par = 0;                           // the equilibria are written in the natural layout
     cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
-        return decltype(l)::init(c->dp, s_phi, u ? s_u : nullptr, pstar ? s_p : nullptr, c->b.fA, c->b.gA, c->stream);
+        cudaError_t r = decltype(l)::init(c->dp, s_phi, u ? s_u : nullptr, pstar ? s_p : nullptr, c->b.fA, c->b.gA,
+                                          c->stream);
+        if (r == cudaSuccess && c->b.inplace) r = decltype(l)::save_outlet(c->dp, c->b, c->stream);
+        return r;
     });
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -515,8 +547,9 @@ int lbm_get_fields(lbm_ctx* c, float* phi, float* u, float* p, int on_device)
 {
     if (!c) return LBM_ERR_ARG;
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
-    // outputs are computed into the f buffer B, then copied out
-    float* o_phi = static_cast<float*>(c->b.fB);
+    // outputs are computed into the f buffer B (or the field buffer of the
+    // in-place layout), then copied out
+    float* o_phi = c->b.inplace ? c->fieldbuf : static_cast<float*>(c->b.fB);
     float* o_u = o_phi + c->N;
     float* o_p = o_phi + c->N * (1 + c->D);
     cudaError_t e = with_launch(c->D, c->p.storage,
@@ -531,12 +564,13 @@ int lbm_get_fields(lbm_ctx* c, float* phi, float* u, float* p, int on_device)
     return LBM_OK;
 }
 
-// float32 staging planes (2 Q N) for checkpoints: the external layout is
-// population-major planes, the state is blocked
+// float32 staging planes (kStagePops N) for checkpoints: the external layout
+// is population-major planes, the state is blocked (maybe 16-bit, maybe
+// swapped); the sets are converted a few populations at a time
 static int ensure_staging(lbm_ctx* c)
 {
     if (c->staging) return LBM_OK;
-    LBM_CUDA(c, cudaMalloc(reinterpret_cast<void**>(&c->staging), 2 * size_t(c->N) * c->Q * sizeof(float)));
+    LBM_CUDA(c, cudaMalloc(reinterpret_cast<void**>(&c->staging), size_t(kStagePops) * c->N * sizeof(float)));
     return LBM_OK;
 }
 
@@ -545,18 +579,21 @@ int lbm_get_populations(lbm_ctx* c, float* f, float* g, int on_device)
     if (!c) return LBM_ERR_ARG;
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    const size_t nb = size_t(c->N) * c->Q * sizeof(float);
-    // the state is blocked (and maybe 16-bit): unpack into float32 planes first
     int r = ensure_staging(c);
     if (r != LBM_OK) return r;
-    float* fo = c->staging;
-    float* go = c->staging + size_t(c->N) * c->Q;
-    cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
-        return decltype(l)::unpack(c->dp, c->b.fA, c->b.gA, fo, go, c->stream);
-    });
-    if (e != cudaSuccess) return cuda_fail(c, e, "unpack kernel");
-    if (f) LBM_CUDA(c, cudaMemcpyAsync(f, fo, nb, kind, c->stream));
-    if (g) LBM_CUDA(c, cudaMemcpyAsync(g, go, nb, kind, c->stream));
+    float* outs[2] = {f, g};
+    for (int set = 0; set < 2; ++set) {
+        if (!outs[set]) continue;
+        for (int a0 = 0; a0 < c->Q; a0 += kStagePops) {
+            const int a1 = std::min(c->Q, a0 + kStagePops);
+            cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+                return decltype(l)::unpack(c->dp, c->b, set, a0, a1, c->staging, c->stream);
+            });
+            if (e != cudaSuccess) return cuda_fail(c, e, "unpack kernel");
+            LBM_CUDA(c, cudaMemcpyAsync(outs[set] + size_t(a0) * c->N, c->staging,
+                                        size_t(a1 - a0) * c->N * sizeof(float), kind, c->stream));
+        }
+    }
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
@@ -566,17 +603,27 @@ int lbm_set_populations(lbm_ctx* c, const float* f, const float* g, int on_devic
     if (!c) return LBM_ERR_ARG;
     if (!f || !g) return fail(c, LBM_ERR_ARG, "f and g are required");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const size_t nb = size_t(c->N) * c->Q * sizeof(float);
     int r = ensure_staging(c);
     if (r != LBM_OK) return r;
-    float* fi = c->staging;
-    float* gi = c->staging + size_t(c->N) * c->Q;
-    LBM_CUDA(c, cudaMemcpyAsync(fi, f, nb, kind, c->stream));
-    LBM_CUDA(c, cudaMemcpyAsync(gi, g, nb, kind, c->stream));
-    cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
-        return decltype(l)::pack(c->dp, fi, gi, c->b.fA, c->b.gA, c->stream);
-    });
-    if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
+    const float* ins[2] = {f, g};
+    void* dst[2] = {c->b.fA, c->b.gA};
+    for (int set = 0; set < 2; ++set) {
+        for (int a0 = 0; a0 < c->Q; a0 += kStagePops) {
+            const int a1 = std::min(c->Q, a0 + kStagePops);
+            LBM_CUDA(c, cudaMemcpyAsync(c->staging, ins[set] + size_t(a0) * c->N,
+                                        size_t(a1 - a0) * c->N * sizeof(float), kind, c->stream));
+            cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+                return decltype(l)::pack(c->dp, c->staging, set, a0, a1, dst[set], c->stream);
+            });
+            if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
+        }
+    }
+    c->b.par = 0;                           // written in the natural layout
+    if (c->b.inplace) {
+        cudaError_t e = with_launch(c->D, c->p.storage,
+                                    [&](auto l) { return decltype(l)::save_outlet(c->dp, c->b, c->stream); });
+        if (e != cudaSuccess) return cuda_fail(c, e, "outlet copy");
+    }
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = true;
     c->step_count = 0;
@@ -603,6 +650,7 @@ int lbm_advect_phase(lbm_ctx* c, const float* u, double scale, int64_t nsteps, i
     for (int f = 0; f < 2 * c->D; ++f)
         if (c->p.bc[f] != LBM_BC_PERIODIC && c->p.bc[f] != LBM_BC_WALL && c->p.bc[f] != LBM_BC_FREESLIP)
             return fail(c, LBM_ERR_ARG, "advect_phase: faces must be periodic, walls or free slip");
+    if (c->b.inplace) return fail(c, LBM_ERR_ARG, "advect_phase: needs layout 0 (two copies)");
     const float* ud = u;
     if (!on_device) {
         if (!c->uadv) LBM_CUDA(c, cudaMalloc(reinterpret_cast<void**>(&c->uadv), size_t(c->N) * c->D * sizeof(float)));

@@ -238,6 +238,8 @@ static lbm::Buffers case_buffers(const lbm_batch* b, int c)
     bu.fB = static_cast<char*>(b->fB) + off;
     bu.gB = static_cast<char*>(b->gB) + off;
     bu.phi = b->phi;
+    bu.inplace = 0;
+    bu.par = 0;
     return bu;
 }
 
@@ -275,6 +277,7 @@ int lbm_batch_create(const lbm_params* params, int32_t ncases, void* stream, lbm
         if (p->lattice != params[0].lattice || p->storage != params[0].storage)
             return bfail(nullptr, LBM_ERR_ARG, "case " + std::to_string(c) + ": lattice and storage must match case 0");
         if (p->storage > 1) return bfail(nullptr, LBM_ERR_ARG, "batches store float32 or float16 (storage 0 or 1)");
+        if (p->layout != 0) return bfail(nullptr, LBM_ERR_ARG, "batches use the A/B layout (layout 0)");
         for (int f = 0; f < 6; ++f)
             if (p->bc[f] != LBM_BC_PERIODIC && p->bc[f] != LBM_BC_WALL)
                 return bfail(nullptr, LBM_ERR_ARG, "case " + std::to_string(c) + ": batch faces are periodic or wall");

@@ -46,6 +46,11 @@ struct DevParams {
     const float* phi_in;
     const float* u_in;
     float* lam;            // outlet: lambda of the maximum / average schemes (one value)
+    // in-place layout: phi of the current state (written by the phi pre-pass)
+    // and the outlet plane after the previous step's outlet rule, f then g,
+    // [2][Q][nface] float32
+    const float* phis;
+    float* outold;
 };
 
 // ------------------------------------------------------------------ layout
@@ -482,20 +487,85 @@ __device__ __forceinline__ int map_phi(int v, int n, int bclo, int bchi, bool& i
     return v;
 }
 
+// phi at the (possibly out-of-range) node (xx, yy, mm) of the march
+// coordinate mm from a phi array of the state, with the ghost rules of the
+// faces (the values phi_at forms from g).
+template <class L>
+__device__ __forceinline__ float phi_ghost(const DevParams& P, const float* __restrict__ phi, int xx, int yy,
+                                           int mm)
+{
+    bool inlet = false;
+    const int x = map_phi(xx, P.nx, P.bc[0], P.bc[1], inlet);
+    if (L::D == 3) {
+        const int y = map_phi(yy, P.ny, P.bc[2], P.bc[3], inlet);
+        const int m = map_phi(mm, P.nz, P.bc[4], P.bc[5], inlet);
+        if (inlet) return P.phi_in[y * P.nx + x];
+        return phi[(int64_t(m) * P.ny + y) * P.nx + x];
+    }
+    const int m = map_phi(mm, P.ny, P.bc[2], P.bc[3], inlet);
+    if (inlet) return P.phi_in[x];
+    return phi[int64_t(m) * P.nx + x];
+}
+
+// ------------------------------------------------------ in-place (AA) layout
+//
+// With one copy per set, a step alternates two forms (k_step_fused STEP_EVEN
+// and STEP_ODD).  After an odd step (and after initialisation) the state is
+// natural: the post-streaming population a of node x is in x's slot a.  After
+// an even step it is swapped: each node's post-collision population a sits
+// in its own slot abar, so the post-streaming population a of node x is the
+// upstream node x - e_a's slot abar -- or, where x - e_a lies beyond a face,
+// what the face rule gives: behind a wall or an open face, node x's own slot
+// a (the reflected population of halfway bounce-back; at open faces the face
+// rules overwrite it); across free-slip faces, the tangential neighbour's
+// mirrored population (eq:free_slip_f/g).  par = 1 marks the swapped state.
+
+// Element holding the post-streaming population a of node (x, y, z).
+template <class L>
+__device__ __forceinline__ uint32_t post_el(const DevParams& P, int x, int y, int z, int a, int par)
+{
+    const uint32_t e0 = pel<L>(pnode(P, x, y, z));
+    if (!par || a == 0) return e0 + 32u * uint32_t(a);
+    const int pos[3] = {x, y, z};
+    const int len[3] = {P.nx, P.ny, P.nz};
+    const int e[3] = {L::ex(a), L::ey(a), L::ez(a)};
+    int s[3] = {x, y, z}, m = 0;
+    bool own = false;
+#pragma unroll
+    for (int d = 0; d < L::D; ++d) {
+        s[d] = pos[d] - e[d];
+        if (s[d] < 0 || s[d] >= len[d]) {
+            const int bc = P.bc[2 * d + (s[d] < 0 ? 0 : 1)];
+            if (bc == BC_PERIODIC) s[d] = s[d] < 0 ? s[d] + len[d] : s[d] - len[d];
+            else if (bc == BC_FREESLIP) { s[d] = pos[d]; m |= 1 << d; }
+            else own = true;
+        }
+    }
+    if (own) return e0 + 32u * uint32_t(a);
+    return pel<L>(pnode(P, s[0], s[1], s[2])) + 32u * uint32_t(L::opp(mirrored<L>(a, m)));
+}
+
 // ---------------------------------------------------------------- kernels
 
-// phi = sum_a g_a of every node into phi[node] (unpadded node order).
+// phi = sum_a g_a of every node into phi[node] (unpadded node order); par:
+// the state is swapped (in-place layout after an even step).  This is also
+// the phi pre-pass of the in-place step.
 template <class L, class S, bool PLANAR>
 __global__ void __launch_bounds__(128) k_phi(const __grid_constant__ DevParams P,
-                                             const typename S::T* __restrict__ g, float* __restrict__ phi)
+                                             const typename S::T* __restrict__ g, int par, float* __restrict__ phi)
 {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
-    const int64_t b = pop_base<L, PLANAR>(P, i, x, y, z), st = pop_stride<PLANAR>(P);
     float s = 0.0f;
+    if (PLANAR || !par) {
+        const int64_t b = pop_base<L, PLANAR>(P, i, x, y, z), st = pop_stride<PLANAR>(P);
 #pragma unroll
-    for (int a = 0; a < L::Q; ++a) s += S::g(__ldg(g + b + a * st), L::w(a));
+        for (int a = 0; a < L::Q; ++a) s += S::g(__ldg(g + b + a * st), L::w(a));
+    } else {
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) s += S::g(__ldg(g + post_el<L>(P, x, y, z, a, 1)), L::w(a));
+    }
     phi[i] = s;
 }
 
@@ -579,17 +649,37 @@ __device__ __forceinline__ float phi_at(const DevParams& P, const typename S::T*
     return s;
 }
 
+// Forms of the fused step.
+//  STEP_AB    A/B buffers: each node reads its own slots of A and pushes its
+//             post-collision populations into B (face rules on the push).
+//  In-place (AA) layout, one copy of each set:
+//  STEP_EVEN  reads the node's own slots and writes each post-collision
+//             population a into the node's own slot abar (streaming is
+//             implicit; no face logic), leaving the state "swapped";
+//  STEP_ODD   reads each population where the even step left it (the
+//             upstream node's opposite slot, or the face rule; aa_src) and
+//             pushes the post-collision populations into their natural slots
+//             (the push of STEP_AB), leaving the state natural again.
+//  In both, a thread writes exactly the slots it read: the read of population
+//  a lands where the push of abar writes.  So no two threads touch one slot.
+//  phi comes from the array of the phi pre-pass (k_phi): the g slots of a
+//  neighbouring node may already hold post-collision values when another
+//  block gets to them.
+enum { STEP_AB = 0, STEP_EVEN = 1, STEP_ODD = 2 };
+
 // One work item of the fused step: the tile (x0, y0) over the planes
 // [m0, m1) of the march axis.  smem: the phi window [3][EY][EX] followed by
-// the stash [2][Q][NT]; every thread of the block calls this.
-template <class L, class S, int TX, int TY>
-__device__ __forceinline__ void fused_item(const DevParams& P, const typename S::T* __restrict__ fA,
-                                           const typename S::T* __restrict__ gA, typename S::T* __restrict__ fB,
-                                           typename S::T* __restrict__ gB, int x0, int y0, int m0, int m1,
+// the stash [2][Q][NT]; every thread of the block calls this.  In the
+// in-place forms fA == fB and gA == gB.
+template <class L, class S, int TX, int TY, int MODE>
+__device__ __forceinline__ void fused_item(const DevParams& P, const typename S::T* fA,
+                                           const typename S::T* gA, typename S::T* fB,
+                                           typename S::T* gB, int x0, int y0, int m0, int m1,
                                            float* smem)
 {
     using Cfg = FusedCfg<L, TX, TY>;
     constexpr int Q = L::Q, EX = Cfg::EX, EXT = Cfg::EXT, NT = Cfg::NT;
+    constexpr bool INPLACE = MODE != STEP_AB;
     float* win = smem;                    // [3][EY][EX]
     float* stash = smem + 3 * EXT;        // [2][Q][NT]
     const int tid = threadIdx.x + ((L::D == 3) ? threadIdx.y * TX : 0);
@@ -597,6 +687,108 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
     const int nm = (L::D == 3) ? P.nz : P.ny;       // length of the march axis
     const int x = x0 + tx, y = y0 + ty;
     const bool own = x < P.nx && ((L::D == 2) || y < P.ny);
+
+    // Push map of the in-plane axes (x, and y in 3D), invariant along the
+    // march: the directions behind a wall or open face (pushed back into this
+    // node's opposite slot; at open faces the face rules overwrite them) or a
+    // free-slip face at this node's x (y), and the element offsets of the
+    // steps -1 and +1 along x (y).  Along x the offset depends only on the
+    // lane x mod 32 (a node n = 32 B + r moves to n + s; the offset is taken
+    // on the block B = 1), and uint32 arithmetic is modular, so the periodic
+    // wrap s = -(nx - 1) gives the right offset too.  A step along y moves
+    // whole blocks.
+    uint32_t hwall = 0, hslip[2] = {0u, 0u};
+    uint32_t ho[2][2] = {{0u, 0u}, {0u, 0u}};
+    {
+        constexpr int DI = (L::D == 3) ? 2 : 1;
+        const int pos[2] = {x, y};
+        const int len[2] = {P.nx, P.ny};
+        const uint32_t nstep[2] = {1u, uint32_t(P.nxp)};
+#pragma unroll
+        for (int d = 0; d < DI; ++d) {
+            int sm = -1, sp = 1;
+            const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
+            if (pos[d] == 0) {
+                if (lo == BC_PERIODIC) sm = len[d] - 1;
+                else if (lo == BC_FREESLIP) hslip[d] |= dirmask<L>(d, -1);
+                else hwall |= dirmask<L>(d, -1);
+            }
+            if (pos[d] == len[d] - 1) {
+                if (hi == BC_PERIODIC) sp = -(len[d] - 1);
+                else if (hi == BC_FREESLIP) hslip[d] |= dirmask<L>(d, 1);
+                else hwall |= dirmask<L>(d, 1);
+            }
+            if (d == 0) {
+                const uint32_t nx0 = uint32_t(x & 31);
+                ho[0][0] = pel<L>(nx0 + 32u + uint32_t(sm)) - pel<L>(nx0 + 32u);
+                ho[0][1] = pel<L>(nx0 + 32u + uint32_t(sp)) - pel<L>(nx0 + 32u);
+            } else {
+                ho[1][0] = uint32_t(sm) * nstep[1] * uint32_t(Q);
+                ho[1][1] = uint32_t(sp) * nstep[1] * uint32_t(Q);
+            }
+        }
+    }
+
+    // The push map of plane mm: element offsets o of the steps along each
+    // axis (wrapped on periodic faces; a step along y or z moves whole
+    // 32-node blocks, so its offset is the node step times Q), the directions
+    // pushed back into the node (walls, open faces) and the free-slip
+    // directions per axis; the in-plane axes from the map above.
+    struct PushMap {
+        uint32_t o[3][2];
+        uint32_t wall, slip[3], off;
+    };
+    auto push_map = [&](int mm) {
+        PushMap M;
+        M.wall = hwall;
+        M.slip[0] = hslip[0];
+        M.slip[1] = (L::D == 3) ? hslip[1] : 0u;
+        M.slip[2] = 0u;
+        M.o[0][0] = ho[0][0];
+        M.o[0][1] = ho[0][1];
+        M.o[1][0] = ho[1][0];
+        M.o[1][1] = ho[1][1];
+        constexpr int d = L::D - 1;             // the march axis
+        const uint32_t nstep = (L::D == 3) ? uint32_t(P.nxp) * uint32_t(P.ny) : uint32_t(P.nxp);
+        int sm = -1, sp = 1;                    // node steps in units of the axis
+        const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
+        if (mm == 0) {
+            if (lo == BC_PERIODIC) sm = nm - 1;
+            else if (lo == BC_FREESLIP) M.slip[d] |= dirmask<L>(d, -1);
+            else M.wall |= dirmask<L>(d, -1);
+        }
+        if (mm == nm - 1) {
+            if (hi == BC_PERIODIC) sp = -(nm - 1);
+            else if (hi == BC_FREESLIP) M.slip[d] |= dirmask<L>(d, 1);
+            else M.wall |= dirmask<L>(d, 1);
+        }
+        M.o[d][0] = uint32_t(sm) * nstep * uint32_t(Q);
+        M.o[d][1] = uint32_t(sp) * nstep * uint32_t(Q);
+        M.off = M.wall | M.slip[0] | M.slip[1] | M.slip[2];
+        return M;
+    };
+    // Element that the push of direction a from the node at element e0 writes
+    // (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g, eq:free_slip_f/g):
+    // the neighbour's slot a, this node's slot abar (wall or open face), or
+    // the tangential neighbour's mirrored slot (free slip).  `any` is false
+    // when no node of the warp has a direction behind a face.
+    auto target = [&](const PushMap& M, uint32_t e0, int a, bool any) -> uint32_t {
+        const uint32_t bit = 1u << a;
+        if (!any || !(M.off & bit)) {
+            uint32_t t = e0;
+            if (L::ex(a)) t += M.o[0][L::ex(a) > 0];
+            if (L::ey(a)) t += M.o[1][L::ey(a) > 0];
+            if (L::D == 3 && L::ez(a)) t += M.o[2][L::ez(a) > 0];
+            return t + 32u * a;
+        }
+        if (M.wall & bit) return e0 + 32u * L::opp(a);
+        const int m = int((M.slip[0] >> a) & 1u) | int((M.slip[1] >> a) & 1u) << 1 | int((M.slip[2] >> a) & 1u) << 2;
+        uint32_t t = e0;
+        if (L::ex(a) && !(m & 1)) t += M.o[0][L::ex(a) > 0];
+        if (L::ey(a) && !(m & 2)) t += M.o[1][L::ey(a) > 0];
+        if (L::D == 3 && L::ez(a) && !(m & 4)) t += M.o[2][L::ez(a) > 0];
+        return t + 32u * mirrored<L>(a, m);
+    };
 
     // phi of plane mm over the extended tile into window slot wslot; the
     // interior g of that plane goes to stash buffer (mm mod 2).  The
@@ -609,19 +801,37 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
         float* sbuf = stash + (mm & 1) * Q * NT;
         if (own) {
             float v;
-            if (mm >= 0 && mm < nm) {       // a plane of the grid: no ghost rule applies
-                // (the same sum, in the same order, as phi_at)
-                const typename S::T* gb = gA + pel<L>((L::D == 3) ? pnode(P, x, y, mm) : pnode(P, x, mm, 0));
-                float sacc = 0.0f;
+            const bool ingrid = mm >= 0 && mm < nm;
+            const uint32_t e0 = ingrid ? pel<L>((L::D == 3) ? pnode(P, x, y, mm) : pnode(P, x, mm, 0)) : 0u;
+            if constexpr (!INPLACE) {
+                if (ingrid) {       // a plane of the grid: no ghost rule applies
+                    // (the same sum, in the same order, as phi_at)
+                    const typename S::T* gb = gA + e0;
+                    float sacc = 0.0f;
 #pragma unroll
-                for (int a = 0; a < Q; ++a) {
-                    const float gv = S::g(__ldg(gb + 32 * a), L::w(a));
-                    if (keep) sbuf[tid + a * NT] = gv;
-                    sacc += gv;
+                    for (int a = 0; a < Q; ++a) {
+                        const float gv = S::g(__ldg(gb + 32 * a), L::w(a));
+                        if (keep) sbuf[tid + a * NT] = gv;
+                        sacc += gv;
+                    }
+                    v = sacc;
+                } else {
+                    v = phi_at<L, S>(P, gA, x, y, mm, keep ? sbuf + tid : nullptr, NT);
                 }
-                v = sacc;
             } else {
-                v = phi_at<L, S>(P, gA, x, y, mm, keep ? sbuf + tid : nullptr, NT);
+                if (keep) {         // keep implies a plane of the grid
+                    if constexpr (MODE == STEP_EVEN) {
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) sbuf[tid + a * NT] = S::g(__ldg(gA + e0 + 32 * a), L::w(a));
+                    } else {
+                        const PushMap M = push_map(mm);
+                        const bool any = !__all_sync(__activemask(), M.off == 0u);
+#pragma unroll
+                        for (int a = 0; a < Q; ++a)
+                            sbuf[tid + a * NT] = S::g(__ldg(gA + target(M, e0, L::opp(a), any)), L::w(a));
+                    }
+                }
+                v = phi_ghost<L>(P, P.phis, x, y, mm);
             }
             wslot[(ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 1] = v;
         }
@@ -640,50 +850,11 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
                 px = ((h - 2 * (wx + 2)) & 1) ? wx + 1 : 0;
                 py = 1 + ((h - 2 * (wx + 2)) >> 1);
             }
-            wslot[py * EX + px] = phi_at<L, S>(P, gA, x0 - 1 + px, (L::D == 3) ? y0 - 1 + py : 0, mm, nullptr, 0);
+            const int hx = x0 - 1 + px, hy = (L::D == 3) ? y0 - 1 + py : 0;
+            if constexpr (!INPLACE) wslot[py * EX + px] = phi_at<L, S>(P, gA, hx, hy, mm, nullptr, 0);
+            else wslot[py * EX + px] = phi_ghost<L>(P, P.phis, hx, hy, mm);
         }
     };
-
-    // Push map of the in-plane axes (x, and y in 3D), invariant along the
-    // march: the directions behind a wall, free-slip or open face at this
-    // node's x (y), and the element offsets of the steps -1 and +1 along x
-    // (y).  Along x the offset depends only on the lane x mod 32 (a node
-    // n = 32 B + r moves to n + s; the offset is taken on the block B = 1),
-    // and uint32 arithmetic is modular, so the periodic wrap s = -(nx - 1)
-    // gives the right offset too.  A step along y moves whole blocks.
-    uint32_t hwall = 0, hopen = 0, hslip[2] = {0u, 0u};
-    uint32_t ho[2][2] = {{0u, 0u}, {0u, 0u}};
-    {
-        constexpr int DI = (L::D == 3) ? 2 : 1;
-        const int pos[2] = {x, y};
-        const int len[2] = {P.nx, P.ny};
-        const uint32_t nstep[2] = {1u, uint32_t(P.nxp)};
-#pragma unroll
-        for (int d = 0; d < DI; ++d) {
-            int sm = -1, sp = 1;
-            const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
-            if (pos[d] == 0) {
-                if (lo == BC_PERIODIC) sm = len[d] - 1;
-                else if (lo == BC_WALL) hwall |= dirmask<L>(d, -1);
-                else if (lo == BC_FREESLIP) hslip[d] |= dirmask<L>(d, -1);
-                else hopen |= dirmask<L>(d, -1);
-            }
-            if (pos[d] == len[d] - 1) {
-                if (hi == BC_PERIODIC) sp = -(len[d] - 1);
-                else if (hi == BC_WALL) hwall |= dirmask<L>(d, 1);
-                else if (hi == BC_FREESLIP) hslip[d] |= dirmask<L>(d, 1);
-                else hopen |= dirmask<L>(d, 1);
-            }
-            if (d == 0) {
-                const uint32_t nx0 = uint32_t(x & 31);
-                ho[0][0] = pel<L>(nx0 + 32u + uint32_t(sm)) - pel<L>(nx0 + 32u);
-                ho[0][1] = pel<L>(nx0 + 32u + uint32_t(sp)) - pel<L>(nx0 + 32u);
-            } else {
-                ho[1][0] = uint32_t(sm) * nstep[1] * uint32_t(Q);
-                ho[1][1] = uint32_t(sp) * nstep[1] * uint32_t(Q);
-            }
-        }
-    }
 
     // window slots of planes m - 1, m, m + 1, rotated after each plane
     float* wlo = win;
@@ -700,10 +871,7 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
             const int z = (L::D == 3) ? m : 0;
             const int yc = (L::D == 3) ? y : m;
             const bool inlet_node = m == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
-            const uint32_t n0 = pnode(P, x, yc, z);
-            const uint32_t e0 = pel<L>(n0);
-            const typename S::T* fblk = fA + e0;
-            auto fa = [&](int a) { return S::f(__ldg(fblk + 32 * a), L::w(a), P); };
+            const uint32_t e0 = pel<L>(pnode(P, x, yc, z));
             auto ga = [&](int a) { return sbuf[a * NT]; };
             const int ctr = (ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 1;
             auto pa = [&](int a) {
@@ -712,85 +880,35 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
                 const float* wslot = dm < 0 ? wlo : (dm > 0 ? whi : wmid);
                 return wslot[ctr + dy * EX + L::ex(a)];
             };
-            // push streaming (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g):
-            // per axis the element offsets of the steps -1 and +1 (wrapped on
-            // periodic faces; a step along y or z moves whole 32-node blocks,
-            // so its offset is the node step times Q), and the directions
-            // whose target lies behind a wall (bounced back into the opposite
-            // slot of this node) or beyond an open face (they leave the domain);
-            // the in-plane axes from the map above, the march axis here
-            uint32_t wallm = hwall, openm = hopen, slipm[3] = {hslip[0], (L::D == 3) ? hslip[1] : 0u, 0u};
-            uint32_t o[3][2];
-            o[0][0] = ho[0][0];
-            o[0][1] = ho[0][1];
-            if (L::D == 3) {
-                o[1][0] = ho[1][0];
-                o[1][1] = ho[1][1];
-            }
-            {
-                constexpr int d = L::D - 1;             // the march axis
-                const uint32_t nstep = (L::D == 3) ? uint32_t(P.nxp) * uint32_t(P.ny) : uint32_t(P.nxp);
-                int sm = -1, sp = 1;                    // node steps in units of the axis
-                const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
-                if (m == 0) {
-                    if (lo == BC_PERIODIC) sm = nm - 1;
-                    else if (lo == BC_WALL) wallm |= dirmask<L>(d, -1);
-                    else if (lo == BC_FREESLIP) slipm[d] |= dirmask<L>(d, -1);
-                    else openm |= dirmask<L>(d, -1);
-                }
-                if (m == nm - 1) {
-                    if (hi == BC_PERIODIC) sp = -(nm - 1);
-                    else if (hi == BC_WALL) wallm |= dirmask<L>(d, 1);
-                    else if (hi == BC_FREESLIP) slipm[d] |= dirmask<L>(d, 1);
-                    else openm |= dirmask<L>(d, 1);
-                }
-                o[d][0] = uint32_t(sm) * nstep * uint32_t(Q);
-                o[d][1] = uint32_t(sp) * nstep * uint32_t(Q);
-            }
-            const uint32_t offm = wallm | openm | slipm[0] | slipm[1] | slipm[2];
-            auto emit = [&](int a, float fs, float gs) {
-                const float wa = L::w(a);           // w of a and of its opposite
-                const uint32_t bit = 1u << a;
-                if (!(offm & bit)) {
-                    uint32_t t = e0;
-                    if (L::ex(a)) t += o[0][L::ex(a) > 0];
-                    if (L::ey(a)) t += o[1][L::ey(a) > 0];
-                    if (L::D == 3 && L::ez(a)) t += o[2][L::ez(a) > 0];
-                    (fB + t)[32 * a] = S::ef(fs, wa, P);
-                    (gB + t)[32 * a] = S::eg(gs, wa);
-                } else if (wallm & bit) {           // wall: back to this node, opposite slot
-                    (fB + e0)[32 * L::opp(a)] = S::ef(fs, wa, P);
-                    (gB + e0)[32 * L::opp(a)] = S::eg(gs, wa);
-                } else if (P.has_slip && !(openm & bit)) {
-                    // free slip (eq:free_slip_f/g): reflected over the crossed slip
-                    // faces, to the tangential neighbour, components reversed
-                    const int m = int((slipm[0] >> a) & 1u) | int((slipm[1] >> a) & 1u) << 1 |
-                                  int((slipm[2] >> a) & 1u) << 2;
-                    uint32_t t = e0;
-                    if (L::ex(a) && !(m & 1)) t += o[0][L::ex(a) > 0];
-                    if (L::ey(a) && !(m & 2)) t += o[1][L::ey(a) > 0];
-                    if (L::D == 3 && L::ez(a) && !(m & 4)) t += o[2][L::ez(a) > 0];
-                    const int am = mirrored<L>(a, m);
-                    (fB + t)[32 * am] = S::ef(fs, wa, P);
-                    (gB + t)[32 * am] = S::eg(gs, wa);
-                }                                   // open face: leaves the domain
-            };
-            if (__all_sync(__activemask(), offm == 0u)) {
-                // no node of the warp has a direction behind a face (the usual
-                // case): every population is pushed to its neighbour, with no
-                // per-direction test (+2 % float32, +15 % float16 throughput)
+            if constexpr (MODE == STEP_EVEN) {
+                // in place: own slots in, own opposite slots out
+                auto fa = [&](int a) { return S::f(__ldg(fA + e0 + 32 * a), L::w(a), P); };
+                auto swap = [&](int a, float fs, float gs) {
+                    const float wa = L::w(a);           // w of a and of its opposite
+                    fB[e0 + 32 * L::opp(a)] = S::ef(fs, wa, P);
+                    gB[e0 + 32 * L::opp(a)] = S::eg(gs, wa);
+                };
+                node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, swap);
+            } else {
+                const PushMap M = push_map(m);
+                // when no node of the warp has a direction behind a face (the
+                // usual case) every population takes the plain neighbour
+                // offset, with no per-direction test (+2 % float32, +15 %
+                // float16 throughput)
+                const bool any = !__all_sync(__activemask(), M.off == 0u);
                 auto push = [&](int a, float fs, float gs) {
                     const float wa = L::w(a);
-                    uint32_t t = e0;
-                    if (L::ex(a)) t += o[0][L::ex(a) > 0];
-                    if (L::ey(a)) t += o[1][L::ey(a) > 0];
-                    if (L::D == 3 && L::ez(a)) t += o[2][L::ez(a) > 0];
-                    (fB + t)[32 * a] = S::ef(fs, wa, P);
-                    (gB + t)[32 * a] = S::eg(gs, wa);
+                    const uint32_t t = target(M, e0, a, any);
+                    fB[t] = S::ef(fs, wa, P);
+                    gB[t] = S::eg(gs, wa);
                 };
-                node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, push);
-            } else {
-                node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, emit);
+                if constexpr (MODE == STEP_AB) {
+                    auto fa = [&](int a) { return S::f(__ldg(fA + e0 + 32 * a), L::w(a), P); };
+                    node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, push);
+                } else {
+                    auto fa = [&](int a) { return S::f(__ldg(fA + target(M, e0, L::opp(a), any)), L::w(a), P); };
+                    node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, push);
+                }
             }
         }
         __syncthreads();
@@ -807,6 +925,7 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
 template <class L, int NT>
 constexpr int fused_min_blocks() { return (L::D == 3) ? 768 / NT : 1024 / NT; }
 
+// The fused step, A/B form: fA, gA -> fB, gB.
 template <class L, class S, int TX, int TY>
 __global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (fused_min_blocks<L, TX *((L::D == 3) ? TY : 1)>()))
 k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typename S::T* __restrict__ fA,
@@ -819,7 +938,24 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typen
         const int x0 = (tile % G.tiles_x) * TX;
         const int y0 = (L::D == 3) ? (tile / G.tiles_x) * TY : 0;
         const int m0 = seg * G.seglen;
-        fused_item<L, S, TX, TY>(P, fA, gA, fB, gB, x0, y0, m0, min(m0 + G.seglen, nm), smem);
+        fused_item<L, S, TX, TY, STEP_AB>(P, fA, gA, fB, gB, x0, y0, m0, min(m0 + G.seglen, nm), smem);
+    }
+}
+
+// The fused step on the in-place layout, form MODE (STEP_EVEN or STEP_ODD):
+// one copy f, g of each set, read and written (not restrict-qualified).
+template <class L, class S, int TX, int TY, int MODE>
+__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (fused_min_blocks<L, TX *((L::D == 3) ? TY : 1)>()))
+k_step_inplace(const __grid_constant__ DevParams P, const FusedGeom G, typename S::T* f, typename S::T* g)
+{
+    extern __shared__ float smem[];
+    const int nm = (L::D == 3) ? P.nz : P.ny;
+    for (int item = blockIdx.x; item < G.items; item += gridDim.x) {
+        const int tile = item % G.ntiles, seg = item / G.ntiles;
+        const int x0 = (tile % G.tiles_x) * TX;
+        const int y0 = (L::D == 3) ? (tile / G.tiles_x) * TY : 0;
+        const int m0 = seg * G.seglen;
+        fused_item<L, S, TX, TY, MODE>(P, f, g, f, g, x0, y0, m0, min(m0 + G.seglen, nm), smem);
     }
 }
 
@@ -868,8 +1004,8 @@ k_step_batch(const BatchCase* __restrict__ cases, const int2* __restrict__ items
         const int y0 = (L::D == 3) ? (tile / sc.G.tiles_x) * TY : 0;
         const int m0 = seg * sc.G.seglen;
         const int64_t off = sc.off;
-        fused_item<L, S, TX, TY>(sc.P, fA + off, gA + off, fB + off, gB + off, x0, y0, m0,
-                                 min(m0 + sc.G.seglen, nm), smem);
+        fused_item<L, S, TX, TY, STEP_AB>(sc.P, fA + off, gA + off, fB + off, gB + off, x0, y0, m0,
+                                          min(m0 + sc.G.seglen, nm), smem);
         __syncthreads();                            // sc and s_item are rewritten next
     }
 }
@@ -882,17 +1018,23 @@ k_step_batch(const BatchCase* __restrict__ cases, const int2* __restrict__ items
 // (eq:gravity_force).  p* cancels, the tangential excess momentum is shared
 // by the two unknowns that carry each tangential component, the phase excess
 // by the unknowns with a tangential component.
+// par: the state is swapped (in-place layout after an even step); the known
+// populations are then read where that layout keeps them, and the unknown
+// ones (arriving from beyond the face) sit in the node's own slots in either
+// layout.
 template <class L, class S>
-__global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __restrict__ fB, typename S::T* __restrict__ gB)
+__global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* fB, typename S::T* gB, int par)
 {
     constexpr int Q = L::Q;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
     if (t >= nface) return;
     // the node (t mod nx, t / nx) of the last-axis plane 0
-    const uint32_t e = (L::D == 2) ? pel<L>(pnode(P, t, 0, 0)) : pel<L>(pnode(P, t % P.nx, t / P.nx, 0));
+    const int tx = (L::D == 2) ? t : t % P.nx, ty = (L::D == 2) ? 0 : t / P.nx;
+    const uint32_t e = (L::D == 2) ? pel<L>(pnode(P, tx, 0, 0)) : pel<L>(pnode(P, tx, ty, 0));
     typename S::T* fn = fB + e;
     typename S::T* gn = gB + e;
+    auto src = [&](int a) { return (L::D == 2) ? post_el<L>(P, tx, 0, 0, a, par) : post_el<L>(P, tx, ty, 0, a, par); };
     const float phin = P.phi_in[t], un = P.u_in[t];
     const float ux = 0.0f, uy = (L::D == 2) ? un : 0.0f, uz = (L::D == 3) ? un : 0.0f;
     const float uu = un * un;
@@ -905,8 +1047,8 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __re
     float f[Q], g[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        f[a] = S::f(fn[32 * a], L::w(a), P);
-        g[a] = S::g(gn[32 * a], L::w(a));
+        f[a] = S::f(fB[src(a)], L::w(a), P);
+        g[a] = S::g(gB[src(a)], L::w(a));
     }
     float Mx = 0.0f, My = 0.0f, theta = 0.0f;
     int ndiag = 0;
@@ -945,7 +1087,8 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* __re
 // bare first moment of f along the outward normal at layer N-1 after
 // streaming, reduced over the layer into *P.lam (one block).
 template <class L, class S>
-__global__ void __launch_bounds__(256) k_outlet_speed(const __grid_constant__ DevParams P, const typename S::T* __restrict__ fB)
+__global__ void __launch_bounds__(256) k_outlet_speed(const __grid_constant__ DevParams P, const typename S::T* __restrict__ fB,
+                                                      int par)
 {
     __shared__ float red[256];
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
@@ -953,12 +1096,12 @@ __global__ void __launch_bounds__(256) k_outlet_speed(const __grid_constant__ De
     float acc = P.outlet_scheme == 1 ? -3.0e38f : 0.0f;
     for (int t = threadIdx.x; t < nface; t += blockDim.x) {
         const int tx = (L::D == 2) ? t : t % P.nx, ty = (L::D == 2) ? 0 : t / P.nx;
-        const uint32_t iM = (L::D == 2) ? pel<L>(pnode(P, tx, nL - 2, 0)) : pel<L>(pnode(P, tx, ty, nL - 2));
         float U = 0.0f;
 #pragma unroll
         for (int a = 0; a < L::Q; ++a) {
             const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
-            if (en) U += float(en) * S::f(fB[iM + 32 * a], L::w(a), P);
+            const uint32_t iM = (L::D == 2) ? post_el<L>(P, tx, nL - 2, 0, a, par) : post_el<L>(P, tx, ty, nL - 2, a, par);
+            if (en) U += float(en) * S::f(fB[iM], L::w(a), P);
         }
         acc = P.outlet_scheme == 1 ? fmaxf(acc, U) : acc + U;
     }
@@ -976,10 +1119,14 @@ __global__ void __launch_bounds__(256) k_outlet_speed(const __grid_constant__ De
 // Convective outlet on the high face of the last axis (eq:implicit_convective,
 // eq:convective_f/g): chi(N, t+1) = (chi(N, t) + lambda chi(N-1, t+1)) / (1 + lambda),
 // lambda = clamp(sum_a f_a e_a.n at layer N-1 after streaming, 0, 1).
-template <class L, class S>
-__global__ void k_outlet(const __grid_constant__ DevParams P, const typename S::T* __restrict__ fA,
-                         const typename S::T* __restrict__ gA, typename S::T* __restrict__ fB,
-                         typename S::T* __restrict__ gB)
+// INPL: in-place layout (par: swapped state); chi(N, t) comes from the copy
+// P.outold the previous outlet rule kept (the step overwrote the state's), and
+// the result is written to the state and to that copy (as stored: rounded to
+// the storage format, so both layouts blend the same values).  A/B: chi(N, t)
+// is A's layer N.
+template <class L, class S, bool INPL>
+__global__ void k_outlet(const __grid_constant__ DevParams P, const typename S::T* fA,
+                         const typename S::T* gA, typename S::T* fB, typename S::T* gB, int par)
 {
     constexpr int Q = L::Q;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -987,23 +1134,51 @@ __global__ void k_outlet(const __grid_constant__ DevParams P, const typename S::
     if (t >= nface) return;
     const int nL = (L::D == 2) ? P.ny : P.nz;
     const int tx = (L::D == 2) ? t : t % P.nx, ty = (L::D == 2) ? 0 : t / P.nx;
-    const uint32_t iN = (L::D == 2) ? pel<L>(pnode(P, tx, nL - 1, 0)) : pel<L>(pnode(P, tx, ty, nL - 1));
-    const uint32_t iM = (L::D == 2) ? pel<L>(pnode(P, tx, nL - 2, 0)) : pel<L>(pnode(P, tx, ty, nL - 2));
+    auto atN = [&](int a) { return (L::D == 2) ? post_el<L>(P, tx, nL - 1, 0, a, par) : post_el<L>(P, tx, ty, nL - 1, a, par); };
+    auto atM = [&](int a) { return (L::D == 2) ? post_el<L>(P, tx, nL - 2, 0, a, par) : post_el<L>(P, tx, ty, nL - 2, a, par); };
     float U = 0.0f;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
-        if (en) U += float(en) * S::f(fB[iM + 32 * a], L::w(a), P);
+        if (en) U += float(en) * S::f(fB[atM(a)], L::w(a), P);
     }
     const float lam = fminf(fmaxf(P.outlet_scheme ? *P.lam : U, 0.0f), 1.0f);
     const float inv = 1.0f / (1.0f + lam);
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const float wa = L::w(a);
-        const float fo = S::f(fA[iN + 32 * a], wa, P), fm = S::f(fB[iM + 32 * a], wa, P);
-        const float go = S::g(gA[iN + 32 * a], wa), gm = S::g(gB[iM + 32 * a], wa);
-        fB[iN + 32 * a] = S::ef((fo + lam * fm) * inv, wa, P);
-        gB[iN + 32 * a] = S::eg((go + lam * gm) * inv, wa);
+        const uint32_t iN = atN(a), iM = atM(a);
+        const float fo = INPL ? P.outold[a * nface + t] : S::f(fA[iN], wa, P);
+        const float go = INPL ? P.outold[(Q + a) * nface + t] : S::g(gA[iN], wa);
+        const float fm = S::f(fB[iM], wa, P), gm = S::g(gB[iM], wa);
+        const typename S::T fs = S::ef((fo + lam * fm) * inv, wa, P);
+        const typename S::T gs = S::eg((go + lam * gm) * inv, wa);
+        fB[iN] = fs;
+        gB[iN] = gs;
+        if (INPL) {
+            P.outold[a * nface + t] = S::f(fs, wa, P);
+            P.outold[(Q + a) * nface + t] = S::g(gs, wa);
+        }
+    }
+}
+
+// The outlet plane of the state (decoded) into P.outold: chi(N, t) of the
+// next outlet rule on the in-place layout, after initialisation or a restore.
+template <class L, class S>
+__global__ void k_save_outlet(const __grid_constant__ DevParams P, const typename S::T* __restrict__ f,
+                              const typename S::T* __restrict__ g, int par)
+{
+    constexpr int Q = L::Q;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
+    if (t >= nface) return;
+    const int nL = (L::D == 2) ? P.ny : P.nz;
+    const int tx = (L::D == 2) ? t : t % P.nx, ty = (L::D == 2) ? 0 : t / P.nx;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const uint32_t iN = (L::D == 2) ? post_el<L>(P, tx, nL - 1, 0, a, par) : post_el<L>(P, tx, ty, nL - 1, a, par);
+        P.outold[a * nface + t] = S::f(f[iN], L::w(a), P);
+        P.outold[(Q + a) * nface + t] = S::g(g[iN], L::w(a));
     }
 }
 
@@ -1053,7 +1228,7 @@ __global__ void k_init(const __grid_constant__ DevParams P, const float* __restr
 template <class L, class S>
 __global__ void __launch_bounds__(128) k_fields(const __grid_constant__ DevParams P,
                                                 const typename S::T* __restrict__ fA,
-                                                const typename S::T* __restrict__ gA,
+                                                const typename S::T* __restrict__ gA, int par,
                                                 const float* __restrict__ phi, float* __restrict__ ophi,
                                                 float* __restrict__ ou, float* __restrict__ op)
 {
@@ -1063,12 +1238,12 @@ __global__ void __launch_bounds__(128) k_fields(const __grid_constant__ DevParam
     if (x >= P.nx) return;
     const int64_t N = P.N;
     const int64_t node = (int64_t(z) * P.ny + y) * P.nx + x;
-    const uint32_t e = pel<L>(pnode(P, x, y, z));
     float f[Q], g[Q], phin[Q], out[5];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        f[a] = S::f(fA[e + 32 * a], L::w(a), P);
-        g[a] = S::g(gA[e + 32 * a], L::w(a));
+        const uint32_t e = post_el<L>(P, x, y, z, a, par);
+        f[a] = S::f(fA[e], L::w(a), P);
+        g[a] = S::g(gA[e], L::w(a));
     }
     gather_phi<L>(P, phi, x, y, z, phin);
     const bool inlet_node = ((L::D == 3) ? z : y) == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
@@ -1248,7 +1423,7 @@ struct DiagPartial {
 template <class L, class S, bool PLANAR>
 __global__ void __launch_bounds__(256) k_diag(const __grid_constant__ DevParams P,
                                               const typename S::T* __restrict__ fA,
-                                              const typename S::T* __restrict__ gA,
+                                              const typename S::T* __restrict__ gA, int par,
                                               const float* __restrict__ phi, double eps,
                                               DiagPartial* __restrict__ part)
 {
@@ -1269,8 +1444,9 @@ __global__ void __launch_bounds__(256) k_diag(const __grid_constant__ DevParams 
         const int64_t b = pop_base<L, PLANAR>(P, node, x, y, z), st = pop_stride<PLANAR>(P);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            f[a] = S::f(fA[b + a * st], L::w(a), P);
-            g[a] = S::g(gA[b + a * st], L::w(a));
+            const int64_t e = (!PLANAR && par) ? int64_t(post_el<L>(P, x, y, z, a, 1)) : b + a * st;
+            f[a] = S::f(fA[e], L::w(a), P);
+            g[a] = S::g(gA[e], L::w(a));
             if (!isfinite(f[a]) || !isfinite(g[a])) bad = 1;
         }
         gather_phi<L>(P, phi, x, y, z, phin);
@@ -1345,9 +1521,13 @@ __global__ void k_collide_cells(const __grid_constant__ DevParams P, int64_t n, 
 // ------------------------------------------------------ host-side launchers
 
 // Device buffers of a context; the population planes hold S::T values.
+// A/B layout: A the current state, B the next.  In-place layout: the state is
+// fA, gA alone (fB, gB unused) and par says whether it is swapped.
 struct Buffers {
     void *fA, *gA, *fB, *gB;
     float* phi;
+    int inplace;
+    int par;
 };
 
 template <class L, class S>
@@ -1356,7 +1536,10 @@ struct Launch {
     // fused single-pass step (k_step_fused + face kernels); geometry from fused_geom
     static cudaError_t step_fused(const DevParams& P, const FusedGeom& G, int nblocks, const Buffers& b,
                                   cudaStream_t s);
-    static cudaError_t fused_geom(const DevParams& P, FusedGeom* G, int* nblocks);
+    // inplace: size the persistent grid for the in-place kernels
+    static cudaError_t fused_geom(const DevParams& P, FusedGeom* G, int* nblocks, bool inplace = false);
+    // the outlet plane of the in-place state into P.outold
+    static cudaError_t save_outlet(const DevParams& P, const Buffers& b, cudaStream_t s);
     // the same launches as step_fused, with mark(mctx) recording an event
     // after each stage
     using MarkFn = cudaError_t (*)(void*);
@@ -1372,9 +1555,12 @@ struct Launch {
     // planes [Q][N] (f32 planes of the caller)
     static cudaError_t diag_planar(const DevParams& P, const Buffers& b, double eps, DiagPartial* part, int nparts,
                                    DiagPartial* res, cudaStream_t s);
-    // populations of the state <-> float32 planes [Q][N] (checkpoints)
-    static cudaError_t unpack(const DevParams& P, const void* f, const void* g, float* fo, float* go, cudaStream_t s);
-    static cudaError_t pack(const DevParams& P, const float* fi, const float* gi, void* f, void* g, cudaStream_t s);
+    // populations a0 .. a1-1 of one set of the state <-> float32 planes
+    // (checkpoints); gset: the g set; unpack reads the layout of b (A), pack
+    // writes the natural layout into dst
+    static cudaError_t unpack(const DevParams& P, const Buffers& b, int gset, int a0, int a1, float* out,
+                              cudaStream_t s);
+    static cudaError_t pack(const DevParams& P, const float* in, int gset, int a0, int a1, void* dst, cudaStream_t s);
     static cudaError_t inlet_profile(const DevParams& P, double cx, double cy, double R, double W, double uj,
                                      float* phi_in, float* u_in, cudaStream_t s);
     static cudaError_t collide_cells(const DevParams& P, int64_t n, const float* f, const float* g,
@@ -1394,18 +1580,33 @@ template <> struct FusedTile<D2Q9> { static constexpr int TX = 64, TY = 1; };
 template <> struct FusedTile<D3Q19> { static constexpr int TX = 32, TY = 6; };
 
 template <class L, class S>
-cudaError_t Launch<L, S>::fused_geom(const DevParams& P, FusedGeom* G, int* nblocks)
+cudaError_t Launch<L, S>::fused_geom(const DevParams& P, FusedGeom* G, int* nblocks, bool inplace)
 {
     constexpr int TX = FusedTile<L>::TX, TY = FusedTile<L>::TY;
     using Cfg = FusedCfg<L, TX, TY>;
-    auto kern = k_step_fused<L, S, TX, TY>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem));
-    if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, Cfg::smem)) != cudaSuccess)
-        return e;
+    if (!inplace) {
+        auto kern = k_step_fused<L, S, TX, TY>;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem))) != cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, Cfg::smem)) != cudaSuccess)
+            return e;
+    } else {
+        // the fewer resident blocks of the two forms
+        auto ke = k_step_inplace<L, S, TX, TY, STEP_EVEN>;
+        auto ko = k_step_inplace<L, S, TX, TY, STEP_ODD>;
+        int pe = 0, po = 0;
+        if ((e = cudaFuncSetAttribute(ke, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem))) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(ko, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem))) != cudaSuccess)
+            return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pe, ke, Cfg::NT, Cfg::smem)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&po, ko, Cfg::NT, Cfg::smem)) != cudaSuccess) return e;
+        per_sm = pe < po ? pe : po;
+    }
     per_sm = per_sm < 1 ? 1 : per_sm;
     const int slots = sms * per_sm;
     G->tiles_x = (P.nx + TX - 1) / TX;
@@ -1452,21 +1653,43 @@ cudaError_t Launch<L, S>::step_timed(const DevParams& P, const FusedGeom& G, int
     using Cfg = FusedCfg<L, TX, TY>;
     const T* fA = static_cast<const T*>(b.fA);
     const T* gA = static_cast<const T*>(b.gA);
-    T* fB = static_cast<T*>(b.fB);
-    T* gB = static_cast<T*>(b.gB);
+    T* fB = static_cast<T*>(b.inplace ? b.fA : b.fB);
+    T* gB = static_cast<T*>(b.inplace ? b.gA : b.gB);
+    const dim3 blk(TX, (L::D == 3) ? TY : 1);
     cudaError_t e;
-    if ((e = mark()) != cudaSuccess) return e;      // no separate phi pass in the fused step
-    k_step_fused<L, S, TX, TY><<<nblocks, dim3(TX, (L::D == 3) ? TY : 1), Cfg::smem, s>>>(P, G, fA, gA, fB, gB);
+    int par = 0;                                    // layout of the state after the step
+    if (!b.inplace) {
+        if ((e = mark()) != cudaSuccess) return e;  // no separate phi pass in the A/B step
+        k_step_fused<L, S, TX, TY><<<nblocks, blk, Cfg::smem, s>>>(P, G, fA, gA, fB, gB);
+    } else {
+        // phi pre-pass into P.phis, then the even (natural -> swapped) or the
+        // odd (swapped -> natural) in-place form
+        k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.par, b.phi);
+        if ((e = mark()) != cudaSuccess) return e;
+        if (b.par == 0) k_step_inplace<L, S, TX, TY, STEP_EVEN><<<nblocks, blk, Cfg::smem, s>>>(P, G, fB, gB);
+        else k_step_inplace<L, S, TX, TY, STEP_ODD><<<nblocks, blk, Cfg::smem, s>>>(P, G, fB, gB);
+        par = b.par ^ 1;
+    }
     if ((e = mark()) != cudaSuccess) return e;
     const int lastlo = (L::D == 2) ? P.bc[2] : P.bc[4];
     const int lasthi = (L::D == 2) ? P.bc[3] : P.bc[5];
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
-    if (lastlo == BC_INLET) k_inlet<L, S><<<(nface + 127) / 128, 128, 0, s>>>(P, fB, gB);
+    if (lastlo == BC_INLET) k_inlet<L, S><<<(nface + 127) / 128, 128, 0, s>>>(P, fB, gB, par);
     if (lasthi == BC_OUTFLOW) {
-        if (P.outlet_scheme) k_outlet_speed<L, S><<<1, 256, 0, s>>>(P, fB);
-        k_outlet<L, S><<<(nface + 127) / 128, 128, 0, s>>>(P, fA, gA, fB, gB);
+        if (P.outlet_scheme) k_outlet_speed<L, S><<<1, 256, 0, s>>>(P, fB, par);
+        if (b.inplace) k_outlet<L, S, true><<<(nface + 127) / 128, 128, 0, s>>>(P, fA, gA, fB, gB, par);
+        else k_outlet<L, S, false><<<(nface + 127) / 128, 128, 0, s>>>(P, fA, gA, fB, gB, par);
     }
     if ((e = mark()) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::save_outlet(const DevParams& P, const Buffers& b, cudaStream_t s)
+{
+    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
+    k_save_outlet<L, S><<<(nface + 127) / 128, 128, 0, s>>>(P, static_cast<const T*>(b.fA), static_cast<const T*>(b.gA),
+                                                           b.par);
     return cudaGetLastError();
 }
 
@@ -1485,9 +1708,9 @@ cudaError_t Launch<L, S>::fields(const DevParams& P, const Buffers& b, float* op
 {
     const T* fA = static_cast<const T*>(b.fA);
     const T* gA = static_cast<const T*>(b.gA);
-    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.phi);
+    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.par, b.phi);
     dim3 grid((P.nx + 127) / 128, P.ny, (L::D == 3) ? P.nz : 1);
-    k_fields<L, S><<<grid, 128, 0, s>>>(P, fA, gA, b.phi, ophi, ou, op);
+    k_fields<L, S><<<grid, 128, 0, s>>>(P, fA, gA, b.par, b.phi, ophi, ou, op);
     return cudaGetLastError();
 }
 
@@ -1497,8 +1720,8 @@ cudaError_t Launch<L, S>::diag(const DevParams& P, const Buffers& b, double eps,
 {
     const T* fA = static_cast<const T*>(b.fA);
     const T* gA = static_cast<const T*>(b.gA);
-    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.phi);
-    k_diag<L, S, false><<<nparts, 256, 0, s>>>(P, fA, gA, b.phi, eps, part);
+    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.par, b.phi);
+    k_diag<L, S, false><<<nparts, 256, 0, s>>>(P, fA, gA, b.par, b.phi, eps, part);
     k_diag_final<L><<<1, 32, 0, s>>>(part, nparts, res);
     return cudaGetLastError();
 }
@@ -1509,56 +1732,57 @@ cudaError_t Launch<L, S>::diag_planar(const DevParams& P, const Buffers& b, doub
 {
     const T* fA = static_cast<const T*>(b.fA);
     const T* gA = static_cast<const T*>(b.gA);
-    k_phi<L, S, true><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.phi);
-    k_diag<L, S, true><<<nparts, 256, 0, s>>>(P, fA, gA, b.phi, eps, part);
+    k_phi<L, S, true><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, 0, b.phi);
+    k_diag<L, S, true><<<nparts, 256, 0, s>>>(P, fA, gA, 0, b.phi, eps, part);
     k_diag_final<L><<<1, 32, 0, s>>>(part, nparts, res);
     return cudaGetLastError();
 }
 
+// Populations a0 .. a1-1 of one set of the state (par: swapped) into float32
+// planes out[(a - a0) N + node]; gset: the set is g (else f).
 template <class L, class S>
-__global__ void k_unpack(const __grid_constant__ DevParams P, const typename S::T* __restrict__ f,
-                         const typename S::T* __restrict__ g, float* __restrict__ fo, float* __restrict__ go)
+__global__ void k_unpack(const __grid_constant__ DevParams P, const typename S::T* __restrict__ src, int gset,
+                         int par, int a0, int a1, float* __restrict__ out)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
+    for (int a = a0; a < a1; ++a) {
+        const uint32_t e = post_el<L>(P, x, y, z, a, par);
+        out[(a - a0) * P.N + i] = gset ? S::g(src[e], L::w(a)) : S::f(src[e], L::w(a), P);
+    }
+}
+
+// float32 planes in[(a - a0) N + node] into populations a0 .. a1-1 of one set
+// of the state, natural layout; gset: the set is g (else f).
+template <class L, class S>
+__global__ void k_pack(const __grid_constant__ DevParams P, const float* __restrict__ in, int gset, int a0, int a1,
+                       typename S::T* __restrict__ dst)
 {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
     const uint32_t e = pel<L>(pnode(P, x, y, z));
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) {
-        fo[a * P.N + i] = S::f(f[e + 32 * a], L::w(a), P);
-        go[a * P.N + i] = S::g(g[e + 32 * a], L::w(a));
+    for (int a = a0; a < a1; ++a) {
+        const float v = in[(a - a0) * P.N + i];
+        dst[e + 32 * a] = gset ? S::eg(v, L::w(a)) : S::ef(v, L::w(a), P);
     }
 }
 
 template <class L, class S>
-__global__ void k_pack(const __grid_constant__ DevParams P, const float* __restrict__ fi,
-                       const float* __restrict__ gi, typename S::T* __restrict__ f, typename S::T* __restrict__ g)
-{
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= P.N) return;
-    const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
-    const uint32_t e = pel<L>(pnode(P, x, y, z));
-#pragma unroll
-    for (int a = 0; a < L::Q; ++a) {
-        f[e + 32 * a] = S::ef(fi[a * P.N + i], L::w(a), P);
-        g[e + 32 * a] = S::eg(gi[a * P.N + i], L::w(a));
-    }
-}
-
-template <class L, class S>
-cudaError_t Launch<L, S>::unpack(const DevParams& P, const void* f, const void* g, float* fo, float* go,
+cudaError_t Launch<L, S>::unpack(const DevParams& P, const Buffers& b, int gset, int a0, int a1, float* out,
                                  cudaStream_t s)
 {
-    k_unpack<L, S><<<unsigned((P.N + 255) / 256), 256, 0, s>>>(P, static_cast<const T*>(f),
-                                                               static_cast<const T*>(g), fo, go);
+    k_unpack<L, S><<<unsigned((P.N + 255) / 256), 256, 0, s>>>(P, static_cast<const T*>(gset ? b.gA : b.fA), gset,
+                                                               b.par, a0, a1, out);
     return cudaGetLastError();
 }
 
 template <class L, class S>
-cudaError_t Launch<L, S>::pack(const DevParams& P, const float* fi, const float* gi, void* f, void* g,
+cudaError_t Launch<L, S>::pack(const DevParams& P, const float* in, int gset, int a0, int a1, void* dst,
                                cudaStream_t s)
 {
-    k_pack<L, S><<<unsigned((P.N + 255) / 256), 256, 0, s>>>(P, fi, gi, static_cast<T*>(f), static_cast<T*>(g));
+    k_pack<L, S><<<unsigned((P.N + 255) / 256), 256, 0, s>>>(P, in, gset, a0, a1, static_cast<T*>(dst));
     return cudaGetLastError();
 }
 
@@ -1574,14 +1798,14 @@ cudaError_t Launch<L, S>::inlet_profile(const DevParams& P, double cx, double cy
 template <class L, class S>
 cudaError_t Launch<L, S>::phi(const DevParams& P, const Buffers& b, cudaStream_t s)
 {
-    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, static_cast<const T*>(b.gA), b.phi);
+    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, static_cast<const T*>(b.gA), b.par, b.phi);
     return cudaGetLastError();
 }
 
 template <class L, class S>
 cudaError_t Launch<L, S>::advect(const DevParams& P, const Buffers& b, const float* uf, float scale, cudaStream_t s)
 {
-    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, static_cast<const T*>(b.gA), b.phi);
+    k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, static_cast<const T*>(b.gA), 0, b.phi);
     k_advect<L, S><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, b.phi, uf, scale, static_cast<const T*>(b.gA),
                                                                static_cast<T*>(b.gB));
     return cudaGetLastError();

@@ -41,6 +41,7 @@ class LbmParams(ctypes.Structure):
         ("bc", ctypes.c_int32 * 6),
         ("visc_model", ctypes.c_int32), ("storage", ctypes.c_int32),
         ("outlet_scheme", ctypes.c_int32), ("diag_every", ctypes.c_int32),
+        ("layout", ctypes.c_int32), ("reserved", ctypes.c_int32),
         ("rho_L", ctypes.c_double), ("rho_H", ctypes.c_double),
         ("tau_L", ctypes.c_double), ("tau_H", ctypes.c_double),
         ("mu_ratio", ctypes.c_double),
@@ -152,6 +153,7 @@ def make_params(p: dict) -> LbmParams:
     s.storage = int(p.get("storage", 0))
     s.outlet_scheme = int(p.get("outlet_scheme", 0))
     s.diag_every = int(p.get("diag_every", 0))
+    s.layout = int(p.get("layout", 0))
     s.rho_L, s.rho_H = float(p["rho_L"]), float(p["rho_H"])
     s.tau_L, s.tau_H = float(p.get("tau_L", 0.0)), float(p["tau_H"])
     s.mu_ratio = float(p.get("mu_ratio", 0.0))

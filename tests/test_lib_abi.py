@@ -37,14 +37,14 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_params_struct_layout(lib):
-    # natural alignment of the C struct: 14 int32 then 17 doubles
-    assert ctypes.sizeof(lib.LbmParams) == 14 * 4 + 17 * 8
-    assert lib.LbmParams.rho_L.offset == 56
-    assert lib.LbmParams.mu_ratio.offset == 88
+    # natural alignment of the C struct: 16 int32 then 17 doubles
+    assert ctypes.sizeof(lib.LbmParams) == 16 * 4 + 17 * 8
+    assert lib.LbmParams.rho_L.offset == 64
+    assert lib.LbmParams.mu_ratio.offset == 96
     assert ctypes.sizeof(lib.LbmDiagOut) == 4 * 8 + 2 * 8 + 2 * 4 + 8
 
 
-@pytest.mark.parametrize("change", ["W", "inlet_without_outlet", "diag_every", "mu_ratio", "tau_L"])
+@pytest.mark.parametrize("change", ["W", "inlet_without_outlet", "diag_every", "mu_ratio", "tau_L", "layout"])
 def test_create_rejects_invalid_parameters_before_touching_a_device(lib, change):
     """Parameter validation of lbm_create (W >= 2, an inlet needs the outlet
     opposite, diag_every >= 0, mu_ratio >= 0, tau_L > 0 unless mu_ratio sets
@@ -59,6 +59,8 @@ def test_create_rejects_invalid_parameters_before_touching_a_device(lib, change)
         p["diag_every"] = -1
     elif change == "mu_ratio":
         p["mu_ratio"] = -2.0
+    elif change == "layout":
+        p["layout"] = 2
     else:
         p["tau_L"] = 0.0
     with pytest.raises(lib.LbmError) as e:
