@@ -769,18 +769,19 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
     };
     // Element that the push of direction a from the node at element e0 writes
     // (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g, eq:free_slip_f/g):
-    // the neighbour's slot a, this node's slot abar (wall or open face), or
-    // the tangential neighbour's mirrored slot (free slip).  `any` is false
-    // when no node of the warp has a direction behind a face.
-    auto target = [&](const PushMap& M, uint32_t e0, int a, bool any) -> uint32_t {
+    // the neighbour's slot a (plain_target: no face behind a, the usual case,
+    // with periodic wraps in the offsets), this node's slot abar (wall or
+    // open face), or the tangential neighbour's mirrored slot (free slip).
+    auto plain_target = [&](const PushMap& M, uint32_t e0, int a) -> uint32_t {
+        uint32_t t = e0;
+        if (L::ex(a)) t += M.o[0][L::ex(a) > 0];
+        if (L::ey(a)) t += M.o[1][L::ey(a) > 0];
+        if (L::D == 3 && L::ez(a)) t += M.o[2][L::ez(a) > 0];
+        return t + 32u * a;
+    };
+    auto target = [&](const PushMap& M, uint32_t e0, int a) -> uint32_t {
         const uint32_t bit = 1u << a;
-        if (!any || !(M.off & bit)) {
-            uint32_t t = e0;
-            if (L::ex(a)) t += M.o[0][L::ex(a) > 0];
-            if (L::ey(a)) t += M.o[1][L::ey(a) > 0];
-            if (L::D == 3 && L::ez(a)) t += M.o[2][L::ez(a) > 0];
-            return t + 32u * a;
-        }
+        if (!(M.off & bit)) return plain_target(M, e0, a);
         if (M.wall & bit) return e0 + 32u * L::opp(a);
         const int m = int((M.slip[0] >> a) & 1u) | int((M.slip[1] >> a) & 1u) << 1 | int((M.slip[2] >> a) & 1u) << 2;
         uint32_t t = e0;
@@ -824,11 +825,18 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
 #pragma unroll
                         for (int a = 0; a < Q; ++a) sbuf[tid + a * NT] = S::g(__ldg(gA + e0 + 32 * a), L::w(a));
                     } else {
+                        // where the even step left each population (the slot
+                        // the push of its opposite writes)
                         const PushMap M = push_map(mm);
-                        const bool any = !__all_sync(__activemask(), M.off == 0u);
+                        if (__all_sync(__activemask(), M.off == 0u)) {
 #pragma unroll
-                        for (int a = 0; a < Q; ++a)
-                            sbuf[tid + a * NT] = S::g(__ldg(gA + target(M, e0, L::opp(a), any)), L::w(a));
+                            for (int a = 0; a < Q; ++a)
+                                sbuf[tid + a * NT] = S::g(__ldg(gA + plain_target(M, e0, L::opp(a))), L::w(a));
+                        } else {
+#pragma unroll
+                            for (int a = 0; a < Q; ++a)
+                                sbuf[tid + a * NT] = S::g(__ldg(gA + target(M, e0, L::opp(a))), L::w(a));
+                        }
                     }
                 }
                 v = phi_ghost<L>(P, P.phis, x, y, mm);
@@ -894,21 +902,25 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
                 // when no node of the warp has a direction behind a face (the
                 // usual case) every population takes the plain neighbour
                 // offset, with no per-direction test (+2 % float32, +15 %
-                // float16 throughput)
-                const bool any = !__all_sync(__activemask(), M.off == 0u);
-                auto push = [&](int a, float fs, float gs) {
-                    const float wa = L::w(a);
-                    const uint32_t t = target(M, e0, a, any);
-                    fB[t] = S::ef(fs, wa, P);
-                    gB[t] = S::eg(gs, wa);
+                // float16 throughput); the two cases are separate copies of
+                // the node update
+                auto step = [&](auto tgt) {
+                    auto push = [&](int a, float fs, float gs) {
+                        const float wa = L::w(a);
+                        const uint32_t t = tgt(M, e0, a);
+                        fB[t] = S::ef(fs, wa, P);
+                        gB[t] = S::eg(gs, wa);
+                    };
+                    if constexpr (MODE == STEP_AB) {
+                        auto fa = [&](int a) { return S::f(__ldg(fA + e0 + 32 * a), L::w(a), P); };
+                        node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, push);
+                    } else {
+                        auto fa = [&](int a) { return S::f(__ldg(fA + tgt(M, e0, L::opp(a))), L::w(a), P); };
+                        node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, push);
+                    }
                 };
-                if constexpr (MODE == STEP_AB) {
-                    auto fa = [&](int a) { return S::f(__ldg(fA + e0 + 32 * a), L::w(a), P); };
-                    node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, push);
-                } else {
-                    auto fa = [&](int a) { return S::f(__ldg(fA + target(M, e0, L::opp(a), any)), L::w(a), P); };
-                    node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, push);
-                }
+                if (__all_sync(__activemask(), M.off == 0u)) step(plain_target);
+                else step(target);
             }
         }
         __syncthreads();
@@ -919,11 +931,59 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
     }
 }
 
+// phi pre-pass of the in-place step: phi = sum_a g_a of every node into
+// P.phis (unpadded node order) from the state in either form (par: swapped).
+// One thread per node of an x row (grid: rows y, planes z); interior nodes of
+// the swapped form take each population from the upstream node's opposite
+// slot by a fixed element offset, nodes on a face through post_el.  The sum
+// is taken in the order of k_phi and of the A/B step's phi.
+template <class L, class S>
+__global__ void __launch_bounds__(128) k_phi_pre(const __grid_constant__ DevParams P,
+                                                 const typename S::T* __restrict__ g, int par,
+                                                 float* __restrict__ phi)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= P.nx) return;
+    const uint32_t n = pnode(P, x, y, z);
+    const uint32_t e0 = pel<L>(n);
+    float s = 0.0f;
+    if (!par) {
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) s += S::g(__ldg(g + e0 + 32 * a), L::w(a));
+    } else {
+        // the upstream coordinates x - 1, x + 1 (y, z likewise), wrapped across
+        // periodic faces; a step beyond any other face goes through post_el
+        // (rows of the face planes only: uniform over a block in y and z)
+        const int xm = x > 0 ? x - 1 : (P.bc[0] == BC_PERIODIC ? P.nx - 1 : -1);
+        const int xp = x < P.nx - 1 ? x + 1 : (P.bc[1] == BC_PERIODIC ? 0 : -1);
+        const int ym = y > 0 ? y - 1 : (P.bc[2] == BC_PERIODIC ? P.ny - 1 : -1);
+        const int yp = y < P.ny - 1 ? y + 1 : (P.bc[3] == BC_PERIODIC ? 0 : -1);
+        const int zm = L::D == 2 ? 0 : (z > 0 ? z - 1 : (P.bc[4] == BC_PERIODIC ? P.nz - 1 : -1));
+        const int zp = L::D == 2 ? 0 : (z < P.nz - 1 ? z + 1 : (P.bc[5] == BC_PERIODIC ? 0 : -1));
+#pragma unroll
+        for (int a = 0; a < L::Q; ++a) {
+            const int sx = L::ex(a) > 0 ? xm : (L::ex(a) < 0 ? xp : x);
+            const int sy = L::ey(a) > 0 ? ym : (L::ey(a) < 0 ? yp : y);
+            const int sz = L::ez(a) > 0 ? zm : (L::ez(a) < 0 ? zp : z);
+            const uint32_t e = (sx < 0 || sy < 0 || sz < 0) ? post_el<L>(P, x, y, z, a, 1)
+                                                            : pel<L>(pnode(P, sx, sy, sz)) + 32u * uint32_t(L::opp(a));
+            s += S::g(__ldg(g + e), L::w(a));
+        }
+    }
+    phi[(int64_t(z) * P.ny + y) * P.nx + x] = s;
+}
+
 // Resident blocks per SM: for D3Q19 as many as hold 24 warps (the pair-form
 // node update needs up to 85 registers), for D2Q9 as many as hold 32 warps
 // (64 registers, no spills).
 template <class L, int NT>
 constexpr int fused_min_blocks() { return (L::D == 3) ? 768 / NT : 1024 / NT; }
+
+// The odd in-place form gathers its populations from 2Q different rows: for
+// D3Q19 it gets the registers of three resident blocks per SM (18 warps).
+template <class L, int NT, int MODE>
+constexpr int inplace_min_blocks() { return (L::D == 3 && MODE == STEP_ODD) ? 576 / NT : fused_min_blocks<L, NT>(); }
 
 // The fused step, A/B form: fA, gA -> fB, gB.
 template <class L, class S, int TX, int TY>
@@ -945,7 +1005,7 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typen
 // The fused step on the in-place layout, form MODE (STEP_EVEN or STEP_ODD):
 // one copy f, g of each set, read and written (not restrict-qualified).
 template <class L, class S, int TX, int TY, int MODE>
-__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (fused_min_blocks<L, TX *((L::D == 3) ? TY : 1)>()))
+__global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (inplace_min_blocks<L, TX *((L::D == 3) ? TY : 1), MODE>()))
 k_step_inplace(const __grid_constant__ DevParams P, const FusedGeom G, typename S::T* f, typename S::T* g)
 {
     extern __shared__ float smem[];
@@ -1664,7 +1724,7 @@ cudaError_t Launch<L, S>::step_timed(const DevParams& P, const FusedGeom& G, int
     } else {
         // phi pre-pass into P.phis, then the even (natural -> swapped) or the
         // odd (swapped -> natural) in-place form
-        k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, gA, b.par, b.phi);
+        k_phi_pre<L, S><<<dim3((P.nx + 127) / 128, P.ny, (L::D == 3) ? P.nz : 1), 128, 0, s>>>(P, gA, b.par, b.phi);
         if ((e = mark()) != cudaSuccess) return e;
         if (b.par == 0) k_step_inplace<L, S, TX, TY, STEP_EVEN><<<nblocks, blk, Cfg::smem, s>>>(P, G, fB, gB);
         else k_step_inplace<L, S, TX, TY, STEP_ODD><<<nblocks, blk, Cfg::smem, s>>>(P, G, fB, gB);

@@ -166,6 +166,210 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, in
             }
 }
 
+// ---------------------------------------------------------- tcgen05 path
+//
+// The forward convolution as an implicit GEMM on the fifth-generation tensor
+// cores: a block computes a 128-position x TN-channel tile of
+// Y[m][co] = sum_k A[m][k] W[co][k] with one tcgen05.mma (M = 128, N = TN,
+// K = 16, bfloat16 operands, float32 accumulator in tensor memory) per 16 k,
+// issued by one thread.  The operand tiles of 64 k are gathered by all 128
+// threads into shared memory in the canonical K-major layout without swizzle
+// (8-row x 16-byte core matrices; core matrices adjacent in k 128 bytes apart,
+// 8-row groups 1024 bytes apart), two stages deep: the gather of stage k + 1
+// overlaps the tensor cores' work on stage k, and an mbarrier that the MMA
+// unit's commit arrives on says when a stage may be overwritten.  The
+// accumulator is read back by the four warps with tcgen05.ld (warp w owns
+// tensor-memory lanes 32 w .. 32 w + 31 = the tile's rows) for the epilogue
+// (bias, ReLU, bfloat16 / float32 outputs, or split-K partial sums).  Every
+// wait on an mbarrier is bounded: on timeout the block records an error flag
+// and leaves after a bounded wait for its own MMAs, freeing its tensor memory.
+
+constexpr int TC_TM = 128, TC_BK = 64;
+constexpr uint32_t TC_SBO = 1024, TC_LBO = 128;       // bytes: 8-row groups, k-adjacent core matrices
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor of tcgen05 (no swizzle): start address,
+// leading (k) and stride (m/n) byte offsets, each >> 4; descriptor version 1.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr)
+{
+    return uint64_t((saddr >> 4) & 0x3FFFu) | (uint64_t((TC_LBO >> 4) & 0x3FFFu) << 16) |
+           (uint64_t((TC_SBO >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: float32 accumulator,
+// bfloat16 A and B, both K-major, N = n, M = 128.
+__host__ __device__ constexpr uint32_t tc_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(TC_TM >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// bounded wait for the phase `parity` of the mbarrier; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+template <int TN>
+__global__ void __launch_bounds__(128) k_conv_fwd_tc(const bf16* __restrict__ X, int xs, int ci, int taps,
+                                                     const bf16* __restrict__ Wt, const float* __restrict__ bias,
+                                                     int co, bf16* __restrict__ Y, int ys, int yo,
+                                                     float* __restrict__ Yf, int yfs, int relu, int M, int H, int W,
+                                                     int kchunk, float* __restrict__ part, int* __restrict__ err)
+{
+    static_assert(TN % 16 == 0 && TN >= 32 && TN <= 256, "N of an M = 128 MMA");
+    constexpr int A_BYTES = TC_TM * TC_BK * 2, B_BYTES = TN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
+    constexpr uint32_t NCOL = TN;                          // float32 accumulator columns (a power of two)
+    extern __shared__ __align__(1024) uint8_t tc_smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + 2 * STAGE);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_smem + 2 * STAGE + 16);
+    int* s_ok = reinterpret_cast<int*>(tc_smem + 2 * STAGE + 20);     // one thread waits, all read
+    const int K = taps * ci;
+    const int m0 = blockIdx.x * TC_TM, n0 = blockIdx.y * TN;
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tslot)),
+                     "r"(NCOL)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    const int nk = (ke - kb + TC_BK - 1) / TC_BK;
+    uint32_t phase0 = 0, phase1 = 0;
+    bool ok = true;
+    for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt & 1;
+        const uint32_t bar = s ? bar1 : bar0;
+        // the MMAs issued on this stage two tiles ago must be done reading it
+        // (thread 0 waits; the block learns the outcome at the barrier)
+        if (kt >= 2) {
+            if (tid == 0) *s_ok = mbar_wait(bar, s ? phase1 : phase0) ? 1 : 0;
+            if (s) phase1 ^= 1u; else phase0 ^= 1u;
+            __syncthreads();
+            ok = *s_ok != 0;
+            if (!ok) break;                               // the same for every thread
+        }
+        uint8_t* As = tc_smem + s * STAGE;
+        uint8_t* Bs = As + A_BYTES;
+        const int k0 = kb + kt * TC_BK;
+        // 8 vectors of 8 k per row: A 128 rows, B TN rows (zero outside)
+        for (int v = tid; v < TC_TM * 8; v += 128) {
+            const int r = v >> 3, q = v & 7, k = k0 + q * 8;
+            const uint4 val = k < ke ? patch8(X, xs, ci, taps, m0 + r, k, M, K, H, W) : make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(As + (r >> 3) * TC_SBO + q * TC_LBO + (r & 7) * 16) = val;
+        }
+        for (int v = tid; v < TN * 8; v += 128) {
+            const int r = v >> 3, q = v & 7, n = n0 + r, k = k0 + q * 8;
+            const uint4 val = (n < co && k < ke) ? *reinterpret_cast<const uint4*>(Wt + int64_t(n) * K + k)
+                                                 : make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(Bs + (r >> 3) * TC_SBO + q * TC_LBO + (r & 7) * 16) = val;
+        }
+        // make the generic-proxy stores visible to the tensor cores' reads
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+#pragma unroll
+            for (int j = 0; j < TC_BK / 16; ++j) {
+                const uint64_t ad = tc_desc(a0 + j * 2 * TC_LBO), bd = tc_desc(b0 + j * 2 * TC_LBO);
+                const uint32_t acc = (kt > 0 || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(tc_idesc(TN)), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                         : "memory");
+        }
+    }
+    // the last commit covers every MMA of the block
+    const int sl = nk > 0 ? (nk - 1) & 1 : 0;
+    if (tid == 0) {
+        if (ok && nk > 0) ok = mbar_wait(sl ? bar1 : bar0, sl ? phase1 : phase0);
+        if (!ok) {
+            atomicExch(err, 1);
+            // drain: give the MMAs in flight a bounded time before the memory goes
+            if (nk > 0) mbar_wait(sl ? bar1 : bar0, sl ? phase1 : phase0);
+        }
+        *s_ok = ok ? 1 : 0;
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    }
+    __syncthreads();
+    ok = *s_ok != 0;
+    if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const int m = m0 + warp * 32 + lane;               // this thread's row of the tile
+#pragma unroll
+        for (int c0 = 0; c0 < TN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (m >= M) continue;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int n = n0 + c0 + e;
+                if (n >= co) continue;
+                const float a = __uint_as_float(r[e]);
+                if (part) {                   // split-K: the raw partial sum of this k range
+                    part[(int64_t(blockIdx.z) * M + m) * co + n] = a;
+                    continue;
+                }
+                float v = a + (bias ? bias[n] : 0.0f);
+                if (relu) v = fmaxf(v, 0.0f);
+                if (Y) Y[int64_t(m) * ys + yo + n] = __float2bfloat16_rn(v);
+                if (Yf) Yf[int64_t(m) * yfs + n] = v;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOL) : "memory");
+    }
+}
+
+template <int TN>
+constexpr int tc_smem_bytes() { return 2 * (TC_TM * TC_BK * 2 + TN * TC_BK * 2) + 32; }
+
 // Sum of the split-K partial sums part[z][m][n] in the order z = 0, 1, ...
 // (deterministic), then bias, ReLU and the outputs of k_conv_fwd.
 __global__ void k_conv_reduce(const float* __restrict__ part, int splits, int M, int co,
@@ -595,6 +799,38 @@ unsigned blocks_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
 constexpr int kTargetBlocks = 2 * 152;                  // two 128-thread blocks per SM of a GB300
 constexpr int64_t kConvWsFloats = int64_t(1) << 22;     // largest split-K workspace (16 MB)
 
+// forward convolution contraction: 0 tcgen05 (tensor memory), 1 warp-level mma.sync
+int g_conv_path = 0;
+// per-device error flag of the tcgen05 kernels (a bounded wait gave up)
+int* g_tc_err[64] = {};
+
+int tc_err_flag(int** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) return nn_fail(LBM_NN_ERR_CUDA, "conv_fwd: no device");
+    if (!g_tc_err[dev]) {
+        e = cudaMalloc(reinterpret_cast<void**>(&g_tc_err[dev]), sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(g_tc_err[dev], 0, sizeof(int));
+        if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("conv_fwd: error flag: ") + cudaGetErrorString(e));
+    }
+    *out = g_tc_err[dev];
+    return LBM_NN_OK;
+}
+
+template <int TN>
+cudaError_t launch_tc(dim3 grid, cudaStream_t s, const bf16* X, int xs, int ci, int taps, const bf16* Wt,
+                      const float* bias, int co, bf16* Y, int ys, int yo, float* Yf, int yfs, int relu, int M, int H,
+                      int W, int kchunk, float* part, int* err)
+{
+    constexpr int smem = tc_smem_bytes<TN>();
+    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_conv_fwd_tc<TN><<<grid, 128, smem, s>>>(X, xs, ci, taps, Wt, bias, co, Y, ys, yo, Yf, yfs, relu, M, H, W, kchunk,
+                                             part, err);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" {
@@ -613,8 +849,12 @@ int lbm_nn_conv_fwd(const void* x, int32_t x_stride, int32_t ci, int32_t taps, c
     if (yf && yf_stride < co) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: f32 output stride below co");
     const int M = nb * h * w, K = taps * ci;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const bool narrow = co <= 32;                 // 128 x 32 tiles: no idle half of a 64-wide tile
-    const int TM = narrow ? 128 : BM, TN = narrow ? 32 : BN;
+    const bool tc = g_conv_path == 0;
+    // tcgen05: 128 x 32 / 64 / 128 tiles by the channel count; mma.sync:
+    // 128 x 32 tiles (no idle half of a 64-wide tile) or 64 x 64
+    const bool narrow = co <= 32;
+    const int TM = tc ? TC_TM : (narrow ? 128 : BM);
+    const int TN = tc ? (co <= 32 ? 32 : co <= 64 ? 64 : 128) : (narrow ? 32 : BN);
     const int tiles = blocks_for(M, TM) * blocks_for(co, TN);
     // Split-K when the output tiles alone leave the GPU mostly idle (the deep,
     // coarse levels of the network): each split writes its partial sums to a
@@ -630,13 +870,29 @@ int lbm_nn_conv_fwd(const void* x, int32_t x_stride, int32_t ci, int32_t taps, c
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ws), size_t(splits) * M * co * sizeof(float), s);
         if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("conv_fwd: workspace: ") + cudaGetErrorString(e));
     }
-    const int kchunk = splits > 1 ? blocks_for(blocks_for(K, splits), BK) * BK : K;
+    const int kstep = tc ? TC_BK : BK;
+    const int kchunk = splits > 1 ? blocks_for(blocks_for(K, splits), kstep) * kstep : K;
     splits = blocks_for(K, kchunk);
     dim3 grid(blocks_for(M, TM), blocks_for(co, TN), splits);
-    auto kern = narrow ? k_conv_fwd<128, 32> : k_conv_fwd<BM, BN>;
-    kern<<<grid, 128, 0, s>>>(static_cast<const bf16*>(x), x_stride, ci, taps, static_cast<const bf16*>(wt), bias, co,
-                              static_cast<bf16*>(y), y_stride, y_offset, yf, yf_stride, relu, M, h, w, kchunk,
-                              splits > 1 ? ws : nullptr);
+    if (tc) {
+        int* err = nullptr;
+        const int r = tc_err_flag(&err);
+        if (r != LBM_NN_OK) return r;
+        const bf16* X = static_cast<const bf16*>(x);
+        const bf16* Wt = static_cast<const bf16*>(wt);
+        bf16* Y = static_cast<bf16*>(y);
+        float* part = splits > 1 ? ws : nullptr;
+        cudaError_t e;
+        if (TN == 32) e = launch_tc<32>(grid, s, X, x_stride, ci, taps, Wt, bias, co, Y, y_stride, y_offset, yf, yf_stride, relu, M, h, w, kchunk, part, err);
+        else if (TN == 64) e = launch_tc<64>(grid, s, X, x_stride, ci, taps, Wt, bias, co, Y, y_stride, y_offset, yf, yf_stride, relu, M, h, w, kchunk, part, err);
+        else e = launch_tc<128>(grid, s, X, x_stride, ci, taps, Wt, bias, co, Y, y_stride, y_offset, yf, yf_stride, relu, M, h, w, kchunk, part, err);
+        if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("conv_fwd: ") + cudaGetErrorString(e));
+    } else {
+        auto kern = narrow ? k_conv_fwd<128, 32> : k_conv_fwd<BM, BN>;
+        kern<<<grid, 128, 0, s>>>(static_cast<const bf16*>(x), x_stride, ci, taps, static_cast<const bf16*>(wt), bias,
+                                  co, static_cast<bf16*>(y), y_stride, y_offset, yf, yf_stride, relu, M, h, w, kchunk,
+                                  splits > 1 ? ws : nullptr);
+    }
     if (ws) {
         k_conv_reduce<<<blocks_for(int64_t(M) * co, 256), 256, 0, s>>>(ws, splits, M, co, bias, relu,
                                                                        static_cast<bf16*>(y), y_stride, y_offset, yf,
@@ -687,6 +943,27 @@ int lbm_nn_conv_wgrad(const void* x, int32_t x_stride, int32_t ci, int32_t taps,
         if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("conv_wgrad: workspace: ") + cudaGetErrorString(e));
     }
     return nn_launch_status("conv_wgrad");
+}
+
+int lbm_nn_set_conv_path(int32_t path)
+{
+    if (path != 0 && path != 1) return nn_fail(LBM_NN_ERR_ARG, "conv path must be 0 (tcgen05) or 1 (mma.sync)");
+    g_conv_path = path;
+    return LBM_NN_OK;
+}
+
+int lbm_nn_conv_status(int32_t* timed_out)
+{
+    if (!timed_out) return nn_fail(LBM_NN_ERR_ARG, "conv_status: NULL");
+    int* err = nullptr;
+    const int r = tc_err_flag(&err);
+    if (r != LBM_NN_OK) return r;
+    int h = 0;
+    cudaError_t e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+    if (e != cudaSuccess) return nn_fail(LBM_NN_ERR_CUDA, std::string("conv_status: ") + cudaGetErrorString(e));
+    *timed_out = h;
+    return LBM_NN_OK;
 }
 
 int lbm_nn_flip_weights(const void* wt, int32_t ci, int32_t co, int32_t taps, void* wflip, void* stream)

@@ -22,7 +22,7 @@ import numpy as np
 from . import lbm as _lbm
 
 LBM_NN_OK, LBM_NN_ERR_ARG, LBM_NN_ERR_CUDA = 0, -1, -2
-NN_EXPORTS = ["lbm_nn_last_error", "lbm_nn_conv_fwd", "lbm_nn_conv_wgrad", "lbm_nn_flip_weights", "lbm_nn_relu_bwd",
+NN_EXPORTS = ["lbm_nn_last_error", "lbm_nn_conv_fwd", "lbm_nn_set_conv_path", "lbm_nn_conv_status", "lbm_nn_conv_wgrad", "lbm_nn_flip_weights", "lbm_nn_relu_bwd",
               "lbm_nn_pool", "lbm_nn_pool_bwd", "lbm_nn_upsample", "lbm_nn_upsample_bwd", "lbm_nn_mse", "lbm_nn_adam",
               "lbm_nn_to_bf16", "lbm_nn_add", "lbm_nn_coarsen", "lbm_nn_refine", "lbm_nn_sharpen", "lbm_nn_mass_project",
               "lbm_nn_interface_stats", "lbm_nn_jet_length"]
@@ -43,6 +43,8 @@ def load():
     sig = {
         "lbm_nn_conv_fwd": [vp, i32, i32, i32, vp, fp, i32, vp, i32, i32, fp, i32, i32, i32, i32, i32, vp],
         "lbm_nn_conv_wgrad": [vp, i32, i32, i32, vp, i32, i32, fp, fp, i32, i32, i32, vp],
+        "lbm_nn_set_conv_path": [i32],
+        "lbm_nn_conv_status": [ctypes.POINTER(ctypes.c_int32)],
         "lbm_nn_flip_weights": [vp, i32, i32, i32, vp, vp],
         "lbm_nn_relu_bwd": [vp, i32, i32, vp, i32, i32, vp, i32, i32, i64, vp],
         "lbm_nn_pool": [vp, i32, i32, vp, i32, i32, i32, i32, i32, i32, vp],
@@ -72,6 +74,22 @@ def load():
 
 def _p(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def set_conv_path(path: int):
+    """0: tcgen05 tensor-memory convolutions (default); 1: warp-level mma.sync."""
+    lib = load()
+    if lib.lbm_nn_set_conv_path(int(path)) != 0:
+        raise NNError(lib.lbm_nn_last_error().decode())
+
+
+def conv_timed_out() -> bool:
+    """True if a bounded wait of the tcgen05 kernels gave up since the last call."""
+    lib = load()
+    t = ctypes.c_int32()
+    if lib.lbm_nn_conv_status(ctypes.byref(t)) != 0:
+        raise NNError(lib.lbm_nn_last_error().decode())
+    return bool(t.value)
 
 
 def _s(stream):

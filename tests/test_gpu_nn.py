@@ -44,11 +44,17 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30)
 
 
-@pytest.mark.parametrize("taps,ci,co", [(9, 8, 16), (9, 32, 72), (1, 32, 8), (9, 16, 130)])
-def test_conv_forward_backward_and_weight_gradient(env, report, taps, ci, co):
+@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("taps,ci,co,B,H,W", [(9, 8, 16, 2, 12, 20), (9, 32, 72, 2, 12, 20), (1, 32, 8, 2, 12, 20),
+                                             (9, 16, 130, 2, 12, 20), (9, 128, 256, 1, 8, 24), (9, 64, 128, 3, 16, 16)])
+def test_conv_forward_backward_and_weight_gradient(env, report, taps, ci, co, B, H, W, path):
+    """Both contractions (path 0: tcgen05 with the accumulator in tensor
+    memory; path 1: warp-level mma.sync).  480 positions are ragged against
+    64- and 128-row tiles; 192 positions with K = 1152 and 256 channels take
+    the split-K path; 130 channels leave a partial channel tile."""
     torch, nn, O = env
+    nn.set_conv_path(path)
     r = np.random.Generator(np.random.PCG64(10 + taps + ci + co))
-    B, H, W = 2, 12, 20                       # 480 positions: ragged against 64-row tiles
     x = bf16_round(r.standard_normal((B, H, W, ci)))
     wt = bf16_round(r.standard_normal((co, taps * ci)) / np.sqrt(taps * ci))
     bias = r.standard_normal(co).astype(np.float32).astype(np.float64)
@@ -84,7 +90,9 @@ def test_conv_forward_backward_and_weight_gradient(env, report, taps, ci, co):
         e_db = rel(db.cpu().numpy(), rdb)
         vals.update(bwd_data=e_dx, wgrad=e_dw, bgrad=e_db)
         assert e_dx < 1e-5 and e_dw < 1e-5 and e_db < 1e-5
-    report("nn_conv_t%d_ci%d_co%d" % (taps, ci, co), **vals)
+    report("nn_conv_t%d_ci%d_co%d_path%d" % (taps, ci, co, path), **vals)
+    assert not nn.conv_timed_out()
+    nn.set_conv_path(0)
 
 
 def test_pool_upsample_relu_kernels(env):

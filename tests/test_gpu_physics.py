@@ -71,11 +71,11 @@ def test_laplace_3d_drop(lib, report):
     """tab:laplace_errors at sigma = 1e-3: 100^3 periodic box, drops of
     R = 15 .. 35, W = 4, rho* = 1000, tau = 0.5, 50,000 iterations.
     eq:laplace_law takes R as the radius of the drop in its equilibrium
-    state: here the radius of the sphere holding the drop's phase volume,
-    (3 sum(phi) / (4 pi))^(1/3); dp = 2 sigma / R in 3D (reading R10).  The
-    paper prints 0.91 % (R = 15) falling to 0.31 % (R = 35); this model's
-    pressure jump is a few per cent low, falling with R like (W / R)^2, the
-    order of the diffuse interface's curvature error."""
+    state: here the radius of the sphere enclosing as many nodes as the
+    phi > 1/2 region (the interface is phi = 1/2); dp = 2 sigma / R in 3D
+    (reading R10).  The paper prints 0.91 % (R = 15) falling to 0.31 %
+    (R = 35); this model's pressure jump is a few per cent low and, like the
+    paper's, its error falls as the drop grows (about 1 / R)."""
     sigma = 1e-3
     errs = []
     for R in (15.0, 20.0, 25.0, 30.0, 35.0):
@@ -84,14 +84,16 @@ def test_laplace_3d_drop(lib, report):
         sim.init_fields(phi, u, ps)
         sim.step(50000)
         d = sim.diag(1e-3)
-        r_eq = (3.0 * d["sum_phi"] / (4.0 * np.pi)) ** (1.0 / 3.0)
-        err = d["dp_laplace"] / (2 * sigma / r_eq) - 1
-        report("laplace_3d_R%d" % int(R), rel_err=err, rel_err_initial_radius=d["dp_laplace"] / (2 * sigma / R) - 1,
-               r_eq=r_eq, dp=d["dp_laplace"], mass=d["sum_phi"])
+        js = sim.jet_stats(0.5, 8)
+        assert js["n_components"] == 1 and js["has_jet"] == 0      # one drop, clear of z = 0
+        r_half = (3.0 * js["drop_volume"] / (4.0 * np.pi)) ** (1.0 / 3.0)
+        err = d["dp_laplace"] / (2 * sigma / r_half) - 1
+        report("laplace_3d_R%d" % int(R), rel_err=err, r_half=r_half, rel_err_initial_radius=d["dp_laplace"] / (2 * sigma / R) - 1,
+               dp=d["dp_laplace"], mass=d["sum_phi"])
         assert d["finite"] == 1
         errs.append(err)
         sim.close()
     errs = np.abs(np.array(errs))
-    assert errs.max() < 0.06
-    # the error shrinks with the drop, like the paper's
-    assert errs[-1] < errs[0] and errs[2] < errs[0]
+    assert errs.max() < 0.05
+    # the error shrinks as the drop grows, like the paper's
+    assert np.all(np.diff(errs) < 0.002) and errs[-1] < 0.7 * errs[0]
