@@ -578,6 +578,7 @@ def run_learned(args):
     from paper_2505_12205_gb300 import build, nn, surrogate as S
     build.build()
     torch.cuda.set_device(0)
+    nn.set_conv_path(0 if args.conv_path == "tcgen05" else 1)
     t0, t1 = LEARNED["t0"], LEARNED["t1"]
     log = lambda msg: print("[learned] " + msg, file=sys.stderr, flush=True)
     tic = time.perf_counter()
@@ -648,16 +649,18 @@ def run_nn(args):
     torch.cuda.set_device(0)
     nn.load()
     cin, ch, head, H, W = 8, (32, 64, 128, 256), 8, 512, 128
+    nb = args.batch
+    nn.set_conv_path(0 if args.conv_path == "tcgen05" else 1)
     net = nn.UNet(cin=cin, ch=ch, head=head)
     net.init_he(seed=7)
     g = torch.Generator(device="cuda")
     g.manual_seed(C.SEED + 9)
-    x = (0.5 * torch.randn(H * W, cin, generator=g, device="cuda")).to(torch.bfloat16).contiguous()
-    t = torch.randn(H * W, 3, generator=g, device="cuda").contiguous()
+    x = (0.5 * torch.randn(nb * H * W, cin, generator=g, device="cuda")).to(torch.bfloat16).contiguous()
+    t = torch.randn(nb * H * W, 3, generator=g, device="cuda").contiguous()
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
-        net.forward(x, 1, H, W, target=t)
-        net.backward(x, 1, H, W)
+        net.forward(x, nb, H, W, target=t)
+        net.backward(x, nb, H, W)
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
@@ -665,17 +668,18 @@ def run_nn(args):
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record(stream)
     for _ in range(args.steps):
-        net.forward(x, 1, H, W)
+        net.forward(x, nb, H, W)
     e1.record(stream)
     for _ in range(args.steps):
-        net.forward(x, 1, H, W, target=t)
-        net.backward(x, 1, H, W)
+        net.forward(x, nb, H, W, target=t)
+        net.backward(x, nb, H, W)
     e2.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms_inf = e0.elapsed_time(e1) / args.steps
     ms_train = e1.elapsed_time(e2) / args.steps
-    f_inf = unet_flops(cin, ch, head, H, W)
+    f_inf = nb * unet_flops(cin, ch, head, H, W)
+    timed_out = nn.conv_timed_out()
     tf_inf = f_inf / (ms_inf * 1e-3) / 1e12
     tf_train = 3 * f_inf / (ms_train * 1e-3) / 1e12
     try:
@@ -686,18 +690,22 @@ def run_nn(args):
     line = {"metric": "TFLOP/s", "value": tf_inf, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_inf, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16 operands, f32 accumulation", "data": "synthetic",
-            "config": {"workload": "encoder-decoder 32-256 channels on a 128 x 512 x 8 input (learned fast-forward)",
-                       "gflop_per_inference": f_inf / 1e9, "l2": "weights and activations are L2-resident"},
+            "config": {"workload": "encoder-decoder 32-256 channels on %d x 128 x 512 x 8 inputs (learned fast-forward)" % nb,
+                       "batch": nb, "conv_path": args.conv_path,
+                       "gflop_per_inference": f_inf / 1e9, "l2": "weights and activations are L2-resident"
+                       if nb <= 4 else "activations partly beyond L2"},
             "training_step": {"ms": ms_train, "tflops": tf_train},
             "roofline": {"bound": "tensor", "achieved": tf_inf, "peak": peak, "unit": "TFLOP/s",
                          "frac": tf_inf / peak, "traffic": None, "peak_source": kind,
-                         "kernel": "k_conv_fwd (mma.sync m16n8k16 bf16) + split-K reduction"},
+                         "kernel": ("k_conv_fwd_tc (tcgen05.mma, tensor-memory accumulator)" if args.conv_path == "tcgen05"
+                                    else "k_conv_fwd (mma.sync m16n8k16 bf16)") + " + split-K reduction"},
+            "bounded_wait_timed_out": timed_out,
             "clocks": clk}
     print(json.dumps(line))
     return 0
 
 
-JETSWEEP = dict(We=[1.0, 2.2, 3.5, 5.0], nx=192, ny=192, nz=640, Rn=16.0, steps=48000, sample_from=24000,
+JETSWEEP = dict(We=[1.0, 2.2, 3.5, 5.0, 10.0], nx=192, ny=192, nz=640, Rn=16.0, steps=48000, sample_from=24000,
                 sample_every=500)
 
 
@@ -711,7 +719,7 @@ def run_jet_sweep(args):
     D = 2.0 * cfg["Rn"]
     rows = []
     tic = time.perf_counter()
-    for We in cfg["We"]:
+    for We in (args.we if args.we else cfg["We"]):
         p, phi, u, ps = C.jet3d(nx=cfg["nx"], ny=cfg["ny"], nz=cfg["nz"], Rn=cfg["Rn"], We=We)
         p["bc"] = [C.FREESLIP, C.FREESLIP, C.FREESLIP, C.FREESLIP, C.INLET, C.OUTFLOW]
         sim = lbm.LBM(p)
@@ -753,6 +761,11 @@ def main():
                     help="population storage format (arithmetic is float32); default fp32 for the "
                          "jet, fp16 for the sweep")
     ap.add_argument("--workload", default="jet", choices=["jet", "rt2d", "sweep", "learned", "jet-sweep", "nn"])
+    ap.add_argument("--batch", type=int, default=1, help="inputs per inference of the nn workload")
+    ap.add_argument("--conv-path", default="tcgen05", choices=["tcgen05", "mma.sync"],
+                    help="convolution contraction of the nn / learned workloads")
+    ap.add_argument("--we", type=float, nargs="+", default=None,
+                    help="Weber numbers of the jet-sweep workload (default: 1, 2.2, 3.5, 5, 10)")
     ap.add_argument("--layout", default="ab", choices=["ab", "inplace"],
                     help="population layout of the jet / rt2d workloads: two copies (A/B) or one (in place)")
     ap.add_argument("--diag-every", type=int, default=100,

@@ -156,7 +156,10 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out);
 /* Set the state to the equilibria of the given fields (eq:equilibrium,
  * eq:equilibrium_function): g_a = phi Gamma_a(u), f_a = p* w_a + Gamma_a(u)
  * - w_a.  phi: [N]; u: [D][N] or NULL (zero); pstar: [N] or NULL (zero),
- * p* = p / (rho c_s^2). */
+ * p* = p / (rho c_s^2).  Host arrays that are page-locked (cudaHostAlloc,
+ * cudaHostRegister, torch pin_memory) are read by the kernel in place; other
+ * host arrays are copied to the device first.  Synchronises when on_device
+ * is 0. */
 int lbm_init_fields(lbm_ctx* ctx, const float* phi, const float* u, const float* pstar,
                     int on_device);
 
@@ -182,8 +185,9 @@ int lbm_diag_last(const lbm_ctx* ctx, lbm_diag_out* out, int64_t* step);
 
 /* Macroscopic fields of the current state, computed with the same device
  * code as the step: phi [N], u [D][N] (eq:velocity_update), p [N]
- * (p = p* rho c_s^2).  Any output may be NULL.  Synchronises when on_device
- * is 0. */
+ * (p = p* rho c_s^2).  Any output may be NULL.  Page-locked host outputs are
+ * written by the kernel in place, other host outputs through a device copy.
+ * Synchronises when on_device is 0. */
 int lbm_get_fields(lbm_ctx* ctx, float* phi, float* u, float* p, int on_device);
 
 /* Raw state (checkpoint): the post-streaming populations f and g, each

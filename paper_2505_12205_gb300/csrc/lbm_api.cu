@@ -481,10 +481,43 @@ int lbm_sync(lbm_ctx* c)
     return LBM_OK;
 }
 
+// The device address of page-locked (pinned or registered) host memory, or
+// nullptr for any other pointer: kernels then read or write the caller's host
+// array directly (over the GPU's host link), with no staging copy.
+static const void* host_view(const void* p)
+{
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();                 // not a CUDA-known pointer: no sticky error
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 int lbm_init_fields(lbm_ctx* c, const float* phi, const float* u, const float* pstar, int on_device)
 {
     if (!c) return LBM_ERR_ARG;
     if (!phi) return fail(c, LBM_ERR_ARG, "phi is NULL");
+    if (!on_device) {
+        // page-locked host fields: the init kernel reads them in place
+        const float* vphi = static_cast<const float*>(host_view(phi));
+        const float* vu = static_cast<const float*>(host_view(u));
+        const float* vp = static_cast<const float*>(host_view(pstar));
+        if (vphi && (!u || vu) && (!pstar || vp)) {
+            c->b.par = 0;
+            cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
+                cudaError_t r = decltype(l)::init(c->dp, vphi, vu, vp, c->b.fA, c->b.gA, c->stream);
+                if (r == cudaSuccess && c->b.inplace) r = decltype(l)::save_outlet(c->dp, c->b, c->stream);
+                return r;
+            });
+            if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+            LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+            c->initialised = true;
+            c->step_count = 0;
+            return LBM_OK;
+        }
+    }
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const size_t nb = size_t(c->N) * sizeof(float);
     // stage the fields in the f buffer B (Q * elem >= 4 (D + 2) bytes per
@@ -547,6 +580,19 @@ int lbm_get_fields(lbm_ctx* c, float* phi, float* u, float* p, int on_device)
 {
     if (!c) return LBM_ERR_ARG;
     if (!c->initialised) return fail(c, LBM_ERR_STATE, "no state");
+    if (!on_device && (phi || u || p)) {
+        // page-locked host outputs: the fields kernel writes them in place
+        float* vphi = static_cast<float*>(const_cast<void*>(host_view(phi)));
+        float* vu = static_cast<float*>(const_cast<void*>(host_view(u)));
+        float* vp = static_cast<float*>(const_cast<void*>(host_view(p)));
+        if ((!phi || vphi) && (!u || vu) && (!p || vp)) {
+            cudaError_t e = with_launch(c->D, c->p.storage,
+                                        [&](auto l) { return decltype(l)::fields(c->dp, c->b, vphi, vu, vp, c->stream); });
+            if (e != cudaSuccess) return cuda_fail(c, e, "fields kernel");
+            LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+            return LBM_OK;
+        }
+    }
     // outputs are computed into the f buffer B (or the field buffer of the
     // in-place layout), then copied out
     float* o_phi = c->b.inplace ? c->fieldbuf : static_cast<float*>(c->b.fB);

@@ -952,23 +952,55 @@ __global__ void __launch_bounds__(128) k_phi_pre(const __grid_constant__ DevPara
 #pragma unroll
         for (int a = 0; a < L::Q; ++a) s += S::g(__ldg(g + e0 + 32 * a), L::w(a));
     } else {
-        // the upstream coordinates x - 1, x + 1 (y, z likewise), wrapped across
-        // periodic faces; a step beyond any other face goes through post_el
-        // (rows of the face planes only: uniform over a block in y and z)
-        const int xm = x > 0 ? x - 1 : (P.bc[0] == BC_PERIODIC ? P.nx - 1 : -1);
-        const int xp = x < P.nx - 1 ? x + 1 : (P.bc[1] == BC_PERIODIC ? 0 : -1);
-        const int ym = y > 0 ? y - 1 : (P.bc[2] == BC_PERIODIC ? P.ny - 1 : -1);
-        const int yp = y < P.ny - 1 ? y + 1 : (P.bc[3] == BC_PERIODIC ? 0 : -1);
-        const int zm = L::D == 2 ? 0 : (z > 0 ? z - 1 : (P.bc[4] == BC_PERIODIC ? P.nz - 1 : -1));
-        const int zp = L::D == 2 ? 0 : (z < P.nz - 1 ? z + 1 : (P.bc[5] == BC_PERIODIC ? 0 : -1));
+        // element offsets of the node steps -1 and +1 along each axis, wrapped
+        // across periodic faces (along x they depend on the lane x mod 32:
+        // taken on the block B = 1, modular uint32 arithmetic); a step beyond
+        // any other face goes through post_el (face planes in y and z are
+        // whole blocks; in x the two edge lanes)
+        const int pos[3] = {x, y, z}, len[3] = {P.nx, P.ny, P.nz};
+        const uint32_t r = uint32_t(x & 31), nstep[3] = {1u, uint32_t(P.nxp), uint32_t(P.nxp) * uint32_t(P.ny)};
+        uint32_t off[3][2];
+        bool open[3][2];
 #pragma unroll
-        for (int a = 0; a < L::Q; ++a) {
-            const int sx = L::ex(a) > 0 ? xm : (L::ex(a) < 0 ? xp : x);
-            const int sy = L::ey(a) > 0 ? ym : (L::ey(a) < 0 ? yp : y);
-            const int sz = L::ez(a) > 0 ? zm : (L::ez(a) < 0 ? zp : z);
-            const uint32_t e = (sx < 0 || sy < 0 || sz < 0) ? post_el<L>(P, x, y, z, a, 1)
-                                                            : pel<L>(pnode(P, sx, sy, sz)) + 32u * uint32_t(L::opp(a));
-            s += S::g(__ldg(g + e), L::w(a));
+        for (int d = 0; d < 3; ++d) {
+            int sm = -1, sp = 1;
+            open[d][0] = open[d][1] = false;
+            if (d < L::D) {
+                if (pos[d] == 0) {
+                    if (P.bc[2 * d] == BC_PERIODIC) sm = len[d] - 1;
+                    else open[d][0] = true;
+                }
+                if (pos[d] == len[d] - 1) {
+                    if (P.bc[2 * d + 1] == BC_PERIODIC) sp = -(len[d] - 1);
+                    else open[d][1] = true;
+                }
+            }
+            if (d == 0) {
+                off[0][0] = pel<L>(r + 32u + uint32_t(sm)) - pel<L>(r + 32u);
+                off[0][1] = pel<L>(r + 32u + uint32_t(sp)) - pel<L>(r + 32u);
+            } else {
+                off[d][0] = uint32_t(sm) * nstep[d] * uint32_t(L::Q);
+                off[d][1] = uint32_t(sp) * nstep[d] * uint32_t(L::Q);
+            }
+        }
+        const bool any_open = open[0][0] || open[0][1] || open[1][0] || open[1][1] || open[2][0] || open[2][1];
+        if (!any_open) {
+            // every population from the upstream node by its fixed offset: all
+            // loads first, then the sum in the order of k_phi
+            typename S::T v[L::Q];
+#pragma unroll
+            for (int a = 0; a < L::Q; ++a) {
+                uint32_t el = e0 + 32u * uint32_t(L::opp(a));
+                if (L::ex(a)) el += off[0][L::ex(a) > 0 ? 0 : 1];
+                if (L::ey(a)) el += off[1][L::ey(a) > 0 ? 0 : 1];
+                if (L::D == 3 && L::ez(a)) el += off[2][L::ez(a) > 0 ? 0 : 1];
+                v[a] = __ldg(g + el);
+            }
+#pragma unroll
+            for (int a = 0; a < L::Q; ++a) s += S::g(v[a], L::w(a));
+        } else {
+#pragma unroll
+            for (int a = 0; a < L::Q; ++a) s += S::g(__ldg(g + post_el<L>(P, x, y, z, a, 1)), L::w(a));
         }
     }
     phi[(int64_t(z) * P.ny + y) * P.nx + x] = s;

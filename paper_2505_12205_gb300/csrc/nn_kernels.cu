@@ -173,18 +173,20 @@ __global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ X, in
 // Y[m][co] = sum_k A[m][k] W[co][k] with one tcgen05.mma (M = 128, N = TN,
 // K = 16, bfloat16 operands, float32 accumulator in tensor memory) per 16 k,
 // issued by one thread.  The operand tiles of 64 k are gathered by all 128
-// threads into shared memory in the canonical K-major layout without swizzle
-// (8-row x 16-byte core matrices; core matrices adjacent in k 128 bytes apart,
-// 8-row groups 1024 bytes apart), two stages deep: the gather of stage k + 1
-// overlaps the tensor cores' work on stage k, and an mbarrier that the MMA
-// unit's commit arrives on says when a stage may be overwritten.  The
+// threads with 16-byte asynchronous copies (zero-filled outside the image and
+// the matrices) into shared memory in the canonical K-major layout without
+// swizzle (8-row x 16-byte core matrices; core matrices adjacent in k 128
+// bytes apart, 8-row groups 1024 bytes apart), in a ring of three stages: the
+// copies of stages k + 1 and k + 2 are in flight while the tensor cores work
+// on stage k, and an mbarrier that the MMA unit's commit arrives on says when
+// a slot may be refilled.  The
 // accumulator is read back by the four warps with tcgen05.ld (warp w owns
 // tensor-memory lanes 32 w .. 32 w + 31 = the tile's rows) for the epilogue
 // (bias, ReLU, bfloat16 / float32 outputs, or split-K partial sums).  Every
 // wait on an mbarrier is bounded: on timeout the block records an error flag
 // and leaves after a bounded wait for its own MMAs, freeing its tensor memory.
 
-constexpr int TC_TM = 128, TC_BK = 64;
+constexpr int TC_TM = 128, TC_BK = 64, TC_STAGES = 3;
 constexpr uint32_t TC_SBO = 1024, TC_LBO = 128;       // bytes: 8-row groups, k-adjacent core matrices
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
@@ -226,6 +228,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
 template <int TN>
 __global__ void __launch_bounds__(128) k_conv_fwd_tc(const bf16* __restrict__ X, int xs, int ci, int taps,
                                                      const bf16* __restrict__ Wt, const float* __restrict__ bias,
@@ -234,17 +242,18 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const bf16* __restrict__ X,
                                                      int kchunk, float* __restrict__ part, int* __restrict__ err)
 {
     static_assert(TN % 16 == 0 && TN >= 32 && TN <= 256, "N of an M = 128 MMA");
+    constexpr int NS = TC_STAGES;
     constexpr int A_BYTES = TC_TM * TC_BK * 2, B_BYTES = TN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
     constexpr uint32_t NCOL = TN;                          // float32 accumulator columns (a power of two)
     extern __shared__ __align__(1024) uint8_t tc_smem[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + 2 * STAGE);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_smem + 2 * STAGE + 16);
-    int* s_ok = reinterpret_cast<int*>(tc_smem + 2 * STAGE + 20);     // one thread waits, all read
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tc_smem + NS * STAGE);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(tc_smem + NS * STAGE + 8 * NS);
+    int* s_ok = reinterpret_cast<int*>(tc_smem + NS * STAGE + 8 * NS + 4);     // one thread waits, all read
     const int K = taps * ci;
     const int m0 = blockIdx.x * TC_TM, n0 = blockIdx.y * TN;
     const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+    const uint32_t sbase = smem_addr(tc_smem), bar0 = smem_addr(bars);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(tslot)),
@@ -253,8 +262,7 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const bf16* __restrict__ X,
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar1) : "memory");
+        for (int j = 0; j < NS; ++j) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0 + 8 * j) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -262,42 +270,63 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const bf16* __restrict__ X,
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = *tslot;
 
+    // the rows this thread gathers: rq + 16 i, i = 0 .. 7, at the 8-k vector q8;
+    // their pixel index m (-1 beyond M) and coordinates
+    const int rq = tid >> 3, q8 = tid & 7;
+    int pm[8], py[8], px[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + rq + 16 * i;
+        pm[i] = m < M ? m : -1;
+        const int mm = m < M ? m : 0;
+        px[i] = mm % W;
+        py[i] = (mm / W) % H;
+    }
     const int nk = (ke - kb + TC_BK - 1) / TC_BK;
-    uint32_t phase0 = 0, phase1 = 0;
+    // stage kt's operands (A 128 rows, B TN rows, k0 .. k0 + 63, zero outside)
+    // into ring slot kt mod NS by asynchronous copies; one commit group per stage
+    auto gather = [&](int kt) {
+        if (kt < nk) {
+            const uint32_t As = sbase + (kt % NS) * STAGE, Bs = As + A_BYTES;
+            const int k = kb + kt * TC_BK + q8 * 8;
+            const int tap = taps == 9 ? k / ci : 0, c = k - tap * ci;
+            const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = rq + 16 * i, yy = py[i] + dy, xx = px[i] + dx;
+                const bool in = k < ke && pm[i] >= 0 && yy >= 0 && yy < H && xx >= 0 && xx < W;
+                const bf16* src = in ? X + int64_t(pm[i] + dy * W + dx) * xs + c : X;
+                cp_async16(As + (r >> 3) * TC_SBO + q8 * TC_LBO + (r & 7) * 16, src, in ? 16u : 0u);
+            }
+#pragma unroll
+            for (int i = 0; i < TN / 16; ++i) {
+                const int r = rq + 16 * i, n = n0 + r;
+                const bool in = n < co && k < ke;
+                const bf16* src = in ? Wt + int64_t(n) * K + k : Wt;
+                cp_async16(Bs + (r >> 3) * TC_SBO + q8 * TC_LBO + (r & 7) * 16, src, in ? 16u : 0u);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    for (int kt = 0; kt < NS - 1; ++kt) gather(kt);
+
     bool ok = true;
+    int kl = -1;                                          // the last stage whose MMAs were committed
     for (int kt = 0; kt < nk; ++kt) {
-        const int s = kt & 1;
-        const uint32_t bar = s ? bar1 : bar0;
-        // the MMAs issued on this stage two tiles ago must be done reading it
-        // (thread 0 waits; the block learns the outcome at the barrier)
-        if (kt >= 2) {
-            if (tid == 0) *s_ok = mbar_wait(bar, s ? phase1 : phase0) ? 1 : 0;
-            if (s) phase1 ^= 1u; else phase0 ^= 1u;
-            __syncthreads();
-            ok = *s_ok != 0;
-            if (!ok) break;                               // the same for every thread
-        }
-        uint8_t* As = tc_smem + s * STAGE;
-        uint8_t* Bs = As + A_BYTES;
-        const int k0 = kb + kt * TC_BK;
-        // 8 vectors of 8 k per row: A 128 rows, B TN rows (zero outside)
-        for (int v = tid; v < TC_TM * 8; v += 128) {
-            const int r = v >> 3, q = v & 7, k = k0 + q * 8;
-            const uint4 val = k < ke ? patch8(X, xs, ci, taps, m0 + r, k, M, K, H, W) : make_uint4(0u, 0u, 0u, 0u);
-            *reinterpret_cast<uint4*>(As + (r >> 3) * TC_SBO + q * TC_LBO + (r & 7) * 16) = val;
-        }
-        for (int v = tid; v < TN * 8; v += 128) {
-            const int r = v >> 3, q = v & 7, n = n0 + r, k = k0 + q * 8;
-            const uint4 val = (n < co && k < ke) ? *reinterpret_cast<const uint4*>(Wt + int64_t(n) * K + k)
-                                                 : make_uint4(0u, 0u, 0u, 0u);
-            *reinterpret_cast<uint4*>(Bs + (r >> 3) * TC_SBO + q * TC_LBO + (r & 7) * 16) = val;
-        }
-        // make the generic-proxy stores visible to the tensor cores' reads
+        // this thread's copies of stage kt are in; make them visible to the
+        // tensor cores' (async proxy) reads
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 2) : "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        // the MMAs of stage kt - 1 must be done before its slot is refilled
+        // below (thread 0 waits; the block learns the outcome at the barrier)
+        if (tid == 0)
+            *s_ok = kt == 0 || mbar_wait(bar0 + 8 * ((kt - 1) % NS), uint32_t(((kt - 1) / NS) & 1)) ? 1 : 0;
         __syncthreads();
+        ok = *s_ok != 0;
+        if (!ok) break;                                   // the same for every thread
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+            const uint32_t a0 = sbase + (kt % NS) * STAGE, b0 = a0 + A_BYTES;
 #pragma unroll
             for (int j = 0; j < TC_BK / 16; ++j) {
                 const uint64_t ad = tc_desc(a0 + j * 2 * TC_LBO), bd = tc_desc(b0 + j * 2 * TC_LBO);
@@ -308,18 +337,22 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const bf16* __restrict__ X,
                     "l"(ad), "l"(bd), "r"(tc_idesc(TN)), "r"(acc)
                     : "memory");
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             bar0 + 8 * (kt % NS))
                          : "memory");
         }
+        kl = kt;
+        gather(kt + NS - 1);                              // into the slot of stage kt - 1
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     // the last commit covers every MMA of the block
-    const int sl = nk > 0 ? (nk - 1) & 1 : 0;
     if (tid == 0) {
-        if (ok && nk > 0) ok = mbar_wait(sl ? bar1 : bar0, sl ? phase1 : phase0);
+        const uint32_t bl = bar0 + 8 * ((kl < 0 ? 0 : kl) % NS), pl = uint32_t(((kl < 0 ? 0 : kl) / NS) & 1);
+        if (ok && kl >= 0) ok = mbar_wait(bl, pl);
         if (!ok) {
             atomicExch(err, 1);
             // drain: give the MMAs in flight a bounded time before the memory goes
-            if (nk > 0) mbar_wait(sl ? bar1 : bar0, sl ? phase1 : phase0);
+            if (kl >= 0) mbar_wait(bl, pl);
         }
         *s_ok = ok ? 1 : 0;
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -343,9 +376,26 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const bf16* __restrict__ X,
                 : "memory");
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
             if (m >= M) continue;
+            const int nb0 = n0 + c0;
+            if (!part && Y && !Yf && nb0 + 16 <= co && ((ys | (yo + nb0)) & 7) == 0) {
+                // 16 channels of one position: two 16-byte stores
+                uint32_t h[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    float v0 = __uint_as_float(r[2 * e]) + (bias ? bias[nb0 + 2 * e] : 0.0f);
+                    float v1 = __uint_as_float(r[2 * e + 1]) + (bias ? bias[nb0 + 2 * e + 1] : 0.0f);
+                    if (relu) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+                    h[e] = *reinterpret_cast<const uint32_t*>(&b2);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(Y + int64_t(m) * ys + yo + nb0);
+                dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+                dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+                continue;
+            }
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
-                const int n = n0 + c0 + e;
+                const int n = nb0 + e;
                 if (n >= co) continue;
                 const float a = __uint_as_float(r[e]);
                 if (part) {                   // split-K: the raw partial sum of this k range
@@ -368,7 +418,7 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(const bf16* __restrict__ X,
 }
 
 template <int TN>
-constexpr int tc_smem_bytes() { return 2 * (TC_TM * TC_BK * 2 + TN * TC_BK * 2) + 32; }
+constexpr int tc_smem_bytes() { return TC_STAGES * (TC_TM * TC_BK * 2 + TN * TC_BK * 2) + 8 * TC_STAGES + 16; }
 
 // Sum of the split-K partial sums part[z][m][n] in the order z = 0, 1, ...
 // (deterministic), then bias, ReLU and the outputs of k_conv_fwd.
