@@ -578,7 +578,7 @@ def run_learned(args):
     from paper_2505_12205_gb300 import build, nn, surrogate as S
     build.build()
     torch.cuda.set_device(0)
-    nn.set_conv_path(0 if args.conv_path == "tcgen05" else 1)
+    nn.set_conv_path({"tcgen05": 0, "mma.sync": 1, "auto": 2}[args.conv_path])
     t0, t1 = LEARNED["t0"], LEARNED["t1"]
     log = lambda msg: print("[learned] " + msg, file=sys.stderr, flush=True)
     tic = time.perf_counter()
@@ -594,7 +594,18 @@ def run_learned(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - tic
     val, pers = S.evaluate(net, Xt, Yt, np.arange(Xt.shape[0]))
-    res = [S.fast_forward(net, w, t0, t1, skip=args.skip, twins=True) for w in test_We]
+    solves = args.solve or [1]
+    res = [S.fast_forward(net, w, t0, t1, skip=args.skip, twins=True, solve=solves[0]) for w in test_We]
+    more = []
+    for sv in solves[1:]:
+        rs = [S.fast_forward(net, w, t0, t1, skip=args.skip, twins=False, solve=sv) for w in test_We]
+        more.append({"solve": sv, "skip": args.skip,
+                     "speedup_vs_solver": sum(x["ms_solver"] for x in rs) / sum(x["ms_fast_forward"] for x in rs),
+                     "accepted_at_end": sum(1 for x in rs if x["accepted_at_end"]),
+                     "final_interface_distance": [x["final_interface_distance"] for x in rs],
+                     "final_front_error": [x["final_front_error"] for x in rs],
+                     "final_mass_error": [x["final_mass_error"] for x in rs],
+                     "windows": [x["windows"] for x in rs]})
     ms_solver = sum(x["ms_solver"] for x in res)
     ms_ff = sum(x["ms_fast_forward"] for x in res)
     steps = t1 - t0
@@ -606,6 +617,7 @@ def run_learned(args):
         "dtype": "f32 solver, bf16 network with f32 accumulation", "data": "synthetic (generated by the solver)",
         "config": {"workload": LEARNED["name"], "train_We": LEARNED["train_We"], "test_We": test_We,
                    "span_steps": [t0, t1], "pairs": int(X.shape[0]), "epochs": args.epochs, "skip": args.skip,
+                   "solve": solves[0],
                    "network": "4-level encoder-decoder, channels 32-256, 128x512 input"},
         "solver_alone": {"value": len(res) * 3600e3 / ms_solver, "unit": "cases/h"},
         "speedup_vs_solver": ms_solver / ms_ff,
@@ -618,6 +630,7 @@ def run_learned(args):
                   "generate_seconds": t_gen},
         "held_out": {"loss": val, "persistence_loss": pers},
         "per_case": [{k: v for k, v in x.items() if k != "judged"} for x in res],
+        "other_solve_counts": more,
         "judged_windows": [[{k: (round(v, 4) if v is not None else None) for k, v in j.items()} for j in x["judged"]]
                            for x in res],
     }
@@ -650,7 +663,7 @@ def run_nn(args):
     nn.load()
     cin, ch, head, H, W = 8, (32, 64, 128, 256), 8, 512, 128
     nb = args.batch
-    nn.set_conv_path(0 if args.conv_path == "tcgen05" else 1)
+    nn.set_conv_path({"tcgen05": 0, "mma.sync": 1, "auto": 2}[args.conv_path])
     net = nn.UNet(cin=cin, ch=ch, head=head)
     net.init_he(seed=7)
     g = torch.Generator(device="cuda")
@@ -697,8 +710,10 @@ def run_nn(args):
             "training_step": {"ms": ms_train, "tflops": tf_train},
             "roofline": {"bound": "tensor", "achieved": tf_inf, "peak": peak, "unit": "TFLOP/s",
                          "frac": tf_inf / peak, "traffic": None, "peak_source": kind,
-                         "kernel": ("k_conv_fwd_tc (tcgen05.mma, tensor-memory accumulator)" if args.conv_path == "tcgen05"
-                                    else "k_conv_fwd (mma.sync m16n8k16 bf16)") + " + split-K reduction"},
+                         "kernel": {"tcgen05": "k_conv_fwd_tc (tcgen05.mma, tensor-memory accumulator)",
+                                    "mma.sync": "k_conv_fwd (mma.sync m16n8k16 bf16)",
+                                    "auto": "k_conv_fwd_tc (tcgen05) for calls of >= 1,824 output tiles, else "
+                                            "k_conv_fwd (mma.sync)"}[args.conv_path] + " + split-K reduction"},
             "bounded_wait_timed_out": timed_out,
             "clocks": clk}
     print(json.dumps(line))
@@ -762,8 +777,8 @@ def main():
                          "jet, fp16 for the sweep")
     ap.add_argument("--workload", default="jet", choices=["jet", "rt2d", "sweep", "learned", "jet-sweep", "nn"])
     ap.add_argument("--batch", type=int, default=1, help="inputs per inference of the nn workload")
-    ap.add_argument("--conv-path", default="tcgen05", choices=["tcgen05", "mma.sync"],
-                    help="convolution contraction of the nn / learned workloads")
+    ap.add_argument("--conv-path", default="auto", choices=["auto", "tcgen05", "mma.sync"],
+                    help="convolution contraction of the nn / learned workloads (auto: tcgen05 for large calls)")
     ap.add_argument("--we", type=float, nargs="+", default=None,
                     help="Weber numbers of the jet-sweep workload (default: 1, 2.2, 3.5, 5, 10)")
     ap.add_argument("--layout", default="ab", choices=["ab", "inplace"],
@@ -772,6 +787,9 @@ def main():
                     help="steps between the in-step FP64 diagnostics (sum phi, finite check) of lbm_step")
     ap.add_argument("--epochs", type=int, default=24, help="training epochs of the learned workload")
     ap.add_argument("--skip", type=int, default=1, help="windows predicted after each passing check (learned)")
+    ap.add_argument("--solve", type=int, nargs="+", default=None,
+                    help="solver windows required since the last skip before the next (learned; several values: "
+                         "one training, a fast-forward run per value)")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NX", "NY", "NZ"), default=None,
                     help="reduced grid of the same jet workload (profiling captures); for rt2d NX "
                          "(a multiple of 256) and NY, NZ ignored")

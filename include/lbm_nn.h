@@ -49,12 +49,14 @@ int lbm_nn_conv_fwd(const void* x, int32_t x_stride, int32_t ci, int32_t taps, c
                     int32_t relu, int32_t nb, int32_t h, int32_t w, void* stream);
 
 /* The contraction lbm_nn_conv_fwd (and with it the backward-data pass, the
- * same call on flipped weights) runs on: 0 (default) the fifth-generation
- * tensor cores -- tcgen05.mma with the float32 accumulator in tensor memory,
- * 128-position x 32/64/128-channel tiles, operands gathered into shared
- * memory two k-tiles deep; 1 the warp-level mma.sync kernels.  Both sum in
- * float32 over bfloat16 products; they may differ in the order of the sums.
- * Process-wide; LBM_NN_ERR_ARG for other values. */
+ * same call on flipped weights) runs on: 0 the fifth-generation tensor cores
+ * -- tcgen05.mma with the float32 accumulator in tensor memory,
+ * 128-position x 32/64/128-channel tiles, operands brought into shared
+ * memory by asynchronous copies three k-tiles deep; 1 the warp-level
+ * mma.sync kernels; 2 (default) tcgen05 when the call has at least 1,824
+ * output tiles of 128 positions (four waves of three blocks per SM), else
+ * mma.sync.  All sum in float32 over bfloat16 products; they may differ in
+ * the order of the sums.  Process-wide; LBM_NN_ERR_ARG for other values. */
 int lbm_nn_set_conv_path(int32_t path);
 
 /* Whether a bounded wait of the tcgen05 convolution kernels gave up since the

@@ -246,11 +246,14 @@ def solver_twin(We, t0, t1, ref_phi, mode, eps=1e-6, every=2, seed=0, nx=512, ny
 
 
 def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, nx=512, ny=2048, stream=None,
-                 twins=False):
+                 twins=False, solve=1):
     """Run one case from t0 to t1 with the network in the loop (after a
-    passing check the next `skip` windows are predicted, one by one, instead
-    of solved), and the same case with the solver alone; returns the
-    comparison."""
+    passing check, once at least `solve` solver windows have run since the
+    last skip, the next `skip` windows are predicted, one by one, instead of
+    solved), and the same case with the solver alone; returns the
+    comparison.  Every restart from a prediction moves the state a little
+    (the coarse-graining loses detail), so fewer skips per window keep the end
+    state closer to the solver's."""
     import torch
     H, W = ny // FACTOR, nx // FACTOR
     m = H * W
@@ -281,6 +284,7 @@ def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, 
     windows = dict(solver=0, skipped=0, checked_pass=0, checked_fail=0)
     errs = []
     trusted = 0
+    since_skip = 0                  # solver windows since the last skip
     torch.cuda.synchronize()
     ev0.record(st)
     t_wall = time.perf_counter()
@@ -300,6 +304,7 @@ def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, 
             ff.t += K
             windows["skipped"] += 1
             trusted -= 1
+            since_skip = 0
             continue
         # solver window, which also judges the network's prediction of it: the
         # fields a restart from the prediction would start from, with the mass
@@ -307,6 +312,7 @@ def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, 
         # window; none before the first, which therefore cannot pass)
         ff.step(K)
         windows["solver"] += 1
+        since_skip += 1
         m1 = ff.mass()
         m_cur = m1
         target = m1 if rate is None else m0 + K * rate
@@ -319,7 +325,7 @@ def fast_forward(net, We, t0, t1, interface_bound=1.0, mass_bound=1e-4, skip=1, 
         ok = dist <= interface_bound and front <= interface_bound and merr <= mass_bound
         errs.append((dist, front, merr))
         windows["checked_pass" if ok else "checked_fail"] += 1
-        trusted = skip if ok else 0
+        trusted = skip if (ok and since_skip >= solve) else 0
     ev1.record(st)
     torch.cuda.synchronize()
     ms_ff = ev0.elapsed_time(ev1)

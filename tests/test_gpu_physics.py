@@ -97,3 +97,32 @@ def test_laplace_3d_drop(lib, report):
     assert errs.max() < 0.05
     # the error shrinks as the drop grows, like the paper's
     assert np.all(np.diff(errs) < 0.002) and errs[-1] < 0.7 * errs[0]
+
+
+def test_poiseuille_converges_to_the_fd_solution(lib, report):
+    """Layered two-phase Poiseuille flow (Sec. 5.3, rho* = 1000, mu* = 100,
+    tau_H = 0.5), refined at a fixed ratio W / ny = 1/16 and g ~ 1/ny^2: the
+    relative L2 error (eq:l2_norm_error) against a second-order FD solution of
+    eq:momentum_equation with the solver's own rho(phi), mu(phi) falls at
+    second order (the paper's slope -1.94) and reaches ~1e-3 at ny = 256.  The
+    oracle checks the same at ny = 64 and 128 (too slow beyond).  (At ny = 512
+    float32 stops the approach to the steady state: near it the per-step
+    change of u falls below its rounding, a floor that grows like ny^2 --
+    measured 2.1e-3 there.)"""
+    from test_oracle_physics import fd_poiseuille
+    errs = {}
+    for ny, steps in ((64, 40000), (128, 160000), (256, 640000)):
+        p, phi, u, ps = C.poiseuille2d(ny=ny, rho_ratio=1000.0, W=ny / 16.0, g=1e-6 * (64.0 / ny) ** 2)
+        sim = lib.LBM(p)
+        sim.init_fields(phi, u, ps)
+        sim.step(steps)
+        ph, uu, _ = sim.fields()
+        sim.close()
+        ux = uu[0, 0, :, 0].astype(np.float64)
+        ufd = fd_poiseuille(ph[0, :, 0].astype(np.float64), p)
+        errs[ny] = float(np.sqrt(((ux - ufd) ** 2).sum() / (ufd ** 2).sum()))
+    o1, o2 = (np.log2(errs[a] / errs[2 * a]) for a in (64, 128))
+    report("poiseuille_gpu", e64=errs[64], e128=errs[128], e256=errs[256], order_64_128=o1, order_128_256=o2)
+    assert errs[64] < 0.03
+    assert 1.7 < np.log2(errs[64] / errs[256]) / 2 < 2.5 and 1.7 < o1 < 2.5
+    assert errs[256] < 1.5e-3
