@@ -300,7 +300,7 @@ def run_gpu(args):
     else:
         nx, ny, nz = args.grid if args.grid else (WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"])
         p, phi, u, ps = C.jet3d(nx=nx, ny=ny, nz=nz, Rn=WORKLOAD["Rn"], We=WORKLOAD["We"])
-        Q, dim, lat, faces = 19, 3, "D3Q19", 2
+        Q, dim, lat, faces = 19, 3, "D3Q19", 1          # k_faces: inlet + outlet in one launch
         name = WORKLOAD["name"] if not args.grid else "jet3d_D3Q19_%dx%dx%d_fp32 (reduced grid)" % tuple(args.grid)
         if args.storage != "fp32":
             name = name.replace("fp32", args.storage)

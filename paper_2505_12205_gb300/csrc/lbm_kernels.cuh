@@ -1115,12 +1115,9 @@ k_step_batch(const BatchCase* __restrict__ cases, const int2* __restrict__ items
 // ones (arriving from beyond the face) sit in the node's own slots in either
 // layout.
 template <class L, class S>
-__global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* fB, typename S::T* gB, int par)
+__device__ __forceinline__ void inlet_node(const DevParams& P, typename S::T* fB, typename S::T* gB, int par, int t)
 {
     constexpr int Q = L::Q;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
-    if (t >= nface) return;
     // the node (t mod nx, t / nx) of the last-axis plane 0
     const int tx = (L::D == 2) ? t : t % P.nx, ty = (L::D == 2) ? 0 : t / P.nx;
     const uint32_t e = (L::D == 2) ? pel<L>(pnode(P, tx, 0, 0)) : pel<L>(pnode(P, tx, ty, 0));
@@ -1175,6 +1172,13 @@ __global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* fB, 
     }
 }
 
+template <class L, class S>
+__global__ void k_inlet(const __grid_constant__ DevParams P, typename S::T* fB, typename S::T* gB, int par)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ((L::D == 2) ? P.nx : P.nx * P.ny)) inlet_node<L, S>(P, fB, gB, par, t);
+}
+
 // Outlet speed of the maximum / average schemes of eq:velocity_options: the
 // bare first moment of f along the outward normal at layer N-1 after
 // streaming, reduced over the layer into *P.lam (one block).
@@ -1217,13 +1221,11 @@ __global__ void __launch_bounds__(256) k_outlet_speed(const __grid_constant__ De
 // the storage format, so both layouts blend the same values).  A/B: chi(N, t)
 // is A's layer N.
 template <class L, class S, bool INPL>
-__global__ void k_outlet(const __grid_constant__ DevParams P, const typename S::T* fA,
-                         const typename S::T* gA, typename S::T* fB, typename S::T* gB, int par)
+__device__ __forceinline__ void outlet_node(const DevParams& P, const typename S::T* fA, const typename S::T* gA,
+                                            typename S::T* fB, typename S::T* gB, int par, int t)
 {
     constexpr int Q = L::Q;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
-    if (t >= nface) return;
     const int nL = (L::D == 2) ? P.ny : P.nz;
     const int tx = (L::D == 2) ? t : t % P.nx, ty = (L::D == 2) ? 0 : t / P.nx;
     auto atN = [&](int a) { return (L::D == 2) ? post_el<L>(P, tx, nL - 1, 0, a, par) : post_el<L>(P, tx, ty, nL - 1, a, par); };
@@ -1252,6 +1254,28 @@ __global__ void k_outlet(const __grid_constant__ DevParams P, const typename S::
             P.outold[(Q + a) * nface + t] = S::g(gs, wa);
         }
     }
+}
+
+template <class L, class S, bool INPL>
+__global__ void k_outlet(const __grid_constant__ DevParams P, const typename S::T* fA, const typename S::T* gA,
+                         typename S::T* fB, typename S::T* gB, int par)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ((L::D == 2) ? P.nx : P.nx * P.ny)) outlet_node<L, S, INPL>(P, fA, gA, fB, gB, par, t);
+}
+
+// Both open-face rules in one launch (outlet with its local speed): threads
+// [0, nface) take the inlet plane, [nface, 2 nface) the outlet plane.  The
+// two touch disjoint populations (the last axis has at least 4 nodes), so
+// the result equals k_inlet followed by k_outlet.
+template <class L, class S, bool INPL>
+__global__ void k_faces(const __grid_constant__ DevParams P, const typename S::T* fA, const typename S::T* gA,
+                        typename S::T* fB, typename S::T* gB, int par)
+{
+    const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nface) inlet_node<L, S>(P, fB, gB, par, t);
+    else if (t < 2 * nface) outlet_node<L, S, INPL>(P, fA, gA, fB, gB, par, t - nface);
 }
 
 // The outlet plane of the state (decoded) into P.outold: chi(N, t) of the
@@ -1766,11 +1790,18 @@ cudaError_t Launch<L, S>::step_timed(const DevParams& P, const FusedGeom& G, int
     const int lastlo = (L::D == 2) ? P.bc[2] : P.bc[4];
     const int lasthi = (L::D == 2) ? P.bc[3] : P.bc[5];
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
-    if (lastlo == BC_INLET) k_inlet<L, S><<<(nface + 127) / 128, 128, 0, s>>>(P, fB, gB, par);
-    if (lasthi == BC_OUTFLOW) {
-        if (P.outlet_scheme) k_outlet_speed<L, S><<<1, 256, 0, s>>>(P, fB, par);
-        if (b.inplace) k_outlet<L, S, true><<<(nface + 127) / 128, 128, 0, s>>>(P, fA, gA, fB, gB, par);
-        else k_outlet<L, S, false><<<(nface + 127) / 128, 128, 0, s>>>(P, fA, gA, fB, gB, par);
+    if (lastlo == BC_INLET && lasthi == BC_OUTFLOW && !P.outlet_scheme) {
+        // the jet: both face rules in one launch
+        const unsigned nb = (2 * nface + 127) / 128;
+        if (b.inplace) k_faces<L, S, true><<<nb, 128, 0, s>>>(P, fA, gA, fB, gB, par);
+        else k_faces<L, S, false><<<nb, 128, 0, s>>>(P, fA, gA, fB, gB, par);
+    } else {
+        if (lastlo == BC_INLET) k_inlet<L, S><<<(nface + 127) / 128, 128, 0, s>>>(P, fB, gB, par);
+        if (lasthi == BC_OUTFLOW) {
+            if (P.outlet_scheme) k_outlet_speed<L, S><<<1, 256, 0, s>>>(P, fB, par);
+            if (b.inplace) k_outlet<L, S, true><<<(nface + 127) / 128, 128, 0, s>>>(P, fA, gA, fB, gB, par);
+            else k_outlet<L, S, false><<<(nface + 127) / 128, 128, 0, s>>>(P, fA, gA, fB, gB, par);
+        }
     }
     if ((e = mark()) != cudaSuccess) return e;
     return cudaGetLastError();
