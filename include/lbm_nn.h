@@ -61,7 +61,9 @@ int lbm_nn_set_conv_path(int32_t path);
 
 /* Whether a bounded wait of the tcgen05 convolution kernels gave up since the
  * last call (*timed_out = 1; the outputs of that call are not valid), then
- * clears the flag.  Synchronises the device's legacy default stream. */
+ * clears the flag.  The flag is a 4-byte device word allocated on the first
+ * convolution call on each device.  Synchronises the device's legacy default
+ * stream. */
 int lbm_nn_conv_status(int32_t* timed_out);
 
 /* Gradients of a convolution from the gradient dz of its pre-activation

@@ -2,7 +2,8 @@
 
 Float32 arithmetic on the GPU against FP64 in the oracle.  Tolerances:
   * one collision or one step from the same state: relative L2 over the
-    compared array <= 1e-5 and max |gpu - oracle| <= 5e-5 of the array's
+    compared array <= 1e-6 (3e-6 after three steps) and max |gpu - oracle|
+    <= 5e-5 of the array's
     largest magnitude.  The float32 rounding error of a term (eps = 6e-8) is
     amplified by up to rho_H / rho_L through F / rho in the light phase
     (rho_H / rho_L = 20 .. 100 in these cases), which bounds the worst cells;
@@ -43,7 +44,7 @@ def rel_l2(a, b, floor=0.0):
     return np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), floor)
 
 
-def close(a, b, l2=1e-5, mx=5e-5):
+def close(a, b, l2=1e-6, mx=5e-5):
     a = np.asarray(a, np.float64)
     scale = np.abs(b).max()
     return (np.linalg.norm(a - b) <= l2 * np.linalg.norm(b) + 1e-30
@@ -135,7 +136,7 @@ def test_one_step_from_random_state(lib, orc, report, name):
     sim.step(2)
     gf, gg = sim.populations()
     rf, rg = o.populations()
-    assert close(gg, rg, 3e-5, 1e-4) and close(gf, rf, 3e-5, 1e-4)
+    assert close(gg, rg, 3e-6, 1e-4) and close(gf, rf, 3e-6, 1e-4)
 
 
 # ---------------------------------------------------- configured workloads
@@ -235,7 +236,8 @@ def test_inlet_force_shift_matches_the_oracle(lib, orc, report, name):
         sim.step(n)
         gf, gg = sim.populations()
         rf, rg = o.populations()
-        assert close(gg, rg) and close(gf, rf), (np.abs(gf - rf).max(), np.abs(gg - rg).max())
+        report("inlet_force_%s_%d" % (name, n), f_l2=rel_l2(gf, rf), g_l2=rel_l2(gg, rg))
+        assert close(gg, rg, 3e-6) and close(gf, rf, 3e-6), (np.abs(gf - rf).max(), np.abs(gg - rg).max())
     D = 2 if lat == 0 else 3
     u = sim.fields()[1]
     ui = u[:, 0, 0, :] if lat == 0 else u[:, 0].reshape(D, -1)
