@@ -712,7 +712,7 @@ def run_nn(args):
                          "frac": tf_inf / peak, "traffic": None, "peak_source": kind,
                          "kernel": {"tcgen05": "k_conv_fwd_tc (tcgen05.mma, tensor-memory accumulator)",
                                     "mma.sync": "k_conv_fwd (mma.sync m16n8k16 bf16)",
-                                    "auto": "k_conv_fwd_tc (tcgen05) for calls of >= 1,824 output tiles, else "
+                                    "auto": "k_conv_fwd_tc (tcgen05) for calls of >= 4 GFLOP, else "
                                             "k_conv_fwd (mma.sync)"}[args.conv_path] + " + split-K reduction"},
             "bounded_wait_timed_out": timed_out,
             "clocks": clk}

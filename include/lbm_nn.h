@@ -53,9 +53,8 @@ int lbm_nn_conv_fwd(const void* x, int32_t x_stride, int32_t ci, int32_t taps, c
  * -- tcgen05.mma with the float32 accumulator in tensor memory,
  * 128-position x 32/64/128-channel tiles, operands brought into shared
  * memory by asynchronous copies three k-tiles deep; 1 the warp-level
- * mma.sync kernels; 2 (default) tcgen05 when the call has at least 1,824
- * output tiles of 128 positions (four waves of three blocks per SM), else
- * mma.sync.  All sum in float32 over bfloat16 products; they may differ in
+ * mma.sync kernels; 2 (default) tcgen05 for calls of at least 4 GFLOP
+ * (2 positions x co x taps x ci), else mma.sync.  All sum in float32 over bfloat16 products; they may differ in
  * the order of the sums.  Process-wide; LBM_NN_ERR_ARG for other values. */
 int lbm_nn_set_conv_path(int32_t path);
 

@@ -850,12 +850,13 @@ constexpr int kTargetBlocks = 2 * 152;                  // two 128-thread blocks
 constexpr int64_t kConvWsFloats = int64_t(1) << 22;     // largest split-K workspace (16 MB)
 
 // forward convolution contraction: 0 tcgen05 (tensor memory), 1 warp-level
-// mma.sync, 2 (default) by the call's size: tcgen05 when its 128-position
-// output tiles fill at least four waves of three blocks per SM (the tcgen05
-// blocks pay a fixed set-up -- tensor-memory allocation, barriers -- that a
-// single short wave does not amortise), else mma.sync
+// mma.sync, 2 (default) by the call's work: tcgen05 for calls of at least
+// 4 GFLOP (the tcgen05 blocks pay a fixed set-up -- tensor-memory allocation,
+// barriers -- that a call of a few short k loops does not amortise; measured:
+// the network's ~1.2 GFLOP layers of one input are faster on mma.sync, its
+// ~19 GFLOP layers of 16 inputs on tcgen05), else mma.sync
 int g_conv_path = 2;
-constexpr int kTcMinTiles = 4 * 3 * 152;
+constexpr double kTcMinFlop = 4e9;
 // per-device error flag of the tcgen05 kernels (a bounded wait gave up)
 int* g_tc_err[64] = {};
 
@@ -904,8 +905,8 @@ int lbm_nn_conv_fwd(const void* x, int32_t x_stride, int32_t ci, int32_t taps, c
     if (yf && yf_stride < co) return nn_fail(LBM_NN_ERR_ARG, "conv_fwd: f32 output stride below co");
     const int M = nb * h * w, K = taps * ci;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int tc_tiles = int(blocks_for(M, TC_TM)) * int(blocks_for(co, co <= 32 ? 32 : co <= 64 ? 64 : 128));
-    const bool tc = g_conv_path == 0 || (g_conv_path == 2 && tc_tiles >= kTcMinTiles);
+    const double flop = 2.0 * double(M) * double(co) * double(K);
+    const bool tc = g_conv_path == 0 || (g_conv_path == 2 && flop >= kTcMinFlop);
     // tcgen05: 128 x 32 / 64 / 128 tiles by the channel count; mma.sync:
     // 128 x 32 tiles (no idle half of a 64-wide tile) or 64 x 64
     const bool narrow = co <= 32;

@@ -78,7 +78,7 @@ def _p(t):
 
 def set_conv_path(path: int):
     """0: tcgen05 tensor-memory convolutions; 1: warp-level mma.sync; 2 (default):
-    tcgen05 for calls large enough to fill several waves, else mma.sync."""
+    tcgen05 for calls of at least 4 GFLOP, else mma.sync."""
     lib = load()
     if lib.lbm_nn_set_conv_path(int(path)) != 0:
         raise NNError(lib.lbm_nn_last_error().decode())

@@ -27,7 +27,7 @@ def run(*args):
 
 
 @pytest.mark.parametrize("args,Q,launches_per_step", [
-    (("--grid", "64", "64", "128"), 19, 3),
+    (("--grid", "64", "64", "128"), 19, 2),          # k_step_fused + k_faces
     (("--workload", "rt2d", "--grid", "512", "1024", "1"), 9, 1),
 ])
 def test_bench_line(args, Q, launches_per_step):
