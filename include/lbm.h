@@ -76,9 +76,16 @@ typedef enum {
  *               (eq:velocity_options): 0 local u(x, N-1), 1 its maximum, 2 its
  *               average over the layer N-1
  *  storage      population storage format (arithmetic is float32 always):
- *               0 = float32; 1 = float16 and 2 = bfloat16, both storing
- *               each population normalised by its weight: f as
- *               (f_a / w_a) * storage_scale, g as g_a / w_a - 1/2
+ *               0 = float32;
+ *               1 = 16-bit: f in float16 as (f_a / w_a - r_m) * storage_scale,
+ *               r_m a reference of the node's plane m along the last axis
+ *               (z in 3D, y in 2D): the plane's mean p* when lbm_init_fields
+ *               gives the state, its mean f_0 / w_0 when lbm_set_populations
+ *               gives a context its first state, kept after that; g in
+ *               16-bit fixed point, q = rint((g_a / w_a + 1/2) * 65535 / 2)
+ *               saturated to [0, 65535];
+ *               2 = bfloat16: f as (f_a / w_a) * storage_scale, g as
+ *               g_a / w_a - 1/2
  *  diag_every   steps between the in-step diagnostics of lbm_step (FP64
  *               sum of phi, finite check, Laplace pressure sums; Sec. 5.2,
  *               5.4); 0 = off
@@ -124,8 +131,8 @@ typedef struct {
     double inlet_center[2];
     double inlet_radius;
     double storage_scale;   /* power-of-two scale of f in 16-bit storage;
-                               0 = 2048 (f_a / w_a from ~3e-8 to ~30 in
-                               float16 normal range) */
+                               0 = 2048 (a deviation f_a / w_a - r_m from
+                               ~3e-8 to ~30 in float16 normal range) */
 } lbm_params;
 
 /* FP64 diagnostics of the current state (lbm_diag). */
@@ -194,7 +201,10 @@ int lbm_get_fields(lbm_ctx* ctx, float* phi, float* u, float* p, int on_device);
  * [Q][N] float32 (either may be NULL in lbm_get_populations), in the same
  * order whatever the layout.  With float32 storage lbm_set_populations
  * restores it exactly; with 16-bit storage the values are decoded to float32
- * and encoded again on restore (exact up to that rounding).  The conversion
+ * and encoded again on restore: g (storage 1: fixed point) exactly, f to
+ * within half a step of its 16-bit format (storage 1: where f_a / w_a lies
+ * within ~2^-11 of the plane reference, float16 resolves more than the
+ * float32 value carries, so a restart is not bit for bit).  The conversion
  * goes through a staging buffer of 4 N floats (allocated on first use).
  * Synchronises. */
 int lbm_get_populations(lbm_ctx* ctx, float* f, float* g, int on_device);

@@ -60,6 +60,8 @@ struct lbm_ctx {
     float* staging = nullptr;       // float32 planes of kStageSets populations for checkpoints
     float* fieldbuf = nullptr;      // in-place layout: (D + 2) N floats staging the fields
     float* outold = nullptr;        // in-place layout: outlet plane kept for the outlet rule
+    float* fref = nullptr;          // float16 storage: f reference of each plane of the march axis
+    bool ref_set = false;           // fref holds the references of the current encoding
     float* uadv = nullptr;          // prescribed velocity of lbm_advect_phase (host input copied here)
     int* ccl = nullptr;             // jet post-processing scratch: labels, sizes, lo, hi (4 N ints)
     int* ccl_list = nullptr;        // (size, lo, hi) of the components, count at the end
@@ -378,6 +380,11 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
         lbm_destroy(c);
         return r;
     }
+    if (e == cudaSuccess && p->storage == 1) {
+        const size_t nm = size_t(c->D == 2 ? p->ny : p->nz);
+        e = cudaMalloc(reinterpret_cast<void**>(&c->fref), nm * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(c->fref, 0, nm * sizeof(float));
+    }
     if (e == cudaSuccess && c->b.inplace) {
         e = cudaMalloc(reinterpret_cast<void**>(&c->fieldbuf), size_t(c->N) * (c->D + 2) * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&c->outold), 2 * size_t(c->Q) * nface * sizeof(float));
@@ -390,6 +397,7 @@ int lbm_create(const lbm_params* p, void* stream, lbm_ctx** out)
     c->diag_res = c->diag_part + c->diag_nparts;
     c->dp.phis = c->b.phi;
     c->dp.outold = c->outold;
+    c->dp.fref = c->fref;
     e = with_launch(c->D, p->storage, [&](auto l) {
         return decltype(l)::fused_geom(c->dp, &c->geom, &c->fused_blocks, c->b.inplace != 0);
     });
@@ -429,7 +437,7 @@ int lbm_destroy(lbm_ctx* c)
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     cudaFree(c->b.fA); cudaFree(c->b.gA); cudaFree(c->b.fB); cudaFree(c->b.gB);
     cudaFree(c->b.phi); cudaFree(c->face); cudaFree(c->diag_part); cudaFree(c->staging); cudaFree(c->uadv);
-    cudaFree(c->fieldbuf); cudaFree(c->outold);
+    cudaFree(c->fieldbuf); cudaFree(c->outold); cudaFree(c->fref);
     cudaFree(c->ccl); cudaFree(c->ccl_list);
     delete c;
     return LBM_OK;
@@ -507,13 +515,15 @@ int lbm_init_fields(lbm_ctx* c, const float* phi, const float* u, const float* p
         if (vphi && (!u || vu) && (!pstar || vp)) {
             c->b.par = 0;
             cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
-                cudaError_t r = decltype(l)::init(c->dp, vphi, vu, vp, c->b.fA, c->b.gA, c->stream);
+                cudaError_t r = c->fref ? decltype(l)::plane_ref(c->dp, vp, 1.0f, c->fref, c->stream) : cudaSuccess;
+                if (r == cudaSuccess) r = decltype(l)::init(c->dp, vphi, vu, vp, c->b.fA, c->b.gA, c->stream);
                 if (r == cudaSuccess && c->b.inplace) r = decltype(l)::save_outlet(c->dp, c->b, c->stream);
                 return r;
             });
             if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
             LBM_CUDA(c, cudaStreamSynchronize(c->stream));
             c->initialised = true;
+            c->ref_set = true;
             c->step_count = 0;
             return LBM_OK;
         }
@@ -530,14 +540,16 @@ int lbm_init_fields(lbm_ctx* c, const float* phi, const float* u, const float* p
     if (pstar) LBM_CUDA(c, cudaMemcpyAsync(s_p, pstar, nb, kind, c->stream));
     c->b.par = 0;                           // the equilibria are written in the natural layout
     cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
-        cudaError_t r = decltype(l)::init(c->dp, s_phi, u ? s_u : nullptr, pstar ? s_p : nullptr, c->b.fA, c->b.gA,
-                                          c->stream);
+        const float* vp = pstar ? s_p : nullptr;
+        cudaError_t r = c->fref ? decltype(l)::plane_ref(c->dp, vp, 1.0f, c->fref, c->stream) : cudaSuccess;
+        if (r == cudaSuccess) r = decltype(l)::init(c->dp, s_phi, u ? s_u : nullptr, vp, c->b.fA, c->b.gA, c->stream);
         if (r == cudaSuccess && c->b.inplace) r = decltype(l)::save_outlet(c->dp, c->b, c->stream);
         return r;
     });
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     if (!on_device) LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = true;
+    c->ref_set = true;
     c->step_count = 0;
     return LBM_OK;
 }
@@ -658,8 +670,15 @@ int lbm_set_populations(lbm_ctx* c, const float* f, const float* g, int on_devic
             const int a1 = std::min(c->Q, a0 + kStagePops);
             LBM_CUDA(c, cudaMemcpyAsync(c->staging, ins[set] + size_t(a0) * c->N,
                                         size_t(a1 - a0) * c->N * sizeof(float), kind, c->stream));
+            // a context without a state takes the f references from this
+            // state (mean f_0 / w_0 of each plane); one with a state keeps
+            // its own, so that restoring a state it wrote is exact
+            const bool take_ref = c->fref && !c->ref_set && set == 0 && a0 == 0;
             cudaError_t e = with_launch(c->D, c->p.storage, [&](auto l) {
-                return decltype(l)::pack(c->dp, c->staging, set, a0, a1, dst[set], c->stream);
+                cudaError_t r = cudaSuccess;
+                if (take_ref) r = decltype(l)::plane_ref(c->dp, c->staging, c->D == 2 ? 2.25f : 3.0f, c->fref, c->stream);
+                if (r == cudaSuccess) r = decltype(l)::pack(c->dp, c->staging, set, a0, a1, dst[set], c->stream);
+                return r;
             });
             if (e != cudaSuccess) return cuda_fail(c, e, "pack kernel");
         }
@@ -672,6 +691,7 @@ int lbm_set_populations(lbm_ctx* c, const float* f, const float* g, int on_devic
     }
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->initialised = true;
+    c->ref_set = true;
     c->step_count = 0;
     return LBM_OK;
 }

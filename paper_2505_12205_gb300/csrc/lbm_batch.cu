@@ -88,6 +88,7 @@ struct lbm_batch {
     int64_t total_nodes = 0, max_nodes = 0;
     void *fA = nullptr, *gA = nullptr, *fB = nullptr, *gB = nullptr;   // A = current state
     float* phi = nullptr;                  // scratch of the largest case
+    float* fref = nullptr;                 // float16 storage: f references of every case's planes
     DiagPartial* part = nullptr;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -259,7 +260,7 @@ int lbm_batch_destroy(lbm_batch* b)
     }
     if (b->fork) cudaEventDestroy(b->fork);
     cudaFree(b->fA); cudaFree(b->gA); cudaFree(b->fB); cudaFree(b->gB);
-    cudaFree(b->phi); cudaFree(b->part); cudaFree(b->counters);
+    cudaFree(b->phi); cudaFree(b->part); cudaFree(b->counters); cudaFree(b->fref);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;
     return LBM_OK;
@@ -330,6 +331,19 @@ int lbm_batch_create(const lbm_params* params, int32_t ncases, void* stream, lbm
     if ((e = cudaMalloc(reinterpret_cast<void**>(&b->phi), size_t(b->max_nodes) * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(reinterpret_cast<void**>(&b->part), (kDiagParts + 1) * sizeof(DiagPartial))) != cudaSuccess)
         return give_up(bcuda(b, e, "cudaMalloc"));
+    if (b->storage == 1) {
+        // one reference per plane of the march axis per case, zero until the
+        // case is initialised
+        size_t nref = 0;
+        for (int c = 0; c < ncases; ++c) nref += size_t(b->D == 2 ? params[c].ny : params[c].nz);
+        if ((e = cudaMalloc(reinterpret_cast<void**>(&b->fref), nref * sizeof(float))) != cudaSuccess ||
+            (e = cudaMemset(b->fref, 0, nref * sizeof(float))) != cudaSuccess)
+            return give_up(bcuda(b, e, "cudaMalloc(references)"));
+        for (int c = 0, o = 0; c < ncases; ++c) {
+            b->dp[c].fref = b->fref + o;
+            o += b->D == 2 ? params[c].ny : params[c].nz;
+        }
+    }
     if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess)
         return give_up(bcuda(b, e, "event"));
 
@@ -390,7 +404,12 @@ int lbm_batch_init_fields(lbm_batch* b, int32_t c, const float* phi, const float
     if (u) BATCH_CUDA(b, cudaMemcpyAsync(s_u, u, nb * b->D, kind, b->stream));
     if (pstar) BATCH_CUDA(b, cudaMemcpyAsync(s_p, pstar, nb, kind, b->stream));
     cudaError_t e = with_launch(b->D, b->storage, [&](auto l) {
-        return decltype(l)::init(b->dp[c], s_phi, u ? s_u : nullptr, pstar ? s_p : nullptr, bu.fA, bu.gA, b->stream);
+        const float* vp = pstar ? s_p : nullptr;
+        cudaError_t r = b->fref ? decltype(l)::plane_ref(b->dp[c], vp, 1.0f, const_cast<float*>(b->dp[c].fref),
+                                                         b->stream)
+                                : cudaSuccess;
+        if (r == cudaSuccess) r = decltype(l)::init(b->dp[c], s_phi, u ? s_u : nullptr, vp, bu.fA, bu.gA, b->stream);
+        return r;
     });
     if (e != cudaSuccess) return bcuda(b, e, "init kernel");
     if (!on_device) BATCH_CUDA(b, cudaStreamSynchronize(b->stream));

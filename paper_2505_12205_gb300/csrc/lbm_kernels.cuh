@@ -42,6 +42,9 @@ struct DevParams {
     float omega_phi;       // 1 / (tau_phi + 1/2), tau_phi = M / c_s^2
     float gx, gy, gz, rho_ref;
     float fscale, inv_fscale;   // power-of-two scale of f in 16-bit storage
+    // 16-bit storage: reference of f_a / w_a of each plane of the march axis
+    // (z in 3D, y in 2D), one float per plane
+    const float* fref;
     // inlet plane profile (face arrays, precomputed in double on the device)
     const float* phi_in;
     const float* u_in;
@@ -96,38 +99,90 @@ __device__ __forceinline__ int64_t pop_stride(const DevParams& P)
 // ---------------------------------------------------------- storage formats
 //
 // Arithmetic is float32 throughout; the populations may be stored in 16 bits
-// to halve the bytes a step moves.  16-bit formats store each population
-// normalised by its weight: f as (f_a / w_a) * fscale (fscale a power of two,
-// so f_a / w_a = p* + O(u) keeps its relative precision over a wide range),
-// and g as g_a / w_a - 1/2 (in [-1/2, 1/2] up to O(u) overshoot).
+// to halve the bytes a step moves.  Each 16-bit value is normalised by the
+// population's weight w_a so that one format covers every direction.
+//  - f (float16): f_a / w_a = p* + O(u) is stored as its deviation from a
+//    reference r of the node's plane along the march axis (z in 3D, y in 2D),
+//    (f_a / w_a - r) * fscale, fscale a power of two.  The reference (the
+//    plane's mean p* when the context is given its state) removes the
+//    hydrostatic part of p*, so the 11-bit mantissa resolves the velocity
+//    moments instead of the pressure head.
+//  - g (16-bit fixed point, float16 container): g_a / w_a lies in [-1/2, 3/2]
+//    (phi in [0, 1] plus O(u) and interface terms) and is stored as the
+//    unsigned integer q = rint((g_a / w_a + 1/2) * 65535 / 2), saturated to
+//    [0, 65535]: a uniform step of 3.05e-5 in both bulk phases and across the
+//    interface, where float16 resolves only near one value.
+// Every conversion uses explicitly rounded operations (no contraction into a
+// neighbouring multiply-add), so that every kernel that stores or loads a
+// population rounds it the same way.  The format's kRef says whether f takes
+// the plane reference; formats without it ignore the argument.
 struct StoreF32 {
     using T = float;
-    __device__ static float f(T v, float, const DevParams&) { return v; }
+    static constexpr bool kRef = false;
+    __device__ static float f(T v, float, float, const DevParams&) { return v; }
     __device__ static float g(T v, float) { return v; }
-    __device__ static T ef(float v, float, const DevParams&) { return v; }
+    __device__ static T ef(float v, float, float, const DevParams&) { return v; }
     __device__ static T eg(float v, float) { return v; }
 };
 
-// The conversions use explicitly rounded operations (no contraction into a
-// neighbouring multiply-add), so that every kernel that stores or loads a
-// population rounds it the same way.  g is decoded as one fma: h + 1/2 is
-// exact in float32 for every 16-bit h and w/2 is exact, so
-// fma(w, h, w/2) = round(w (h + 1/2)).
+// g fixed point: step 2 / 65535 of g / w.  Decoding is one integer-to-float
+// conversion (exact) and one fma whose constants are w * step (one rounding,
+// the same in every kernel) and w / 2 (exact), so it is correctly rounded
+// with respect to them.  Encoding maps g / w onto [0, 1] with a saturating
+// fma and rounds to the integer with the 1.5 * 2^23 addend: the low 16 bits
+// of the sum are q.  Saturation stores a NaN g as q = 0; a diverging state
+// still shows in f (float16 keeps NaN and infinity), which the finite checks
+// read.
+constexpr float kGStep = 2.0f / 65535.0f;
+
 struct StoreF16 {
     using T = __half;
-    __device__ static float f(T v, float wa, const DevParams& P) { return __fmul_rn(__half2float(v), wa * P.inv_fscale); }
-    __device__ static float g(T v, float wa) { return __fmaf_rn(wa, __half2float(v), 0.5f * wa); }
-    __device__ static T ef(float v, float wa, const DevParams& P) { return __float2half_rn(__fmul_rn(v, P.fscale / wa)); }
-    __device__ static T eg(float v, float wa) { return __float2half_rn(__fmaf_rn(v, 1.0f / wa, -0.5f)); }
+    static constexpr bool kRef = true;
+    __device__ static float f(T v, float wa, float r, const DevParams& P)
+    {
+        return __fmaf_rn(__half2float(v), __fmul_rn(wa, P.inv_fscale), __fmul_rn(wa, r));
+    }
+    __device__ static T ef(float v, float wa, float r, const DevParams& P)
+    {
+        return __float2half_rn(__fmaf_rn(v, P.fscale / wa, -__fmul_rn(r, P.fscale)));
+    }
+    __device__ static float g(T v, float wa)
+    {
+        return __fmaf_rn(__uint2float_rn(unsigned(__half_as_ushort(v))), __fmul_rn(wa, kGStep), -0.5f * wa);
+    }
+    __device__ static T eg(float v, float wa)
+    {
+        const float s = __saturatef(__fmaf_rn(v, 0.5f / wa, 0.25f));
+        const float t = __fmaf_rn(s, 65535.0f, 12582912.0f);
+        return __ushort_as_half((unsigned short)(__float_as_uint(t) & 0xffffu));
+    }
 };
 
+// bfloat16 (8-bit mantissa): f as (f_a / w_a) * fscale, g as g_a / w_a - 1/2,
+// no plane reference.  Too coarse for the high-density-ratio cases; kept as
+// the plain 16-bit float format.
 struct StoreBF16 {
     using T = __nv_bfloat16;
-    __device__ static float f(T v, float wa, const DevParams& P) { return __fmul_rn(__bfloat162float(v), wa * P.inv_fscale); }
+    static constexpr bool kRef = false;
+    __device__ static float f(T v, float wa, float, const DevParams& P) { return __fmul_rn(__bfloat162float(v), wa * P.inv_fscale); }
     __device__ static float g(T v, float wa) { return __fmaf_rn(wa, __bfloat162float(v), 0.5f * wa); }
-    __device__ static T ef(float v, float wa, const DevParams& P) { return __float2bfloat16_rn(__fmul_rn(v, P.fscale / wa)); }
+    __device__ static T ef(float v, float wa, float, const DevParams& P) { return __float2bfloat16_rn(__fmul_rn(v, P.fscale / wa)); }
     __device__ static T eg(float v, float wa) { return __float2bfloat16_rn(__fmaf_rn(v, 1.0f / wa, -0.5f)); }
 };
+
+// Coordinate along the march axis (z in 3D, y in 2D) and the f reference of
+// that plane for the format S (0 for formats without one).
+template <class L>
+__device__ __forceinline__ int march(int y, int z)
+{
+    return (L::D == 3) ? z : y;
+}
+template <class S>
+__device__ __forceinline__ float fref(const DevParams& P, int m)
+{
+    if constexpr (S::kRef) return __ldg(P.fref + m);
+    else return 0.0f;
+}
 
 // ------------------------------------------------------------ node physics
 
@@ -267,8 +322,10 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
         if (L::opp(a) < a) continue;
         const int c = wclass<L>(a);
         const float va = pa(a), vb = pa(L::opp(a));
-        const float dp = va - vb;
-        lps[c] += fmaf(-2.0f, phi, va + vb);            // (phi_a - phi) + (phi_abar - phi)
+        // va + vb and va - vb in one packed fma (fma(vb, +-1, va) rounds as the add does)
+        const float2 sd = __ffma2_rn(make_float2(vb, vb), make_float2(1.0f, -1.0f), make_float2(va, va));
+        const float dp = sd.y;
+        lps[c] += fmaf(-2.0f, phi, sd.x);               // (phi_a - phi) + (phi_abar - phi)
         if (L::ex(a)) gxs[c] = L::ex(a) > 0 ? gxs[c] + dp : gxs[c] - dp;
         if (L::ey(a)) gys[c] = L::ey(a) > 0 ? gys[c] + dp : gys[c] - dp;
         if (L::ez(a)) gzs[c] = L::ez(a) > 0 ? gzs[c] + dp : gzs[c] - dp;
@@ -304,7 +361,9 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
         for (int a = 1; a < Q; ++a) {
             if (L::opp(a) < a) continue;
             const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-            const float s = fv[a] + fv[L::opp(a)], d = fv[a] - fv[L::opp(a)];
+            const float2 sd = __ffma2_rn(make_float2(fv[L::opp(a)], fv[L::opp(a)]), make_float2(1.0f, -1.0f),
+                                         make_float2(fv[a], fv[a]));
+            const float s = sd.x, d = sd.y;
             pstar += s;
             if (ex) jx = ex > 0 ? jx + d : jx - d;
             if (ey) jy = ey > 0 ? jy + d : jy - d;
@@ -422,30 +481,34 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
             const int b = L::opp(a);
             const bool diag = wclass<L>(a) == 2;
             const float W = diag ? W2 : W1;
+            // a and its opposite b in the two lanes of packed float32
+            // operations (each lane rounds as the scalar operation does):
+            // the odd parts of b are those of a negated, so each pair takes
+            // one packed operation where the scalar form takes two
             const float eu = edot<L>(a, ux, uy, uz);
             const float even = fmaf((4.5f * W) * eu, eu, diag ? uw2 : uw1);
-            const float da = fmaf(3.0f * W, eu, even), db = fmaf(-3.0f * W, eu, even);
-            const float fph = edot<L>(a, nx, ny, nz) * (diag ? kw2 : kw1);
-            const float hf = edot<L>(a, frx, fry, frz) * W;
+            const float2 d2 = __ffma2_rn(make_float2(eu, eu), make_float2(3.0f * W, -3.0f * W),
+                                         make_float2(even, even));                     // da, db
+            const float kw = diag ? kw2 : kw1;
+            const float en = edot<L>(a, nx, ny, nz), ef = edot<L>(a, frx, fry, frz);
+            const float2 fph2 = __fmul2_rn(make_float2(en, en), make_float2(kw, -kw));   // +-F^phi (1 - w/2)
+            const float2 hf2 = __fmul2_rn(make_float2(ef, ef), make_float2(W, -W));      // +-F_a / 2
             float proj = -0.0f;
 #pragma unroll
             for (int k = 0; k < L::NS; ++k)
                 if (L::m(k, a)) proj = fmaf(L::rw(k, a), ck[k], proj);
             const float phw = diag ? phw2 : phw1, pw = diag ? pw2 : pw1;
-            {
-                const float geq = fmaf(phi, da, phw);
-                const float feq = pw + da;
-                sg += geq;
-                sf += feq;
-                emit(a, feq + (proj + hf), fmaf(om1, ga(a), fmaf(om, geq, fph)));
-            }
-            {
-                const float geq = fmaf(phi, db, phw);
-                const float feq = pw + db;
-                sg += geq;
-                sf += feq;
-                emit(b, feq + (proj - hf), fmaf(om1, ga(b), fmaf(om, geq, -fph)));
-            }
+            const float2 geq2 = __ffma2_rn(make_float2(phi, phi), d2, make_float2(phw, phw));
+            const float2 feq2 = __fadd2_rn(make_float2(pw, pw), d2);
+            sg += geq2.x;
+            sf += feq2.x;
+            sg += geq2.y;
+            sf += feq2.y;
+            const float2 fo2 = __fadd2_rn(feq2, __fadd2_rn(make_float2(proj, proj), hf2));
+            const float2 gi2 = __ffma2_rn(make_float2(om, om), geq2, fph2);
+            const float2 go2 = __ffma2_rn(make_float2(om1, om1), make_float2(ga(a), ga(b)), gi2);
+            emit(a, fo2.x, go2.x);
+            emit(b, fo2.y, go2.y);
         }
         emit(0, pstar - sf, fmaf(om1, ga(0), om * (phi - sg)));
     }
@@ -520,7 +583,10 @@ __device__ __forceinline__ float phi_ghost(const DevParams& P, const float* __re
 // rules overwrite it); across free-slip faces, the tangential neighbour's
 // mirrored population (eq:free_slip_f/g).  par = 1 marks the swapped state.
 
-// Element holding the post-streaming population a of node (x, y, z).
+// Element holding the post-streaming population a of node (x, y, z).  In
+// 16-bit storage the value there is encoded with the f reference of the
+// plane of (x, y, z), the node it belongs to after streaming, whichever
+// node's slot holds it.
 template <class L>
 __device__ __forceinline__ uint32_t post_el(const DevParams& P, int x, int y, int z, int a, int par)
 {
@@ -737,6 +803,7 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
     struct PushMap {
         uint32_t o[3][2];
         uint32_t wall, slip[3], off;
+        float r[3];             // f references of the planes mm - 1, mm, mm + 1 (wrapped)
     };
     auto push_map = [&](int mm) {
         PushMap M;
@@ -765,6 +832,14 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
         M.o[d][0] = uint32_t(sm) * nstep * uint32_t(Q);
         M.o[d][1] = uint32_t(sp) * nstep * uint32_t(Q);
         M.off = M.wall | M.slip[0] | M.slip[1] | M.slip[2];
+        if constexpr (S::kRef) {
+            // a push across a non-periodic face stays in plane mm
+            M.r[1] = fref<S>(P, mm);
+            M.r[0] = (mm > 0 || lo == BC_PERIODIC) ? fref<S>(P, mm + sm) : M.r[1];
+            M.r[2] = (mm < nm - 1 || hi == BC_PERIODIC) ? fref<S>(P, mm + sp) : M.r[1];
+        } else {
+            M.r[0] = M.r[1] = M.r[2] = 0.0f;
+        }
         return M;
     };
     // Element that the push of direction a from the node at element e0 writes
@@ -789,6 +864,18 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
         if (L::ey(a) && !(m & 2)) t += M.o[1][L::ey(a) > 0];
         if (L::D == 3 && L::ez(a) && !(m & 4)) t += M.o[2][L::ez(a) > 0];
         return t + 32u * mirrored<L>(a, m);
+    };
+    // f reference of the node that the push of direction a reaches (the
+    // element target / plain_target writes belongs to it after streaming):
+    // the plane one step along the march component of a, or this node's
+    // plane where a wall, an open face or a free-slip face of the march axis
+    // keeps the push in it.
+    auto plain_ref = [&](const PushMap& M, int a) -> float {
+        return M.r[1 + ((L::D == 3) ? L::ez(a) : L::ey(a))];
+    };
+    auto face_ref = [&](const PushMap& M, int a) -> float {
+        if ((M.wall | M.slip[L::D - 1]) & (1u << a)) return M.r[1];
+        return plain_ref(M, a);
     };
 
     // phi of plane mm over the extended tile into window slot wslot; the
@@ -890,10 +977,14 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
             };
             if constexpr (MODE == STEP_EVEN) {
                 // in place: own slots in, own opposite slots out
-                auto fa = [&](int a) { return S::f(__ldg(fA + e0 + 32 * a), L::w(a), P); };
+                // the value written into slot abar is the post-streaming
+                // population a of the node the A/B push of a reaches, and is
+                // encoded with the reference of that node's plane
+                const PushMap M = push_map(m);
+                auto fa = [&](int a) { return S::f(__ldg(fA + e0 + 32 * a), L::w(a), M.r[1], P); };
                 auto swap = [&](int a, float fs, float gs) {
                     const float wa = L::w(a);           // w of a and of its opposite
-                    fB[e0 + 32 * L::opp(a)] = S::ef(fs, wa, P);
+                    fB[e0 + 32 * L::opp(a)] = S::ef(fs, wa, face_ref(M, a), P);
                     gB[e0 + 32 * L::opp(a)] = S::eg(gs, wa);
                 };
                 node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, swap);
@@ -904,23 +995,25 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
                 // offset, with no per-direction test (+2 % float32, +15 %
                 // float16 throughput); the two cases are separate copies of
                 // the node update
-                auto step = [&](auto tgt) {
+                auto step = [&](auto tgt, auto tref) {
                     auto push = [&](int a, float fs, float gs) {
                         const float wa = L::w(a);
                         const uint32_t t = tgt(M, e0, a);
-                        fB[t] = S::ef(fs, wa, P);
+                        fB[t] = S::ef(fs, wa, tref(M, a), P);
                         gB[t] = S::eg(gs, wa);
                     };
                     if constexpr (MODE == STEP_AB) {
-                        auto fa = [&](int a) { return S::f(__ldg(fA + e0 + 32 * a), L::w(a), P); };
+                        auto fa = [&](int a) { return S::f(__ldg(fA + e0 + 32 * a), L::w(a), M.r[1], P); };
                         node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, push);
                     } else {
-                        auto fa = [&](int a) { return S::f(__ldg(fA + tgt(M, e0, L::opp(a))), L::w(a), P); };
+                        // population a sits where the push of its opposite
+                        // writes, encoded with this node's plane reference
+                        auto fa = [&](int a) { return S::f(__ldg(fA + tgt(M, e0, L::opp(a))), L::w(a), M.r[1], P); };
                         node_update<L, true>(P, fa, ga, pa, inlet_node, nullptr, push);
                     }
                 };
-                if (__all_sync(__activemask(), M.off == 0u)) step(plain_target);
-                else step(target);
+                if (__all_sync(__activemask(), M.off == 0u)) step(plain_target, plain_ref);
+                else step(target, face_ref);
             }
         }
         __syncthreads();
@@ -1124,6 +1217,7 @@ __device__ __forceinline__ void inlet_node(const DevParams& P, typename S::T* fB
     typename S::T* fn = fB + e;
     typename S::T* gn = gB + e;
     auto src = [&](int a) { return (L::D == 2) ? post_el<L>(P, tx, 0, 0, a, par) : post_el<L>(P, tx, ty, 0, a, par); };
+    const float r0 = fref<S>(P, 0);     // the node's plane
     const float phin = P.phi_in[t], un = P.u_in[t];
     const float ux = 0.0f, uy = (L::D == 2) ? un : 0.0f, uz = (L::D == 3) ? un : 0.0f;
     const float uu = un * un;
@@ -1136,8 +1230,9 @@ __device__ __forceinline__ void inlet_node(const DevParams& P, typename S::T* fB
     float f[Q], g[Q];
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        f[a] = S::f(fB[src(a)], L::w(a), P);
-        g[a] = S::g(gB[src(a)], L::w(a));
+        const uint32_t e = src(a);
+        f[a] = S::f(fB[e], L::w(a), r0, P);
+        g[a] = S::g(gB[e], L::w(a));
     }
     float Mx = 0.0f, My = 0.0f, theta = 0.0f;
     int ndiag = 0;
@@ -1165,7 +1260,7 @@ __device__ __forceinline__ void inlet_node(const DevParams& P, typename S::T* fB
         const float da = gdev<L>(a, ux, uy, uz, uu), db = gdev<L>(ab, ux, uy, uz, uu);
         const float eM = float(t0) * Mx + float(t1) * My;
         // eq:velocity_boundary_distribution on f' = f + F/2, shifted back
-        fn[32 * a] = S::ef(((f[ab] + half(ab)) + (da - db) - 0.5f * eM) - half(a), L::w(a), P);
+        fn[32 * a] = S::ef(((f[ab] + half(ab)) + (da - db) - 0.5f * eM) - half(a), L::w(a), r0, P);
         const float corr = (t0 != 0 || t1 != 0) ? th_n : 0.0f;
         // eq:unknown_distribution_*: g_a = geq_a - (g_abar - geq_abar) - corr, w_a = w_abar
         gn[32 * a] = S::eg(phin * (2.0f * L::w(a) + da + db) - g[ab] - corr, L::w(a));
@@ -1190,6 +1285,7 @@ __global__ void __launch_bounds__(256) k_outlet_speed(const __grid_constant__ De
     const int nface = (L::D == 2) ? P.nx : P.nx * P.ny;
     const int nL = (L::D == 2) ? P.ny : P.nz;
     float acc = P.outlet_scheme == 1 ? -3.0e38f : 0.0f;
+    const float rM = fref<S>(P, nL - 2);
     for (int t = threadIdx.x; t < nface; t += blockDim.x) {
         const int tx = (L::D == 2) ? t : t % P.nx, ty = (L::D == 2) ? 0 : t / P.nx;
         float U = 0.0f;
@@ -1197,7 +1293,7 @@ __global__ void __launch_bounds__(256) k_outlet_speed(const __grid_constant__ De
         for (int a = 0; a < L::Q; ++a) {
             const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
             const uint32_t iM = (L::D == 2) ? post_el<L>(P, tx, nL - 2, 0, a, par) : post_el<L>(P, tx, ty, nL - 2, a, par);
-            if (en) U += float(en) * S::f(fB[iM], L::w(a), P);
+            if (en) U += float(en) * S::f(fB[iM], L::w(a), rM, P);
         }
         acc = P.outlet_scheme == 1 ? fmaxf(acc, U) : acc + U;
     }
@@ -1230,11 +1326,12 @@ __device__ __forceinline__ void outlet_node(const DevParams& P, const typename S
     const int tx = (L::D == 2) ? t : t % P.nx, ty = (L::D == 2) ? 0 : t / P.nx;
     auto atN = [&](int a) { return (L::D == 2) ? post_el<L>(P, tx, nL - 1, 0, a, par) : post_el<L>(P, tx, ty, nL - 1, a, par); };
     auto atM = [&](int a) { return (L::D == 2) ? post_el<L>(P, tx, nL - 2, 0, a, par) : post_el<L>(P, tx, ty, nL - 2, a, par); };
+    const float rN = fref<S>(P, nL - 1), rM = fref<S>(P, nL - 2);     // planes of the two layers
     float U = 0.0f;
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const int en = (L::D == 2) ? L::ey(a) : L::ez(a);
-        if (en) U += float(en) * S::f(fB[atM(a)], L::w(a), P);
+        if (en) U += float(en) * S::f(fB[atM(a)], L::w(a), rM, P);
     }
     const float lam = fminf(fmaxf(P.outlet_scheme ? *P.lam : U, 0.0f), 1.0f);
     const float inv = 1.0f / (1.0f + lam);
@@ -1242,15 +1339,15 @@ __device__ __forceinline__ void outlet_node(const DevParams& P, const typename S
     for (int a = 0; a < Q; ++a) {
         const float wa = L::w(a);
         const uint32_t iN = atN(a), iM = atM(a);
-        const float fo = INPL ? P.outold[a * nface + t] : S::f(fA[iN], wa, P);
+        const float fo = INPL ? P.outold[a * nface + t] : S::f(fA[iN], wa, rN, P);
         const float go = INPL ? P.outold[(Q + a) * nface + t] : S::g(gA[iN], wa);
-        const float fm = S::f(fB[iM], wa, P), gm = S::g(gB[iM], wa);
-        const typename S::T fs = S::ef((fo + lam * fm) * inv, wa, P);
+        const float fm = S::f(fB[iM], wa, rM, P), gm = S::g(gB[iM], wa);
+        const typename S::T fs = S::ef((fo + lam * fm) * inv, wa, rN, P);
         const typename S::T gs = S::eg((go + lam * gm) * inv, wa);
         fB[iN] = fs;
         gB[iN] = gs;
         if (INPL) {
-            P.outold[a * nface + t] = S::f(fs, wa, P);
+            P.outold[a * nface + t] = S::f(fs, wa, rN, P);
             P.outold[(Q + a) * nface + t] = S::g(gs, wa);
         }
     }
@@ -1293,7 +1390,7 @@ __global__ void k_save_outlet(const __grid_constant__ DevParams P, const typenam
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const uint32_t iN = (L::D == 2) ? post_el<L>(P, tx, nL - 1, 0, a, par) : post_el<L>(P, tx, ty, nL - 1, a, par);
-        P.outold[a * nface + t] = S::f(f[iN], L::w(a), P);
+        P.outold[a * nface + t] = S::f(f[iN], L::w(a), fref<S>(P, nL - 1), P);
         P.outold[(Q + a) * nface + t] = S::g(g[iN], L::w(a));
     }
 }
@@ -1317,6 +1414,29 @@ __global__ void k_inlet_profile(int nface, int nx, double cx, double cy, double 
     u_in[t] = float(r < R ? uj : 0.0);
 }
 
+// Mean of scale * X over each plane m of the march axis into ref[m] (one
+// block per plane; each thread sums its strided share in double in node
+// order and the block adds the shares in a fixed tree, so the result depends
+// only on X).  The plane of node i is i / (nodes per plane) in either
+// dimension (z planes of nx ny nodes in 3D, y rows of nx nodes in 2D).
+template <class L>
+__global__ void __launch_bounds__(256) k_plane_ref(const __grid_constant__ DevParams P, const float* __restrict__ X,
+                                                   float scale, float* __restrict__ ref)
+{
+    __shared__ double red[256];
+    const int64_t plane = (L::D == 3) ? int64_t(P.nx) * P.ny : int64_t(P.nx);
+    const float* xp = X + int64_t(blockIdx.x) * plane;
+    double acc = 0.0;
+    for (int64_t k = threadIdx.x; k < plane; k += 256) acc += double(xp[k]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ref[blockIdx.x] = float(double(scale) * red[0] / double(plane));
+}
+
 // Equilibrium initialisation from float32 fields (eq:equilibrium,
 // eq:equilibrium_function).
 template <class L, class S>
@@ -1333,10 +1453,11 @@ __global__ void k_init(const __grid_constant__ DevParams P, const float* __restr
     equilibria<L>(ph, ps, ux, uy, uz, geq, feq);
     const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
     const uint32_t e = pel<L>(pnode(P, x, y, z));
+    const float r = fref<S>(P, march<L>(y, z));
 #pragma unroll
     for (int a = 0; a < L::Q; ++a) {
         g[e + 32 * a] = S::eg(geq[a], L::w(a));
-        f[e + 32 * a] = S::ef(feq[a], L::w(a), P);
+        f[e + 32 * a] = S::ef(feq[a], L::w(a), r, P);
     }
 }
 
@@ -1358,7 +1479,7 @@ __global__ void __launch_bounds__(128) k_fields(const __grid_constant__ DevParam
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const uint32_t e = post_el<L>(P, x, y, z, a, par);
-        f[a] = S::f(fA[e], L::w(a), P);
+        f[a] = S::f(fA[e], L::w(a), fref<S>(P, march<L>(y, z)), P);
         g[a] = S::g(gA[e], L::w(a));
     }
     gather_phi<L>(P, phi, x, y, z, phin);
@@ -1561,7 +1682,7 @@ __global__ void __launch_bounds__(256) k_diag(const __grid_constant__ DevParams 
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             const int64_t e = (!PLANAR && par) ? int64_t(post_el<L>(P, x, y, z, a, 1)) : b + a * st;
-            f[a] = S::f(fA[e], L::w(a), P);
+            f[a] = S::f(fA[e], L::w(a), fref<S>(P, march<L>(y, z)), P);
             g[a] = S::g(gA[e], L::w(a));
             if (!isfinite(f[a]) || !isfinite(g[a])) bad = 1;
         }
@@ -1683,6 +1804,9 @@ struct Launch {
                                      const float* phin, float* fs, float* gs, float* out, cudaStream_t s);
     // phi = sum_a g_a of the state in A into b.phi (unpadded node order)
     static cudaError_t phi(const DevParams& P, const Buffers& b, cudaStream_t s);
+    // f references of 16-bit storage: ref[m] = scale * (mean of X over plane m
+    // of the march axis), X float32 in the unpadded node order (NULL: 0)
+    static cudaError_t plane_ref(const DevParams& P, const float* X, float scale, float* ref, cudaStream_t s);
     // one step of the phase field alone in the velocity scale * uf (g: A -> B)
     static cudaError_t advect(const DevParams& P, const Buffers& b, const float* uf, float scale, cudaStream_t s);
 };
@@ -1872,7 +1996,7 @@ __global__ void k_unpack(const __grid_constant__ DevParams P, const typename S::
     const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
     for (int a = a0; a < a1; ++a) {
         const uint32_t e = post_el<L>(P, x, y, z, a, par);
-        out[(a - a0) * P.N + i] = gset ? S::g(src[e], L::w(a)) : S::f(src[e], L::w(a), P);
+        out[(a - a0) * P.N + i] = gset ? S::g(src[e], L::w(a)) : S::f(src[e], L::w(a), fref<S>(P, march<L>(y, z)), P);
     }
 }
 
@@ -1886,9 +2010,10 @@ __global__ void k_pack(const __grid_constant__ DevParams P, const float* __restr
     if (i >= P.N) return;
     const int x = int(i % P.nx), y = int((i / P.nx) % P.ny), z = int(i / (int64_t(P.nx) * P.ny));
     const uint32_t e = pel<L>(pnode(P, x, y, z));
+    const float r = gset ? 0.0f : fref<S>(P, march<L>(y, z));
     for (int a = a0; a < a1; ++a) {
         const float v = in[(a - a0) * P.N + i];
-        dst[e + 32 * a] = gset ? S::eg(v, L::w(a)) : S::ef(v, L::w(a), P);
+        dst[e + 32 * a] = gset ? S::eg(v, L::w(a)) : S::ef(v, L::w(a), r, P);
     }
 }
 
@@ -1922,6 +2047,15 @@ template <class L, class S>
 cudaError_t Launch<L, S>::phi(const DevParams& P, const Buffers& b, cudaStream_t s)
 {
     k_phi<L, S, false><<<unsigned((P.N + 127) / 128), 128, 0, s>>>(P, static_cast<const T*>(b.gA), b.par, b.phi);
+    return cudaGetLastError();
+}
+
+template <class L, class S>
+cudaError_t Launch<L, S>::plane_ref(const DevParams& P, const float* X, float scale, float* ref, cudaStream_t s)
+{
+    const int nm = (L::D == 3) ? P.nz : P.ny;
+    if (!X) return cudaMemsetAsync(ref, 0, sizeof(float) * size_t(nm), s);
+    k_plane_ref<L><<<unsigned(nm), 256, 0, s>>>(P, X, scale, ref);
     return cudaGetLastError();
 }
 

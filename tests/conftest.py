@@ -34,3 +34,21 @@ def report():
             with open(path, "a") as f:
                 f.write(json.dumps({"test": name, **{k: float(v) for k, v in values.items()}}) + "\n")
     return rec
+
+
+@pytest.fixture(scope="session")
+def oracle_fields(oracle_mod):
+    """Fields (phi, u, p) of the FP64 oracle after `steps` steps of a case,
+    computed once per session: the parity tests of the float32 and the 16-bit
+    storage formats compare against the same oracle runs."""
+    cache = {}
+
+    def run(key, case, steps):
+        if (key, steps) not in cache:
+            p, phi, u, ps = case
+            o = oracle_mod.Oracle(p)
+            o.init_fields(phi, u, ps)
+            o.step(steps)
+            cache[(key, steps)] = o.fields()
+        return cache[(key, steps)]
+    return run

@@ -174,7 +174,7 @@ def test_drop2d_128_parity_1000_steps(lib, orc, report):
     assert abs(d1["sum_phi"] - r_phi.sum()) / r_phi.sum() < 2e-6
 
 
-def test_rt2d_parity_full_size(lib, orc, report):
+def test_rt2d_parity_full_size(lib, oracle_fields, report):
     """256 x 1024 Rayleigh-Taylor (At = 0.5, Re = 3000, W = 5, at rest in
     hydrostatic balance), relative L2 after 1000 steps.  Float32 storage alone
     limits this case to about the stated 1e-5: the oracle with its state
@@ -188,16 +188,13 @@ def test_rt2d_parity_full_size(lib, orc, report):
     sim.init_fields(phi, u, ps)
     sim.step(1000)
     g_phi, g_u, _ = sim.fields()
-    o = orc.Oracle(p)
-    o.init_fields(phi, u, ps)
-    o.step(1000)
-    r_phi, r_u, _ = o.fields()
+    r_phi, r_u, _ = oracle_fields("rt2d", (p, phi, u, ps), 1000)
     report("rt2d_1000", phi_l2=rel_l2(g_phi, r_phi), u_l2=rel_l2(g_u, r_u))
     assert rel_l2(g_phi, r_phi) <= 2e-5
     assert rel_l2(g_u, r_u) <= 3e-5
 
 
-def test_jet3d_quarter_scale_parity_500_steps(lib, orc, report):
+def test_jet3d_quarter_scale_parity_500_steps(lib, oracle_fields, report):
     """The 3D jet at a quarter of the 256 x 256 x 1024 workload's size
     (64 x 64 x 256, nozzle radius 4, same faces and physics), 500 steps:
     relative L2 of phi and u <= 1e-5."""
@@ -206,10 +203,7 @@ def test_jet3d_quarter_scale_parity_500_steps(lib, orc, report):
     sim.init_fields(phi, u, ps)
     sim.step(500)
     g_phi, g_u, _ = sim.fields()
-    o = orc.Oracle(p)
-    o.init_fields(phi, u, ps)
-    o.step(500)
-    r_phi, r_u, _ = o.fields()
+    r_phi, r_u, _ = oracle_fields("jet3d_quarter", (p, phi, u, ps), 500)
     report("jet3d_quarter_500", phi_l2=rel_l2(g_phi, r_phi), u_l2=rel_l2(g_u, r_u))
     assert rel_l2(g_phi, r_phi) <= 1e-5
     assert rel_l2(g_u, r_u) <= 1e-5
