@@ -307,13 +307,17 @@ def run_gpu(args):
         kname = "k_step_fused<D3Q19,32,6> (phi + collide + push-stream, one pass)"
         extra = {"We": WORKLOAD["We"]}
     p["storage"] = {"fp32": 0, "fp16": 1, "bf16": 2}[args.storage]
+    if args.storage != "fp32":
+        # 16-bit storage: the A/B step holds two x-adjacent nodes per thread
+        kname = (("k_step_fused2<D2Q9,64,1> (phi + collide + push-stream, one pass, two nodes per thread)") if rt else
+                 ("k_step_fused2<D3Q19,64,4> (phi + collide + push-stream, one pass, two nodes per thread)"))
     inplace = args.layout == "inplace"
     p["layout"] = 1 if inplace else 0
     p["diag_every"] = args.diag_every
     if inplace:
         name += " (in-place layout)"
-        kname = kname.replace("k_step_fused", "k_step_inplace").replace(
-            "(phi + collide + push-stream, one pass)", "(collide + in-place stream, even/odd forms; phi by a pre-pass)")
+        kname = ("k_step_inplace<D2Q9,64,1>" if rt else "k_step_inplace<D3Q19,32,6>") + \
+            " (collide + in-place stream, even/odd forms; phi by a pre-pass)"
     elem = 4 if args.storage == "fp32" else 2
     N = p["nx"] * p["ny"] * p["nz"]
     stream = torch.cuda.current_stream()

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <type_traits>
 
 #include "lbm_lattice.cuh"
 
@@ -116,13 +117,24 @@ __device__ __forceinline__ int64_t pop_stride(const DevParams& P)
 // neighbouring multiply-add), so that every kernel that stores or loads a
 // population rounds it the same way.  The format's kRef says whether f takes
 // the plane reference; formats without it ignore the argument.
+//
+// T2 holds the values of two x-adjacent nodes (x even), one aligned 2-element
+// access; f2 / g2 / ef2 / eg2 convert both, each lane exactly as the scalar
+// conversion does, and lo / hi take one node's value out of a pair.
 struct StoreF32 {
     using T = float;
+    using T2 = float2;
     static constexpr bool kRef = false;
     __device__ static float f(T v, float, float, const DevParams&) { return v; }
     __device__ static float g(T v, float) { return v; }
     __device__ static T ef(float v, float, float, const DevParams&) { return v; }
     __device__ static T eg(float v, float) { return v; }
+    __device__ static float2 f2(T2 v, float, float, const DevParams&) { return v; }
+    __device__ static float2 g2(T2 v, float) { return v; }
+    __device__ static T2 ef2(float2 v, float, float, const DevParams&) { return v; }
+    __device__ static T2 eg2(float2 v, float) { return v; }
+    __device__ static T lo(T2 v) { return v.x; }
+    __device__ static T hi(T2 v) { return v.y; }
 };
 
 // g fixed point: step 2 / 65535 of g / w.  Decoding is one integer-to-float
@@ -156,6 +168,39 @@ struct StoreF16 {
         const float t = __fmaf_rn(s, 65535.0f, 12582912.0f);
         return __ushort_as_half((unsigned short)(__float_as_uint(t) & 0xffffu));
     }
+    using T2 = __half2;
+    __device__ static float2 f2(T2 v, float wa, float r, const DevParams& P)
+    {
+        const float c = __fmul_rn(wa, P.inv_fscale), o = __fmul_rn(wa, r);
+        return __ffma2_rn(__half22float2(v), make_float2(c, c), make_float2(o, o));
+    }
+    __device__ static T2 ef2(float2 v, float wa, float r, const DevParams& P)
+    {
+        const float c = P.fscale / wa, o = -__fmul_rn(r, P.fscale);
+        const float2 t = __ffma2_rn(v, make_float2(c, c), make_float2(o, o));
+        return __floats2half2_rn(t.x, t.y);
+    }
+    __device__ static float2 g2(T2 v, float wa)
+    {
+        const unsigned u = bits(v);
+        const float c = __fmul_rn(wa, kGStep), o = -0.5f * wa;
+        return __ffma2_rn(make_float2(__uint2float_rn(u & 0xffffu), __uint2float_rn(u >> 16)), make_float2(c, c),
+                          make_float2(o, o));
+    }
+    __device__ static T2 eg2(float2 v, float wa)
+    {
+        const float k = 0.5f / wa;
+        const float2 s = make_float2(__saturatef(__fmaf_rn(v.x, k, 0.25f)), __saturatef(__fmaf_rn(v.y, k, 0.25f)));
+        const float2 t = __ffma2_rn(s, make_float2(65535.0f, 65535.0f), make_float2(12582912.0f, 12582912.0f));
+        const unsigned u = __byte_perm(__float_as_uint(t.x), __float_as_uint(t.y), 0x5410);
+        return __halves2half2(__ushort_as_half((unsigned short)(u & 0xffffu)), __ushort_as_half((unsigned short)(u >> 16)));
+    }
+    __device__ static T lo(T2 v) { return __low2half(v); }
+    __device__ static T hi(T2 v) { return __high2half(v); }
+    __device__ static unsigned bits(T2 v)
+    {
+        return unsigned(__half_as_ushort(__low2half(v))) | (unsigned(__half_as_ushort(__high2half(v))) << 16);
+    }
 };
 
 // bfloat16 (8-bit mantissa): f as (f_a / w_a) * fscale, g as g_a / w_a - 1/2,
@@ -167,6 +212,19 @@ struct StoreBF16 {
     __device__ static float f(T v, float wa, float, const DevParams& P) { return __fmul_rn(__bfloat162float(v), wa * P.inv_fscale); }
     __device__ static float g(T v, float wa) { return __fmaf_rn(wa, __bfloat162float(v), 0.5f * wa); }
     __device__ static T ef(float v, float wa, float, const DevParams& P) { return __float2bfloat16_rn(__fmul_rn(v, P.fscale / wa)); }
+    using T2 = __nv_bfloat162;
+    __device__ static float2 f2(T2 v, float wa, float r, const DevParams& P)
+    {
+        return make_float2(f(__low2bfloat16(v), wa, r, P), f(__high2bfloat16(v), wa, r, P));
+    }
+    __device__ static float2 g2(T2 v, float wa) { return make_float2(g(__low2bfloat16(v), wa), g(__high2bfloat16(v), wa)); }
+    __device__ static T2 ef2(float2 v, float wa, float r, const DevParams& P)
+    {
+        return __halves2bfloat162(ef(v.x, wa, r, P), ef(v.y, wa, r, P));
+    }
+    __device__ static T2 eg2(float2 v, float wa) { return __halves2bfloat162(eg(v.x, wa), eg(v.y, wa)); }
+    __device__ static T lo(T2 v) { return __low2bfloat16(v); }
+    __device__ static T hi(T2 v) { return __high2bfloat16(v); }
     __device__ static T eg(float v, float wa) { return __float2bfloat16_rn(__fmaf_rn(v, 1.0f / wa, -0.5f)); }
 };
 
@@ -288,9 +346,58 @@ __device__ __forceinline__ float edot(int a, float vx, float vy, float vz)
     return s;
 }
 
-// Macroscopic update and collision of one node, written as a stream over
-// the populations so that no per-population output array has to live in
-// registers:
+// Arithmetic on the values of one node (V = float) or of two nodes held in
+// the two lanes of packed float32 instructions (V = float2).  Every lane
+// rounds as the scalar operation does (round to nearest, no contraction:
+// a - b as fma(b, -1, a) is the same rounding as the subtraction), so a
+// node's result has the same bits in either form.
+template <class V>
+struct Lanes;
+template <>
+struct Lanes<float> {
+    static __device__ __forceinline__ float s(float a) { return a; }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float neg(float a) { return -a; }
+    static __device__ __forceinline__ float rcp(float a) { return 1.0f / a; }
+    static __device__ __forceinline__ float clamp01(float a) { return fminf(fmaxf(a, 0.0f), 1.0f); }
+    template <class F>
+    static __device__ __forceinline__ float map2(float a, float b, F f) { return f(a, b); }
+};
+template <>
+struct Lanes<float2> {
+    static __device__ __forceinline__ float2 s(float a) { return make_float2(a, a); }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+    static __device__ __forceinline__ float2 rcp(float2 a) { return make_float2(1.0f / a.x, 1.0f / a.y); }
+    static __device__ __forceinline__ float2 clamp01(float2 a)
+    {
+        return make_float2(fminf(fmaxf(a.x, 0.0f), 1.0f), fminf(fmaxf(a.y, 0.0f), 1.0f));
+    }
+    template <class F>
+    static __device__ __forceinline__ float2 map2(float2 a, float2 b, F f) { return make_float2(f(a.x, b.x), f(a.y, b.y)); }
+};
+
+// e_a . v in the lanes of V
+template <class L, class V>
+__device__ __forceinline__ V edot_v(int a, V vx, V vy, V vz)
+{
+    using O = Lanes<V>;
+    V s = O::s(-0.0f);
+    if (L::ex(a)) s = L::ex(a) > 0 ? O::add(s, vx) : O::sub(s, vx);
+    if (L::ey(a)) s = L::ey(a) > 0 ? O::add(s, vy) : O::sub(s, vy);
+    if (L::ez(a)) s = L::ez(a) > 0 ? O::add(s, vz) : O::sub(s, vz);
+    return s;
+}
+
+// Macroscopic update and collision of one node (V = float) or of two nodes
+// (V = float2, one per lane), written as a stream over the populations so
+// that no per-population output array has to live in registers:
 //   fa(a)   -> f_a,  ga(a) -> g_a   (post-streaming populations)
 //   pa(a)   -> phi(x + e_a)          (stencil values; pa(0) = phi(x), the
 //                                     node's own sum_a g_a)
@@ -301,90 +408,102 @@ __device__ __forceinline__ float edot(int a, float vx, float vy, float vz)
 // inlet_node: the node lies on the inlet face, where derivatives of phi are
 // not evaluated (the inlet is single phase in the paper's treatment), so the
 // interfacial forces vanish there.  out (may be null): phi, u_x, u_y, u_z, p.
-template <class L, bool collide, class FA, class GA, class PA, class EM>
+template <class T>
+struct NoDeduce {
+    using type = T;
+};
+template <class L, bool collide, class V = float, class FA, class GA, class PA, class EM>
 __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA pa, bool inlet_node,
-                                            float* out, EM emit)
+                                            typename NoDeduce<V>::type* out, EM emit)
 {
+    using O = Lanes<V>;
     constexpr int Q = L::Q;
     constexpr float W1 = L::w(1);                       // axis weight
     constexpr float W2 = L::w(Q - 1);                   // diagonal weight
     static_assert(wclass<L>(1) == 1 && wclass<L>(Q - 1) == 2, "direction order");
     static_assert(rest_is_stress_free<L>(), "the rest population carries no stress moment");
 
-    const float phi = pa(0);                            // eq:phase_field_variable
+    const V phi = pa(0);                                // eq:phase_field_variable
 
     // eq:gradient_phi, eq:laplacian_phi over opposite pairs, per weight class
     // (c / (c_s^2 dx) = 3, 2 c^2 / (c_s^2 dx^2) = 6)
-    float gxs[3] = {-0.0f, -0.0f, -0.0f}, gys[3] = {-0.0f, -0.0f, -0.0f}, gzs[3] = {-0.0f, -0.0f, -0.0f};
-    float lps[3] = {-0.0f, -0.0f, -0.0f};
+    V gxs[3] = {O::s(-0.0f), O::s(-0.0f), O::s(-0.0f)}, gys[3] = {O::s(-0.0f), O::s(-0.0f), O::s(-0.0f)};
+    V gzs[3] = {O::s(-0.0f), O::s(-0.0f), O::s(-0.0f)}, lps[3] = {O::s(-0.0f), O::s(-0.0f), O::s(-0.0f)};
 #pragma unroll
     for (int a = 1; a < Q; ++a) {
         if (L::opp(a) < a) continue;
         const int c = wclass<L>(a);
-        const float va = pa(a), vb = pa(L::opp(a));
-        // va + vb and va - vb in one packed fma (fma(vb, +-1, va) rounds as the add does)
-        const float2 sd = __ffma2_rn(make_float2(vb, vb), make_float2(1.0f, -1.0f), make_float2(va, va));
-        const float dp = sd.y;
-        lps[c] += fmaf(-2.0f, phi, sd.x);               // (phi_a - phi) + (phi_abar - phi)
-        if (L::ex(a)) gxs[c] = L::ex(a) > 0 ? gxs[c] + dp : gxs[c] - dp;
-        if (L::ey(a)) gys[c] = L::ey(a) > 0 ? gys[c] + dp : gys[c] - dp;
-        if (L::ez(a)) gzs[c] = L::ez(a) > 0 ? gzs[c] + dp : gzs[c] - dp;
+        const V va = pa(a), vb = pa(L::opp(a));
+        const V dp = O::sub(va, vb);
+        lps[c] = O::add(lps[c], O::fma(O::s(-2.0f), phi, O::add(va, vb)));   // (phi_a - phi) + (phi_abar - phi)
+        if (L::ex(a)) gxs[c] = L::ex(a) > 0 ? O::add(gxs[c], dp) : O::sub(gxs[c], dp);
+        if (L::ey(a)) gys[c] = L::ey(a) > 0 ? O::add(gys[c], dp) : O::sub(gys[c], dp);
+        if (L::ez(a)) gzs[c] = L::ez(a) > 0 ? O::add(gzs[c], dp) : O::sub(gzs[c], dp);
     }
-    float dx = fmaf(3.0f * W2, gxs[2], (3.0f * W1) * gxs[1]);
-    float dy = fmaf(3.0f * W2, gys[2], (3.0f * W1) * gys[1]);
-    float dz = (L::D == 2) ? 0.0f : fmaf(3.0f * W2, gzs[2], (3.0f * W1) * gzs[1]);
-    float lap = fmaf(6.0f * W2, lps[2], (6.0f * W1) * lps[1]);
-    if (inlet_node) dx = dy = dz = lap = 0.0f;
+    V dx = O::fma(O::s(3.0f * W2), gxs[2], O::mul(O::s(3.0f * W1), gxs[1]));
+    V dy = O::fma(O::s(3.0f * W2), gys[2], O::mul(O::s(3.0f * W1), gys[1]));
+    V dz = (L::D == 2) ? O::s(0.0f) : O::fma(O::s(3.0f * W2), gzs[2], O::mul(O::s(3.0f * W1), gzs[1]));
+    V lap = O::fma(O::s(6.0f * W2), lps[2], O::mul(O::s(6.0f * W1), lps[1]));
+    if (inlet_node) dx = dy = dz = lap = O::s(0.0f);
 
     // phi clamped inside the material properties only
-    const float ph = fminf(fmaxf(phi, 0.0f), 1.0f);
-    const float rho = fmaf(ph, P.rho_H - P.rho_L, P.rho_L);      // eq:density_interpolation
-    const float inv_rho = 1.0f / rho;
-    float tau;
-    if (P.visc_model == 1) tau = fmaf(ph, P.tau_H - P.tau_L, P.tau_L);   // eq:relaxation_time
-    else tau = fmaf(ph, P.mu_H - P.mu_L, P.mu_L) * (3.0f * inv_rho);   // eq:dynamic_viscosity, nu = c_s^2 tau
-    const float s_nu = 1.0f / (tau + 0.5f);
+    const V ph = O::clamp01(phi);
+    const V rho = O::fma(ph, O::s(P.rho_H - P.rho_L), O::s(P.rho_L));   // eq:density_interpolation
+    const V inv_rho = O::rcp(rho);
+    // Every product that feeds a sum is written as an explicit fma: the
+    // compiler fuses a packed multiply into a following packed add whatever
+    // the contraction setting, so with V = float2 a separate product and sum
+    // would round differently from V = float.
+    V tau, tau_h;                                       // tau, tau + 1/2
+    if (P.visc_model == 1) {
+        tau = O::fma(ph, O::s(P.tau_H - P.tau_L), O::s(P.tau_L));   // eq:relaxation_time
+        tau_h = O::add(tau, O::s(0.5f));
+    } else {
+        const V mu = O::fma(ph, O::s(P.mu_H - P.mu_L), O::s(P.mu_L)), c3 = O::mul(O::s(3.0f), inv_rho);
+        tau = O::mul(mu, c3);                                       // eq:dynamic_viscosity, nu = c_s^2 tau
+        tau_h = O::fma(mu, c3, O::s(0.5f));
+    }
+    const V s_nu = O::rcp(tau_h);
 
     // chemical potential (sign reading: 4 beta (phi - phi_L)(phi - phi_H)(phi - phi_0))
-    const float mu_phi = fmaf(-P.kappa, lap, 4.0f * P.beta * phi * (phi - 1.0f) * (phi - 0.5f));
+    const V mu_phi = O::fma(O::s(-P.kappa), lap,
+                            O::mul(O::mul(O::mul(O::s(4.0f * P.beta), phi), O::sub(phi, O::s(1.0f))),
+                                   O::sub(phi, O::s(0.5f))));
 
     // zeroth, first and second moments of f (eq:normalized_pressure) from
     // the pair sums s = f_a + f_abar and differences d = f_a - f_abar
-    float pstar, jx = -0.0f, jy = -0.0f, jz = -0.0f;
-    float sxx = -0.0f, syy = -0.0f, szz = -0.0f, sxy = -0.0f, sxz = -0.0f, syz = -0.0f;
+    V pstar, jx = O::s(-0.0f), jy = O::s(-0.0f), jz = O::s(-0.0f);
+    V sxx = O::s(-0.0f), syy = O::s(-0.0f), szz = O::s(-0.0f), sxy = O::s(-0.0f), sxz = O::s(-0.0f),
+      syz = O::s(-0.0f);
     {
-        float fv[Q];
-#pragma unroll
-        for (int a = 0; a < Q; ++a) fv[a] = fa(a);
-        pstar = fv[0];
+        pstar = fa(0);
 #pragma unroll
         for (int a = 1; a < Q; ++a) {
             if (L::opp(a) < a) continue;
             const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-            const float2 sd = __ffma2_rn(make_float2(fv[L::opp(a)], fv[L::opp(a)]), make_float2(1.0f, -1.0f),
-                                         make_float2(fv[a], fv[a]));
-            const float s = sd.x, d = sd.y;
-            pstar += s;
-            if (ex) jx = ex > 0 ? jx + d : jx - d;
-            if (ey) jy = ey > 0 ? jy + d : jy - d;
-            if (ez) jz = ez > 0 ? jz + d : jz - d;
-            if (ex) sxx += s;
-            if (ey) syy += s;
-            if (ez) szz += s;
-            if (ex * ey) sxy = ex * ey > 0 ? sxy + s : sxy - s;
-            if (ex * ez) sxz = ex * ez > 0 ? sxz + s : sxz - s;
-            if (ey * ez) syz = ey * ez > 0 ? syz + s : syz - s;
+            const V va = fa(a), vb = fa(L::opp(a));
+            const V s = O::add(va, vb), d = O::sub(va, vb);
+            pstar = O::add(pstar, s);
+            if (ex) jx = ex > 0 ? O::add(jx, d) : O::sub(jx, d);
+            if (ey) jy = ey > 0 ? O::add(jy, d) : O::sub(jy, d);
+            if (ez) jz = ez > 0 ? O::add(jz, d) : O::sub(jz, d);
+            if (ex) sxx = O::add(sxx, s);
+            if (ey) syy = O::add(syy, s);
+            if (ez) szz = O::add(szz, s);
+            if (ex * ey) sxy = ex * ey > 0 ? O::add(sxy, s) : O::sub(sxy, s);
+            if (ex * ez) sxz = ex * ez > 0 ? O::add(sxz, s) : O::sub(sxz, s);
+            if (ey * ez) syz = ey * ez > 0 ? O::add(syz, s) : O::sub(syz, s);
         }
     }
     const float drho = P.rho_H - P.rho_L;                     // eq:density_gradient_phase_field
-    const float rx = drho * dx, ry = drho * dy, rz = drho * dz;
-    const float cp = -pstar * (1.0f / 3.0f);                  // eq:pressure_force
-    const float fb = rho - P.rho_ref;                          // eq:gravity_force
-    float Fx = fmaf(fb, P.gx, fmaf(cp, rx, mu_phi * dx));      // F_s + F_p + F_b
-    float Fy = fmaf(fb, P.gy, fmaf(cp, ry, mu_phi * dy));
-    float Fz = (L::D == 2) ? 0.0f : fmaf(fb, P.gz, fmaf(cp, rz, mu_phi * dz));
-    const float h_rho = 0.5f * inv_rho;
-    const float p3 = pstar * (1.0f / 3.0f);
+    const V rx = O::mul(O::s(drho), dx), ry = O::mul(O::s(drho), dy), rz = O::mul(O::s(drho), dz);
+    const V cp = O::mul(O::neg(pstar), O::s(1.0f / 3.0f));  // eq:pressure_force
+    const V fb = O::sub(rho, O::s(P.rho_ref));              // eq:gravity_force
+    V Fx = O::fma(fb, O::s(P.gx), O::fma(cp, rx, O::mul(mu_phi, dx)));   // F_s + F_p + F_b
+    V Fy = O::fma(fb, O::s(P.gy), O::fma(cp, ry, O::mul(mu_phi, dy)));
+    V Fz = (L::D == 2) ? O::s(0.0f) : O::fma(fb, O::s(P.gz), O::fma(cp, rz, O::mul(mu_phi, dz)));
+    const V h_rho = O::mul(O::s(0.5f), inv_rho);
+    auto less_p3 = [&](V sd) { return O::fma(pstar, O::s(-1.0f / 3.0f), sd); };   // Pi_dd - p* c_s^2
 
     // Viscous force, eq:viscous_force_wmrt, with the predictor velocity u0.
     // Second moments of M^-1 S M (f - feq(u0)): the non-equilibrium stress
@@ -393,68 +512,70 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
     // at s_nu and the trace at 1, so the relaxed stress is
     // s_nu D + (1 - s_nu) tr(D) / dim I.
     {
-        const float u0x = fmaf(Fx, h_rho, jx), u0y = fmaf(Fy, h_rho, jy);
-        const float u0z = (L::D == 2) ? 0.0f : fmaf(Fz, h_rho, jz);
-        const float dxx = fmaf(-u0x, u0x, sxx - p3), dyy = fmaf(-u0y, u0y, syy - p3);
-        const float dzz = (L::D == 2) ? 0.0f : fmaf(-u0z, u0z, szz - p3);
-        const float dxy = fmaf(-u0x, u0y, sxy);
-        const float iso = (1.0f - s_nu) * (dxx + dyy + dzz) * (1.0f / float(L::D));
-        const float txx = fmaf(s_nu, dxx, iso), tyy = fmaf(s_nu, dyy, iso);
-        const float txy = s_nu * dxy;
+        const V u0x = O::fma(Fx, h_rho, jx), u0y = O::fma(Fy, h_rho, jy);
+        const V u0z = (L::D == 2) ? O::s(0.0f) : O::fma(Fz, h_rho, jz);
+        const V dxx = O::fma(O::neg(u0x), u0x, less_p3(sxx)), dyy = O::fma(O::neg(u0y), u0y, less_p3(syy));
+        const V dzz = (L::D == 2) ? O::s(0.0f) : O::fma(O::neg(u0z), u0z, less_p3(szz));
+        const V dxy = O::fma(O::neg(u0x), u0y, sxy);
+        const V iso = O::mul(O::mul(O::sub(O::s(1.0f), s_nu), O::add(O::add(dxx, dyy), dzz)), O::s(1.0f / float(L::D)));
+        const V txx = O::fma(s_nu, dxx, iso), tyy = O::fma(s_nu, dyy, iso);
+        const V txy = O::mul(s_nu, dxy);
         // nu / c_s^2 = tau
         if constexpr (L::D == 2) {
-            Fx = fmaf(-tau, fmaf(txy, ry, txx * rx), Fx);
-            Fy = fmaf(-tau, fmaf(tyy, ry, txy * rx), Fy);
+            Fx = O::fma(O::neg(tau), O::fma(txy, ry, O::mul(txx, rx)), Fx);
+            Fy = O::fma(O::neg(tau), O::fma(tyy, ry, O::mul(txy, rx)), Fy);
         } else {
-            const float dxz = fmaf(-u0x, u0z, sxz), dyz = fmaf(-u0y, u0z, syz);
-            const float tzz = fmaf(s_nu, dzz, iso), txz = s_nu * dxz, tyz = s_nu * dyz;
-            Fx = fmaf(-tau, fmaf(txz, rz, fmaf(txy, ry, txx * rx)), Fx);
-            Fy = fmaf(-tau, fmaf(tyz, rz, fmaf(tyy, ry, txy * rx)), Fy);
-            Fz = fmaf(-tau, fmaf(tzz, rz, fmaf(tyz, ry, txz * rx)), Fz);
+            const V dxz = O::fma(O::neg(u0x), u0z, sxz), dyz = O::fma(O::neg(u0y), u0z, syz);
+            const V tzz = O::fma(s_nu, dzz, iso), txz = O::mul(s_nu, dxz), tyz = O::mul(s_nu, dyz);
+            Fx = O::fma(O::neg(tau), O::fma(txz, rz, O::fma(txy, ry, O::mul(txx, rx))), Fx);
+            Fy = O::fma(O::neg(tau), O::fma(tyz, rz, O::fma(tyy, ry, O::mul(txy, rx))), Fy);
+            Fz = O::fma(O::neg(tau), O::fma(tzz, rz, O::fma(tyz, ry, O::mul(txz, rx))), Fz);
         }
     }
 
     // eq:velocity_update
-    const float ux = fmaf(Fx, h_rho, jx), uy = fmaf(Fy, h_rho, jy);
-    const float uz = (L::D == 2) ? 0.0f : fmaf(Fz, h_rho, jz);
+    const V ux = O::fma(Fx, h_rho, jx), uy = O::fma(Fy, h_rho, jy);
+    const V uz = (L::D == 2) ? O::s(0.0f) : O::fma(Fz, h_rho, jz);
 
     if (out) {
         out[0] = phi;
         out[1] = ux;
         out[2] = uy;
         out[3] = uz;
-        out[4] = pstar * rho * (1.0f / 3.0f);
+        out[4] = O::mul(O::mul(pstar, rho), O::s(1.0f / 3.0f));
     }
     if constexpr (!collide) {
         return;
     } else {
-        const float uu = fmaf(uz, uz, fmaf(uy, uy, ux * ux));
+        const V uu = O::fma(uz, uz, O::fma(uy, uy, O::mul(ux, ux)));
 
         // g forcing: eq:forcing_term, n = 0 where |grad phi| < 1e-12
-        const float gn2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float hp = phi - 0.5f;
-        const float amp = (gn2 >= 1e-24f) ? fmaf(-4.0f * hp, hp, 1.0f) * P.inv_W * rsqrtf(gn2) : 0.0f;
-        const float nx = amp * dx, ny = amp * dy, nz = amp * dz;
+        const V gn2 = O::fma(dz, dz, O::fma(dy, dy, O::mul(dx, dx)));
+        const V hp = O::sub(phi, O::s(0.5f));
+        const float inv_W = P.inv_W;
+        const V amp = O::map2(gn2, hp, [inv_W](float g2, float h) {
+            return (g2 >= 1e-24f) ? __fmul_rn(__fmul_rn(__fmaf_rn(-4.0f * h, h, 1.0f), inv_W), rsqrtf(g2)) : 0.0f;
+        });
 
         // f: eq:force_term, eq:equilibrium_modified, eq:mrt_collision with
         // M^-1 S M = I - (1 - s_nu) P:
         //   f* = f - M^-1 S M (f - feq + F/2) + F = feq + F/2 + (1 - s_nu) P (f - feq + F/2).
         // The stress-row moments of f - feq + F/2 are combinations of the
         // non-equilibrium stress E = Pi(f) - p* c_s^2 I - u u (F/2 has none).
-        const float exx = fmaf(-ux, ux, sxx - p3), eyy = fmaf(-uy, uy, syy - p3);
-        const float ezz = (L::D == 2) ? 0.0f : fmaf(-uz, uz, szz - p3);
-        const float exy = fmaf(-ux, uy, sxy), exz = fmaf(-ux, uz, sxz), eyz = fmaf(-uy, uz, syz);
-        float ck[L::NS];
-        const float r = 1.0f - s_nu;
+        const V exx = O::fma(O::neg(ux), ux, less_p3(sxx)), eyy = O::fma(O::neg(uy), uy, less_p3(syy));
+        const V ezz = (L::D == 2) ? O::s(0.0f) : O::fma(O::neg(uz), uz, less_p3(szz));
+        const V exy = O::fma(O::neg(ux), uy, sxy), exz = O::fma(O::neg(ux), uz, sxz), eyz = O::fma(O::neg(uy), uz, syz);
+        V ck[L::NS];
+        const V r = O::sub(O::s(1.0f), s_nu);
         if constexpr (L::D == 2) {
-            ck[0] = r * (exx - eyy);                        // p_xx row of eq:A1
-            ck[1] = r * exy;                                // p_xy row
+            ck[0] = O::mul(r, O::sub(exx, eyy));             // p_xx row of eq:A1
+            ck[1] = O::mul(r, exy);                          // p_xy row
         } else {
-            ck[0] = r * exy;                                // rows 5-9 of eq:A2
-            ck[1] = r * eyz;
-            ck[2] = r * exz;
-            ck[3] = r * (fmaf(2.0f, exx, -eyy) - ezz);
-            ck[4] = r * (eyy - ezz);
+            ck[0] = O::mul(r, exy);                          // rows 5-9 of eq:A2
+            ck[1] = O::mul(r, eyz);
+            ck[2] = O::mul(r, exz);
+            ck[3] = O::mul(r, O::sub(O::fma(O::s(2.0f), exx, O::neg(eyy)), ezz));
+            ck[4] = O::mul(r, O::sub(eyy, ezz));
         }
 
         // g: eq:equilibrium_with_force, eq:lbe_interface,
@@ -469,48 +590,44 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
         // sum_a feq_a = p* hold to the rounding of one sum: float32 weights do
         // not add up to exactly 1, and without this every collision would
         // create or destroy mass.
-        const float phw1 = phi * W1, phw2 = phi * W2, pw1 = pstar * W1, pw2 = pstar * W2;
-        const float uw1 = (-1.5f * W1) * uu, uw2 = (-1.5f * W2) * uu;
+        const V phw1 = O::mul(phi, O::s(W1)), phw2 = O::mul(phi, O::s(W2));
+        const V uw1 = O::mul(O::s(-1.5f * W1), uu), uw2 = O::mul(O::s(-1.5f * W2), uu);
         const float kw1 = kph * W1, kw2 = kph * W2;
-        const float fr = 1.5f * inv_rho;                    // F_a / 2 = 1.5 w_a e_a . F / rho
-        const float frx = Fx * fr, fry = Fy * fr, frz = Fz * fr;
-        float sg = -0.0f, sf = -0.0f;
+        const V fr = O::mul(O::s(1.5f), inv_rho);          // F_a / 2 = 1.5 w_a e_a . F / rho
+        V sg = O::s(-0.0f), sf = O::s(-0.0f);
 #pragma unroll
         for (int a = 1; a < Q; ++a) {
             if (L::opp(a) < a) continue;
             const int b = L::opp(a);
             const bool diag = wclass<L>(a) == 2;
             const float W = diag ? W2 : W1;
-            // a and its opposite b in the two lanes of packed float32
-            // operations (each lane rounds as the scalar operation does):
-            // the odd parts of b are those of a negated, so each pair takes
-            // one packed operation where the scalar form takes two
-            const float eu = edot<L>(a, ux, uy, uz);
-            const float even = fmaf((4.5f * W) * eu, eu, diag ? uw2 : uw1);
-            const float2 d2 = __ffma2_rn(make_float2(eu, eu), make_float2(3.0f * W, -3.0f * W),
-                                         make_float2(even, even));                     // da, db
-            const float kw = diag ? kw2 : kw1;
-            const float en = edot<L>(a, nx, ny, nz), ef = edot<L>(a, frx, fry, frz);
-            const float2 fph2 = __fmul2_rn(make_float2(en, en), make_float2(kw, -kw));   // +-F^phi (1 - w/2)
-            const float2 hf2 = __fmul2_rn(make_float2(ef, ef), make_float2(W, -W));      // +-F_a / 2
-            float proj = -0.0f;
+            const V eu = edot_v<L>(a, ux, uy, uz);
+            const V even = O::fma(O::mul(O::s(4.5f * W), eu), eu, diag ? uw2 : uw1);
+            const V da = O::fma(O::s(3.0f * W), eu, even), db = O::fma(O::s(-3.0f * W), eu, even);
+            // F^phi_a (1 - w_phi / 2) = (e_a . grad phi) amp w_a (1 - w_phi / 2)
+            const V fph = O::mul(O::mul(edot_v<L>(a, dx, dy, dz), amp), O::s(diag ? kw2 : kw1));
+            const V ef = O::mul(edot_v<L>(a, Fx, Fy, Fz), fr);          // F_a / 2 = ef w_a
+            V proj = O::s(-0.0f);
 #pragma unroll
             for (int k = 0; k < L::NS; ++k)
-                if (L::m(k, a)) proj = fmaf(L::rw(k, a), ck[k], proj);
-            const float phw = diag ? phw2 : phw1, pw = diag ? pw2 : pw1;
-            const float2 geq2 = __ffma2_rn(make_float2(phi, phi), d2, make_float2(phw, phw));
-            const float2 feq2 = __fadd2_rn(make_float2(pw, pw), d2);
-            sg += geq2.x;
-            sf += feq2.x;
-            sg += geq2.y;
-            sf += feq2.y;
-            const float2 fo2 = __fadd2_rn(feq2, __fadd2_rn(make_float2(proj, proj), hf2));
-            const float2 gi2 = __ffma2_rn(make_float2(om, om), geq2, fph2);
-            const float2 go2 = __ffma2_rn(make_float2(om1, om1), make_float2(ga(a), ga(b)), gi2);
-            emit(a, fo2.x, go2.x);
-            emit(b, fo2.y, go2.y);
+                if (L::m(k, a)) proj = O::fma(O::s(L::rw(k, a)), ck[k], proj);
+            const V phw = diag ? phw2 : phw1;
+            {
+                const V geq = O::fma(phi, da, phw);
+                const V feq = O::fma(pstar, O::s(W), da);
+                sg = O::add(sg, geq);
+                sf = O::add(sf, feq);
+                emit(a, O::add(feq, O::fma(ef, O::s(W), proj)), O::fma(O::s(om1), ga(a), O::fma(O::s(om), geq, fph)));
+            }
+            {
+                const V geq = O::fma(phi, db, phw);
+                const V feq = O::fma(pstar, O::s(W), db);
+                sg = O::add(sg, geq);
+                sf = O::add(sf, feq);
+                emit(b, O::add(feq, O::fma(ef, O::s(-W), proj)), O::fma(O::s(om1), ga(b), O::fma(O::s(om), geq, O::neg(fph))));
+            }
         }
-        emit(0, pstar - sf, fmaf(om1, ga(0), om * (phi - sg)));
+        emit(0, O::sub(pstar, sf), O::fma(O::s(om1), ga(0), O::mul(O::s(om), O::sub(phi, sg))));
     }
 }
 
@@ -715,6 +832,136 @@ __device__ __forceinline__ float phi_at(const DevParams& P, const typename S::T*
     return s;
 }
 
+// Push map of one node and plane of the fused step: element offsets o of
+// the steps -1, +1 along each axis (wrapped on periodic faces; a step along y
+// or the march axis moves whole 32-node blocks, so its offset is the node
+// step times Q), the directions pushed back into the node (walls, open faces:
+// the face rules overwrite those), the free-slip directions per axis, and
+// the f references of the planes mm - 1, mm, mm + 1 of the march axis.
+struct PushMap {
+    uint32_t o[3][2];
+    uint32_t wall, slip[3], off;
+    float r[3];
+};
+
+// Element that the push of direction a from the node at element e0 writes
+// (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g, eq:free_slip_f/g):
+// the neighbour's slot a (push_plain: no face behind a, the usual case, with
+// periodic wraps in the offsets), this node's slot abar (wall or open face),
+// or the tangential neighbour's mirrored slot (free slip).
+template <class L>
+__device__ __forceinline__ uint32_t push_plain(const PushMap& M, uint32_t e0, int a)
+{
+    uint32_t t = e0;
+    if (L::ex(a)) t += M.o[0][L::ex(a) > 0];
+    if (L::ey(a)) t += M.o[1][L::ey(a) > 0];
+    if (L::D == 3 && L::ez(a)) t += M.o[2][L::ez(a) > 0];
+    return t + 32u * a;
+}
+template <class L>
+__device__ __forceinline__ uint32_t push_target(const PushMap& M, uint32_t e0, int a)
+{
+    const uint32_t bit = 1u << a;
+    if (!(M.off & bit)) return push_plain<L>(M, e0, a);
+    if (M.wall & bit) return e0 + 32u * L::opp(a);
+    const int m = int((M.slip[0] >> a) & 1u) | int((M.slip[1] >> a) & 1u) << 1 | int((M.slip[2] >> a) & 1u) << 2;
+    uint32_t t = e0;
+    if (L::ex(a) && !(m & 1)) t += M.o[0][L::ex(a) > 0];
+    if (L::ey(a) && !(m & 2)) t += M.o[1][L::ey(a) > 0];
+    if (L::D == 3 && L::ez(a) && !(m & 4)) t += M.o[2][L::ez(a) > 0];
+    return t + 32u * mirrored<L>(a, m);
+}
+// f reference of the node that the push of direction a reaches (the element
+// the push writes belongs to it after streaming): the plane one step along
+// the march component of a, or this node's plane where a wall, an open face
+// or a free-slip face of the march axis keeps the push in it.
+template <class L>
+__device__ __forceinline__ float push_ref_plain(const PushMap& M, int a)
+{
+    return M.r[1 + ((L::D == 3) ? L::ez(a) : L::ey(a))];
+}
+template <class L>
+__device__ __forceinline__ float push_ref(const PushMap& M, int a)
+{
+    if ((M.wall | M.slip[L::D - 1]) & (1u << a)) return M.r[1];
+    return push_ref_plain<L>(M, a);
+}
+
+// The in-plane part of a node's push map (x, and y in 3D), invariant along
+// the march: the directions behind a wall or open face or a free-slip face at
+// the node's x (y), and the element offsets of the steps -1 and +1 along x
+// (y).  Along x the offset depends only on the lane x mod 32 (a node
+// n = 32 B + r moves to n + s; the offset is taken on the block B = 1), and
+// uint32 arithmetic is modular, so the periodic wrap s = -(nx - 1) gives the
+// right offset too.  A step along y moves whole blocks.
+template <class L>
+__device__ __forceinline__ void inplane_push(const DevParams& P, int x, int y, PushMap& H)
+{
+    constexpr int Q = L::Q;
+    H.wall = 0u;
+    H.slip[0] = H.slip[1] = H.slip[2] = 0u;
+    H.o[0][0] = H.o[0][1] = H.o[1][0] = H.o[1][1] = H.o[2][0] = H.o[2][1] = 0u;
+    constexpr int DI = (L::D == 3) ? 2 : 1;
+    const int pos[2] = {x, y};
+    const int len[2] = {P.nx, P.ny};
+#pragma unroll
+    for (int d = 0; d < DI; ++d) {
+        int sm = -1, sp = 1;
+        const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
+        if (pos[d] == 0) {
+            if (lo == BC_PERIODIC) sm = len[d] - 1;
+            else if (lo == BC_FREESLIP) H.slip[d] |= dirmask<L>(d, -1);
+            else H.wall |= dirmask<L>(d, -1);
+        }
+        if (pos[d] == len[d] - 1) {
+            if (hi == BC_PERIODIC) sp = -(len[d] - 1);
+            else if (hi == BC_FREESLIP) H.slip[d] |= dirmask<L>(d, 1);
+            else H.wall |= dirmask<L>(d, 1);
+        }
+        if (d == 0) {
+            const uint32_t nx0 = uint32_t(x & 31);
+            H.o[0][0] = pel<L>(nx0 + 32u + uint32_t(sm)) - pel<L>(nx0 + 32u);
+            H.o[0][1] = pel<L>(nx0 + 32u + uint32_t(sp)) - pel<L>(nx0 + 32u);
+        } else {
+            H.o[1][0] = uint32_t(sm) * uint32_t(P.nxp) * uint32_t(Q);
+            H.o[1][1] = uint32_t(sp) * uint32_t(P.nxp) * uint32_t(Q);
+        }
+    }
+}
+
+// The march-axis part of the push map of plane mm (its offsets, face bits
+// and the plane references); M.off is formed from all face bits.
+template <class L, class S>
+__device__ __forceinline__ void march_push(const DevParams& P, int mm, PushMap& M)
+{
+    constexpr int d = L::D - 1;                 // the march axis
+    const int nm = (L::D == 3) ? P.nz : P.ny;
+    const uint32_t nstep = (L::D == 3) ? uint32_t(P.nxp) * uint32_t(P.ny) : uint32_t(P.nxp);
+    int sm = -1, sp = 1;                        // node steps in units of the axis
+    const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
+    if (mm == 0) {
+        if (lo == BC_PERIODIC) sm = nm - 1;
+        else if (lo == BC_FREESLIP) M.slip[d] |= dirmask<L>(d, -1);
+        else M.wall |= dirmask<L>(d, -1);
+    }
+    if (mm == nm - 1) {
+        if (hi == BC_PERIODIC) sp = -(nm - 1);
+        else if (hi == BC_FREESLIP) M.slip[d] |= dirmask<L>(d, 1);
+        else M.wall |= dirmask<L>(d, 1);
+    }
+    M.o[d][0] = uint32_t(sm) * nstep * uint32_t(L::Q);
+    M.o[d][1] = uint32_t(sp) * nstep * uint32_t(L::Q);
+    M.off = M.wall | M.slip[0] | M.slip[1] | M.slip[2];
+    if constexpr (S::kRef) {
+        // a push across a non-periodic face stays in plane mm
+        M.r[1] = fref<S>(P, mm);
+        M.r[0] = (mm > 0 || lo == BC_PERIODIC) ? fref<S>(P, mm + sm) : M.r[1];
+        M.r[2] = (mm < nm - 1 || hi == BC_PERIODIC) ? fref<S>(P, mm + sp) : M.r[1];
+    } else {
+        M.r[0] = M.r[1] = M.r[2] = 0.0f;
+    }
+}
+
 // Forms of the fused step.
 //  STEP_AB    A/B buffers: each node reads its own slots of A and pushes its
 //             post-collision populations into B (face rules on the push).
@@ -754,129 +1001,18 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
     const int x = x0 + tx, y = y0 + ty;
     const bool own = x < P.nx && ((L::D == 2) || y < P.ny);
 
-    // Push map of the in-plane axes (x, and y in 3D), invariant along the
-    // march: the directions behind a wall or open face (pushed back into this
-    // node's opposite slot; at open faces the face rules overwrite them) or a
-    // free-slip face at this node's x (y), and the element offsets of the
-    // steps -1 and +1 along x (y).  Along x the offset depends only on the
-    // lane x mod 32 (a node n = 32 B + r moves to n + s; the offset is taken
-    // on the block B = 1), and uint32 arithmetic is modular, so the periodic
-    // wrap s = -(nx - 1) gives the right offset too.  A step along y moves
-    // whole blocks.
-    uint32_t hwall = 0, hslip[2] = {0u, 0u};
-    uint32_t ho[2][2] = {{0u, 0u}, {0u, 0u}};
-    {
-        constexpr int DI = (L::D == 3) ? 2 : 1;
-        const int pos[2] = {x, y};
-        const int len[2] = {P.nx, P.ny};
-        const uint32_t nstep[2] = {1u, uint32_t(P.nxp)};
-#pragma unroll
-        for (int d = 0; d < DI; ++d) {
-            int sm = -1, sp = 1;
-            const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
-            if (pos[d] == 0) {
-                if (lo == BC_PERIODIC) sm = len[d] - 1;
-                else if (lo == BC_FREESLIP) hslip[d] |= dirmask<L>(d, -1);
-                else hwall |= dirmask<L>(d, -1);
-            }
-            if (pos[d] == len[d] - 1) {
-                if (hi == BC_PERIODIC) sp = -(len[d] - 1);
-                else if (hi == BC_FREESLIP) hslip[d] |= dirmask<L>(d, 1);
-                else hwall |= dirmask<L>(d, 1);
-            }
-            if (d == 0) {
-                const uint32_t nx0 = uint32_t(x & 31);
-                ho[0][0] = pel<L>(nx0 + 32u + uint32_t(sm)) - pel<L>(nx0 + 32u);
-                ho[0][1] = pel<L>(nx0 + 32u + uint32_t(sp)) - pel<L>(nx0 + 32u);
-            } else {
-                ho[1][0] = uint32_t(sm) * nstep[1] * uint32_t(Q);
-                ho[1][1] = uint32_t(sp) * nstep[1] * uint32_t(Q);
-            }
-        }
-    }
-
-    // The push map of plane mm: element offsets o of the steps along each
-    // axis (wrapped on periodic faces; a step along y or z moves whole
-    // 32-node blocks, so its offset is the node step times Q), the directions
-    // pushed back into the node (walls, open faces) and the free-slip
-    // directions per axis; the in-plane axes from the map above.
-    struct PushMap {
-        uint32_t o[3][2];
-        uint32_t wall, slip[3], off;
-        float r[3];             // f references of the planes mm - 1, mm, mm + 1 (wrapped)
-    };
+    // push map: the in-plane part once, the march-axis part per plane
+    PushMap H;
+    inplane_push<L>(P, x, y, H);
     auto push_map = [&](int mm) {
-        PushMap M;
-        M.wall = hwall;
-        M.slip[0] = hslip[0];
-        M.slip[1] = (L::D == 3) ? hslip[1] : 0u;
-        M.slip[2] = 0u;
-        M.o[0][0] = ho[0][0];
-        M.o[0][1] = ho[0][1];
-        M.o[1][0] = ho[1][0];
-        M.o[1][1] = ho[1][1];
-        constexpr int d = L::D - 1;             // the march axis
-        const uint32_t nstep = (L::D == 3) ? uint32_t(P.nxp) * uint32_t(P.ny) : uint32_t(P.nxp);
-        int sm = -1, sp = 1;                    // node steps in units of the axis
-        const int lo = P.bc[2 * d], hi = P.bc[2 * d + 1];
-        if (mm == 0) {
-            if (lo == BC_PERIODIC) sm = nm - 1;
-            else if (lo == BC_FREESLIP) M.slip[d] |= dirmask<L>(d, -1);
-            else M.wall |= dirmask<L>(d, -1);
-        }
-        if (mm == nm - 1) {
-            if (hi == BC_PERIODIC) sp = -(nm - 1);
-            else if (hi == BC_FREESLIP) M.slip[d] |= dirmask<L>(d, 1);
-            else M.wall |= dirmask<L>(d, 1);
-        }
-        M.o[d][0] = uint32_t(sm) * nstep * uint32_t(Q);
-        M.o[d][1] = uint32_t(sp) * nstep * uint32_t(Q);
-        M.off = M.wall | M.slip[0] | M.slip[1] | M.slip[2];
-        if constexpr (S::kRef) {
-            // a push across a non-periodic face stays in plane mm
-            M.r[1] = fref<S>(P, mm);
-            M.r[0] = (mm > 0 || lo == BC_PERIODIC) ? fref<S>(P, mm + sm) : M.r[1];
-            M.r[2] = (mm < nm - 1 || hi == BC_PERIODIC) ? fref<S>(P, mm + sp) : M.r[1];
-        } else {
-            M.r[0] = M.r[1] = M.r[2] = 0.0f;
-        }
+        PushMap M = H;
+        march_push<L, S>(P, mm, M);
         return M;
     };
-    // Element that the push of direction a from the node at element e0 writes
-    // (eq:streaming_f/g, eq:periodic_f/g, eq:no_slip_f/g, eq:free_slip_f/g):
-    // the neighbour's slot a (plain_target: no face behind a, the usual case,
-    // with periodic wraps in the offsets), this node's slot abar (wall or
-    // open face), or the tangential neighbour's mirrored slot (free slip).
-    auto plain_target = [&](const PushMap& M, uint32_t e0, int a) -> uint32_t {
-        uint32_t t = e0;
-        if (L::ex(a)) t += M.o[0][L::ex(a) > 0];
-        if (L::ey(a)) t += M.o[1][L::ey(a) > 0];
-        if (L::D == 3 && L::ez(a)) t += M.o[2][L::ez(a) > 0];
-        return t + 32u * a;
-    };
-    auto target = [&](const PushMap& M, uint32_t e0, int a) -> uint32_t {
-        const uint32_t bit = 1u << a;
-        if (!(M.off & bit)) return plain_target(M, e0, a);
-        if (M.wall & bit) return e0 + 32u * L::opp(a);
-        const int m = int((M.slip[0] >> a) & 1u) | int((M.slip[1] >> a) & 1u) << 1 | int((M.slip[2] >> a) & 1u) << 2;
-        uint32_t t = e0;
-        if (L::ex(a) && !(m & 1)) t += M.o[0][L::ex(a) > 0];
-        if (L::ey(a) && !(m & 2)) t += M.o[1][L::ey(a) > 0];
-        if (L::D == 3 && L::ez(a) && !(m & 4)) t += M.o[2][L::ez(a) > 0];
-        return t + 32u * mirrored<L>(a, m);
-    };
-    // f reference of the node that the push of direction a reaches (the
-    // element target / plain_target writes belongs to it after streaming):
-    // the plane one step along the march component of a, or this node's
-    // plane where a wall, an open face or a free-slip face of the march axis
-    // keeps the push in it.
-    auto plain_ref = [&](const PushMap& M, int a) -> float {
-        return M.r[1 + ((L::D == 3) ? L::ez(a) : L::ey(a))];
-    };
-    auto face_ref = [&](const PushMap& M, int a) -> float {
-        if ((M.wall | M.slip[L::D - 1]) & (1u << a)) return M.r[1];
-        return plain_ref(M, a);
-    };
+    auto plain_target = [&](const PushMap& M, uint32_t e0, int a) { return push_plain<L>(M, e0, a); };
+    auto target = [&](const PushMap& M, uint32_t e0, int a) { return push_target<L>(M, e0, a); };
+    auto plain_ref = [&](const PushMap& M, int a) { return push_ref_plain<L>(M, a); };
+    auto face_ref = [&](const PushMap& M, int a) { return push_ref<L>(M, a); };
 
     // phi of plane mm over the extended tile into window slot wslot; the
     // interior g of that plane goes to stash buffer (mm mod 2).  The
@@ -1024,6 +1160,192 @@ __device__ __forceinline__ void fused_item(const DevParams& P, const typename S:
     }
 }
 
+// ------------------------------------ fused A/B step, two nodes per thread
+//
+// The A/B step with each thread holding two x-adjacent nodes (x0 + 2t and
+// x0 + 2t + 1) in the two lanes of packed float32 instructions: the node
+// update runs once for both (node_update with V = float2), a population of
+// both nodes is one aligned 2-element load, and a push that does not move
+// along x is one aligned 2-element store (along x the two targets straddle a
+// pair boundary and are stored one by one).  Each lane's arithmetic is that
+// of fused_item, so the result is the same bits.  The tile is TX x TY nodes
+// on (TX / 2) x TY threads; the phi window rows start two columns left of
+// the tile, so that the pairs of the tile are 8-byte aligned.
+template <class L, int TX, int TY>
+struct Fused2Cfg {
+    static_assert(TX % 2 == 0, "node pairs");
+    static constexpr int EX = TX + 4;                   // columns -2 .. TX + 1
+    static constexpr int EY = (L::D == 3) ? TY + 2 : 1;
+    static constexpr int EXT = EX * EY;
+    static constexpr int NT = TX * ((L::D == 3) ? TY : 1);   // nodes of the tile
+    static constexpr int NTH = NT / 2;                        // threads
+    static constexpr size_t smem = sizeof(float) * (3 * EXT + 2 * L::Q * NT);
+};
+
+template <class L, class S, int TX, int TY>
+__device__ __forceinline__ void fused_item2(const DevParams& P, const typename S::T* __restrict__ fA,
+                                            const typename S::T* __restrict__ gA, typename S::T* __restrict__ fB,
+                                            typename S::T* __restrict__ gB, int x0, int y0, int m0, int m1,
+                                            float* smem)
+{
+    using Cfg = Fused2Cfg<L, TX, TY>;
+    using O = Lanes<float2>;
+    using T = typename S::T;
+    using T2 = typename S::T2;
+    constexpr int Q = L::Q, EX = Cfg::EX, EXT = Cfg::EXT, NT = Cfg::NT, NTH = Cfg::NTH;
+    float* win = smem;                    // [3][EY][EX]
+    float* stash = smem + 3 * EXT;        // [2][Q][NT]
+    const int tid = threadIdx.x + ((L::D == 3) ? threadIdx.y * (TX / 2) : 0);
+    const int tx = 2 * threadIdx.x, ty = (L::D == 3) ? threadIdx.y : 0;   // tile column of node 0
+    const int nm = (L::D == 3) ? P.nz : P.ny;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool own0 = x < P.nx && ((L::D == 2) || y < P.ny);
+    const bool own1 = own0 && x + 1 < P.nx;
+    const int nid = ty * TX + tx;                                       // stash column of node 0
+    const int wc = (ty + ((L::D == 3) ? 1 : 0)) * EX + tx + 2;          // window index of node 0
+
+    PushMap H0, H1;                       // in-plane push maps of the two nodes
+    inplane_push<L>(P, x, y, H0);
+    inplane_push<L>(P, x + 1, y, H1);
+
+    // phi of plane mm over the extended tile into window slot wslot, and the
+    // interior g of that plane into stash buffer (mm mod 2), as in fused_item
+    const int wx = min(TX, P.nx - x0), wy = (L::D == 3) ? min(TY, P.ny - y0) : 1;
+    const int nh = (L::D == 3) ? 2 * (wx + 2) + 2 * wy : 2;
+    auto fill = [&](int mm, float* wslot, bool keep) {
+        float* sbuf = stash + (mm & 1) * Q * NT;
+        if (own0) {
+            float2 v;
+            if (mm >= 0 && mm < nm) {
+                const uint32_t e0 = pel<L>((L::D == 3) ? pnode(P, x, y, mm) : pnode(P, x, mm, 0));
+                const T2* gb = reinterpret_cast<const T2*>(gA + e0);
+                float2 sacc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    const float2 gv = S::g2(__ldg(gb + 16 * a), L::w(a));
+                    if (keep) *reinterpret_cast<float2*>(sbuf + nid + a * NT) = gv;
+                    sacc = O::add(sacc, gv);
+                }
+                v = sacc;
+            } else {
+                v.x = phi_at<L, S>(P, gA, x, y, mm, keep ? sbuf + nid : nullptr, NT);
+                v.y = own1 ? phi_at<L, S>(P, gA, x + 1, y, mm, keep ? sbuf + nid + 1 : nullptr, NT) : 0.0f;
+            }
+            if (own1) *reinterpret_cast<float2*>(wslot + wc) = v;
+            else wslot[wc] = v.x;
+        }
+        for (int h = tid; h < nh; h += NTH) {
+            int px, py;
+            if (L::D == 2) {
+                px = h ? wx + 1 : 0;
+                py = 0;
+            } else if (h < wx + 2) {
+                px = h;
+                py = 0;
+            } else if (h < 2 * (wx + 2)) {
+                px = h - (wx + 2);
+                py = wy + 1;
+            } else {
+                px = ((h - 2 * (wx + 2)) & 1) ? wx + 1 : 0;
+                py = 1 + ((h - 2 * (wx + 2)) >> 1);
+            }
+            const int hx = x0 - 1 + px, hy = (L::D == 3) ? y0 - 1 + py : 0;
+            wslot[py * EX + px + 1] = phi_at<L, S>(P, gA, hx, hy, mm, nullptr, 0);
+        }
+    };
+
+    float* wlo = win;
+    float* wmid = win + EXT;
+    float* whi = win + 2 * EXT;
+    __syncthreads();
+    fill(m0 - 1, wlo, false);
+    fill(m0, wmid, true);
+    for (int m = m0; m < m1; ++m) {
+        fill(m + 1, whi, m + 1 < m1);
+        __syncthreads();
+        if (own0) {
+            const float* sbuf = stash + (m & 1) * Q * NT + nid;
+            const int z = (L::D == 3) ? m : 0;
+            const int yc = (L::D == 3) ? y : m;
+            const bool inlet_node = m == 0 && P.bc[(L::D == 3) ? 4 : 2] == BC_INLET;
+            const uint32_t e0 = pel<L>(pnode(P, x, yc, z));
+            PushMap M0 = H0, M1 = H1;
+            march_push<L, S>(P, m, M0);
+            march_push<L, S>(P, m, M1);
+            auto ga = [sbuf](int a) { return *reinterpret_cast<const float2*>(sbuf + a * NT); };
+            // phi at x + e_a of both nodes from the aligned pairs of the row
+            // (A = columns -2, -1 of node 0, B = 0, 1, C = 2, 3)
+            auto pa = [wlo, wmid, whi, wc](int a) -> float2 {
+                const int dm = (L::D == 3) ? L::ez(a) : L::ey(a);
+                const int dy = (L::D == 3) ? L::ey(a) : 0;
+                const float* r = (dm < 0 ? wlo : (dm > 0 ? whi : wmid)) + wc + dy * EX;
+                const float2 B = *reinterpret_cast<const float2*>(r);
+                if (L::ex(a) == 0) return B;
+                if (L::ex(a) < 0) {
+                    const float2 A = *reinterpret_cast<const float2*>(r - 2);
+                    return make_float2(A.y, B.x);
+                }
+                const float2 C = *reinterpret_cast<const float2*>(r + 2);
+                return make_float2(B.y, C.x);
+            };
+            const T2* fp = reinterpret_cast<const T2*>(fA + e0);
+            const float rm = M0.r[1];
+            auto fa = [&P, fp, rm](int a) { return S::f2(__ldg(fp + 16 * a), L::w(a), rm, P); };
+            // no face behind any direction of the warp's nodes: a push along
+            // y or the march axis is one pair store, one along x two stores
+            auto push_plain2 = [&P, fB, gB, e0, own1, M0, M1](int a, float2 fs, float2 gs) {
+                const float wa = L::w(a);
+                const T2 fe = S::ef2(fs, wa, push_ref_plain<L>(M0, a), P), ge = S::eg2(gs, wa);
+                const uint32_t t0 = push_plain<L>(M0, e0, a);
+                if (L::ex(a) == 0 && own1) {
+                    *reinterpret_cast<T2*>(fB + t0) = fe;
+                    *reinterpret_cast<T2*>(gB + t0) = ge;
+                } else {
+                    fB[t0] = S::lo(fe);
+                    gB[t0] = S::lo(ge);
+                    if (own1) {
+                        const uint32_t t1 = (L::ex(a) == 0) ? t0 + 1u : push_plain<L>(M1, e0 + 1u, a);
+                        fB[t1] = S::hi(fe);
+                        gB[t1] = S::hi(ge);
+                    }
+                }
+            };
+            if (__all_sync(__activemask(), (M0.off | M1.off) == 0u)) {
+                node_update<L, true, float2>(P, fa, ga, pa, inlet_node, nullptr, push_plain2);
+            } else {
+                // some node of the warp has a face behind a direction: the two
+                // nodes one after the other through the scalar update, each
+                // with its own push map (the same arithmetic per node)
+#pragma unroll 1
+                for (int k = 0; k < 2; ++k) {
+                    if (k == 1 && !own1) break;
+                    PushMap Mk = k ? H1 : H0;
+                    march_push<L, S>(P, m, Mk);
+                    const uint32_t ek = e0 + uint32_t(k);
+                    auto fak = [&](int a) { return S::f(__ldg(fA + ek + 32 * a), L::w(a), rm, P); };
+                    auto gak = [&](int a) { return sbuf[a * NT + k]; };
+                    auto pak = [&](int a) {
+                        const int dm = (L::D == 3) ? L::ez(a) : L::ey(a);
+                        const int dy = (L::D == 3) ? L::ey(a) : 0;
+                        return (dm < 0 ? wlo : (dm > 0 ? whi : wmid))[wc + k + dy * EX + L::ex(a)];
+                    };
+                    auto pushk = [&](int a, float fs, float gs) {
+                        const uint32_t t = push_target<L>(Mk, ek, a);
+                        fB[t] = S::ef(fs, L::w(a), push_ref<L>(Mk, a), P);
+                        gB[t] = S::eg(gs, L::w(a));
+                    };
+                    node_update<L, true>(P, fak, gak, pak, inlet_node, nullptr, pushk);
+                }
+            }
+        }
+        __syncthreads();
+        float* t = wlo;
+        wlo = wmid;
+        wmid = whi;
+        whi = t;
+    }
+}
+
 // phi pre-pass of the in-place step: phi = sum_a g_a of every node into
 // P.phis (unpadded node order) from the state in either form (par: swapped).
 // One thread per node of an x row (grid: rows y, planes z); interior nodes of
@@ -1110,7 +1432,7 @@ constexpr int fused_min_blocks() { return (L::D == 3) ? 768 / NT : 1024 / NT; }
 template <class L, int NT, int MODE>
 constexpr int inplace_min_blocks() { return (L::D == 3 && MODE == STEP_ODD) ? 576 / NT : fused_min_blocks<L, NT>(); }
 
-// The fused step, A/B form: fA, gA -> fB, gB.
+// The fused step, A/B form: fA, gA -> fB, gB, one node per thread.
 template <class L, class S, int TX, int TY>
 __global__ void __launch_bounds__(TX *((L::D == 3) ? TY : 1), (fused_min_blocks<L, TX *((L::D == 3) ? TY : 1)>()))
 k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typename S::T* __restrict__ fA,
@@ -1124,6 +1446,23 @@ k_step_fused(const __grid_constant__ DevParams P, const FusedGeom G, const typen
         const int y0 = (L::D == 3) ? (tile / G.tiles_x) * TY : 0;
         const int m0 = seg * G.seglen;
         fused_item<L, S, TX, TY, STEP_AB>(P, fA, gA, fB, gB, x0, y0, m0, min(m0 + G.seglen, nm), smem);
+    }
+}
+
+// The fused step, A/B form, two nodes per thread (MINB resident blocks).
+template <class L, class S, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(Fused2Cfg<L, TX, TY>::NTH, MINB)
+k_step_fused2(const __grid_constant__ DevParams P, const FusedGeom G, const typename S::T* __restrict__ fA,
+              const typename S::T* __restrict__ gA, typename S::T* __restrict__ fB, typename S::T* __restrict__ gB)
+{
+    extern __shared__ float smem[];
+    const int nm = (L::D == 3) ? P.nz : P.ny;
+    for (int item = blockIdx.x; item < G.items; item += gridDim.x) {
+        const int tile = item % G.ntiles, seg = item / G.ntiles;
+        const int x0 = (tile % G.tiles_x) * TX;
+        const int y0 = (L::D == 3) ? (tile / G.tiles_x) * TY : 0;
+        const int m0 = seg * G.seglen;
+        fused_item2<L, S, TX, TY>(P, fA, gA, fB, gB, x0, y0, m0, min(m0 + G.seglen, nm), smem);
     }
 }
 
@@ -1819,21 +2158,47 @@ template <class L> struct FusedTile;
 template <> struct FusedTile<D2Q9> { static constexpr int TX = 64, TY = 1; };
 template <> struct FusedTile<D3Q19> { static constexpr int TX = 32, TY = 6; };
 
+// The A/B step of each lattice and storage format: PAIR, two nodes per
+// thread (fused_item2) or one (fused_item), the tile and, for pairs, the
+// resident blocks per SM (a thread's register budget is 64 K / (threads x
+// blocks)).  Measured on the 3D jet and the 2D Rayleigh-Taylor workloads:
+// pairs gain with 16-bit storage (9 % on the jet, 14 % on Rayleigh-Taylor,
+// fewer instructions per update where the step is bound by issue), not with
+// float32, where the step is bound by memory latency and one node per thread
+// keeps twice the warps resident.
+template <class L, class S> struct ABStep {
+    static constexpr bool PAIR = !std::is_same<S, StoreF32>::value;
+    static constexpr int TX = PAIR ? 64 : FusedTile<L>::TX;
+    static constexpr int TY = (L::D == 2) ? 1 : (PAIR ? 4 : FusedTile<L>::TY);
+    static constexpr int MINB = (L::D == 2) ? 20 : 4;
+};
+
 template <class L, class S>
 cudaError_t Launch<L, S>::fused_geom(const DevParams& P, FusedGeom* G, int* nblocks, bool inplace)
 {
     constexpr int TX = FusedTile<L>::TX, TY = FusedTile<L>::TY;
+    using AB = ABStep<L, S>;
+    constexpr int TX2 = AB::TX, TY2 = AB::TY;
     using Cfg = FusedCfg<L, TX, TY>;
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if (!inplace) {
-        auto kern = k_step_fused<L, S, TX, TY>;
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg::smem))) != cudaSuccess)
-            return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::NT, Cfg::smem)) != cudaSuccess)
-            return e;
+        // the A/B step of this format: two nodes per thread, or one
+        auto occupancy = [&](auto kern, int threads, size_t smem) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+            return r;
+        };
+        if constexpr (AB::PAIR) {
+            using Cfg2 = Fused2Cfg<L, TX2, TY2>;
+            e = occupancy(k_step_fused2<L, S, TX2, TY2, AB::MINB>, Cfg2::NTH, Cfg2::smem);
+        } else {
+            using Cfg1 = FusedCfg<L, TX2, TY2>;
+            e = occupancy(k_step_fused<L, S, TX2, TY2>, Cfg1::NT, Cfg1::smem);
+        }
+        if (e != cudaSuccess) return e;
     } else {
         // the fewer resident blocks of the two forms
         auto ke = k_step_inplace<L, S, TX, TY, STEP_EVEN>;
@@ -1849,8 +2214,9 @@ cudaError_t Launch<L, S>::fused_geom(const DevParams& P, FusedGeom* G, int* nblo
     }
     per_sm = per_sm < 1 ? 1 : per_sm;
     const int slots = sms * per_sm;
-    G->tiles_x = (P.nx + TX - 1) / TX;
-    G->tiles_y = (L::D == 3) ? (P.ny + TY - 1) / TY : 1;
+    const int tx = inplace ? TX : TX2, ty = inplace ? TY : TY2;
+    G->tiles_x = (P.nx + tx - 1) / tx;
+    G->tiles_y = (L::D == 3) ? (P.ny + ty - 1) / ty : 1;
     G->ntiles = G->tiles_x * G->tiles_y;
     const int nm = (L::D == 3) ? P.nz : P.ny;
     // segments: the count that maximises the useful share of the slots'
@@ -1900,7 +2266,16 @@ cudaError_t Launch<L, S>::step_timed(const DevParams& P, const FusedGeom& G, int
     int par = 0;                                    // layout of the state after the step
     if (!b.inplace) {
         if ((e = mark()) != cudaSuccess) return e;  // no separate phi pass in the A/B step
-        k_step_fused<L, S, TX, TY><<<nblocks, blk, Cfg::smem, s>>>(P, G, fA, gA, fB, gB);
+        using AB = ABStep<L, S>;
+        if constexpr (AB::PAIR) {
+            using Cfg2 = Fused2Cfg<L, AB::TX, AB::TY>;
+            const dim3 blk2(AB::TX / 2, (L::D == 3) ? AB::TY : 1);
+            k_step_fused2<L, S, AB::TX, AB::TY, AB::MINB><<<nblocks, blk2, Cfg2::smem, s>>>(P, G, fA, gA, fB, gB);
+        } else {
+            using Cfg1 = FusedCfg<L, AB::TX, AB::TY>;
+            const dim3 blk1(AB::TX, (L::D == 3) ? AB::TY : 1);
+            k_step_fused<L, S, AB::TX, AB::TY><<<nblocks, blk1, Cfg1::smem, s>>>(P, G, fA, gA, fB, gB);
+        }
     } else {
         // phi pre-pass into P.phis, then the even (natural -> swapped) or the
         // odd (swapped -> natural) in-place form
