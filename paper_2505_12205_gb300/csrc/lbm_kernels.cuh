@@ -395,6 +395,21 @@ __device__ __forceinline__ V edot_v(int a, V vx, V vy, V vz)
     return s;
 }
 
+// a + b and a - b.  One node's (V = float): both in one packed fma,
+// fma(b, +-1, a), which rounds each lane as the add and the subtraction do.
+template <class V>
+__device__ __forceinline__ void sum_diff(V a, V b, V& s, V& d)
+{
+    if constexpr (std::is_same<V, float>::value) {
+        const float2 sd = __ffma2_rn(make_float2(b, b), make_float2(1.0f, -1.0f), make_float2(a, a));
+        s = sd.x;
+        d = sd.y;
+    } else {
+        s = Lanes<V>::add(a, b);
+        d = Lanes<V>::sub(a, b);
+    }
+}
+
 // Macroscopic update and collision of one node (V = float) or of two nodes
 // (V = float2, one per lane), written as a stream over the populations so
 // that no per-population output array has to live in registers:
@@ -433,9 +448,9 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
     for (int a = 1; a < Q; ++a) {
         if (L::opp(a) < a) continue;
         const int c = wclass<L>(a);
-        const V va = pa(a), vb = pa(L::opp(a));
-        const V dp = O::sub(va, vb);
-        lps[c] = O::add(lps[c], O::fma(O::s(-2.0f), phi, O::add(va, vb)));   // (phi_a - phi) + (phi_abar - phi)
+        V sp, dp;
+        sum_diff(pa(a), pa(L::opp(a)), sp, dp);
+        lps[c] = O::add(lps[c], O::fma(O::s(-2.0f), phi, sp));   // (phi_a - phi) + (phi_abar - phi)
         if (L::ex(a)) gxs[c] = L::ex(a) > 0 ? O::add(gxs[c], dp) : O::sub(gxs[c], dp);
         if (L::ey(a)) gys[c] = L::ey(a) > 0 ? O::add(gys[c], dp) : O::sub(gys[c], dp);
         if (L::ez(a)) gzs[c] = L::ez(a) > 0 ? O::add(gzs[c], dp) : O::sub(gzs[c], dp);
@@ -481,8 +496,8 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
         for (int a = 1; a < Q; ++a) {
             if (L::opp(a) < a) continue;
             const int ex = L::ex(a), ey = L::ey(a), ez = L::ez(a);
-            const V va = fa(a), vb = fa(L::opp(a));
-            const V s = O::add(va, vb), d = O::sub(va, vb);
+            V s, d;
+            sum_diff(fa(a), fa(L::opp(a)), s, d);
             pstar = O::add(pstar, s);
             if (ex) jx = ex > 0 ? O::add(jx, d) : O::sub(jx, d);
             if (ey) jy = ey > 0 ? O::add(jy, d) : O::sub(jy, d);
@@ -612,6 +627,23 @@ __device__ __forceinline__ void node_update(const DevParams& P, FA fa, GA ga, PA
             for (int k = 0; k < L::NS; ++k)
                 if (L::m(k, a)) proj = O::fma(O::s(L::rw(k, a)), ck[k], proj);
             const V phw = diag ? phw2 : phw1;
+            if constexpr (std::is_same<V, float>::value) {
+                // one node: a and b in the two lanes of packed operations,
+                // each lane the operation of the general form below
+                const float2 d2 = __ffma2_rn(make_float2(eu, eu), make_float2(3.0f * W, -3.0f * W), make_float2(even, even));
+                const float2 geq2 = __ffma2_rn(make_float2(phi, phi), d2, make_float2(phw, phw));
+                const float2 feq2 = __ffma2_rn(make_float2(pstar, pstar), make_float2(W, W), d2);
+                sg = O::add(sg, geq2.x);
+                sf = O::add(sf, feq2.x);
+                sg = O::add(sg, geq2.y);
+                sf = O::add(sf, feq2.y);
+                const float2 fo2 = __fadd2_rn(feq2, __ffma2_rn(make_float2(ef, ef), make_float2(W, -W), make_float2(proj, proj)));
+                const float2 gi2 = __ffma2_rn(make_float2(om, om), geq2, make_float2(fph, O::neg(fph)));
+                const float2 go2 = __ffma2_rn(make_float2(om1, om1), make_float2(ga(a), ga(b)), gi2);
+                emit(a, fo2.x, go2.x);
+                emit(b, fo2.y, go2.y);
+                continue;
+            }
             {
                 const V geq = O::fma(phi, da, phw);
                 const V feq = O::fma(pstar, O::s(W), da);
@@ -1427,10 +1459,18 @@ __global__ void __launch_bounds__(128) k_phi_pre(const __grid_constant__ DevPara
 template <class L, int NT>
 constexpr int fused_min_blocks() { return (L::D == 3) ? 768 / NT : 1024 / NT; }
 
-// The odd in-place form gathers its populations from 2Q different rows: for
-// D3Q19 it gets the registers of three resident blocks per SM (18 warps).
+// Tile of the in-place forms and the threads per SM each is compiled for:
+// the odd form gathers its populations from 2Q different rows and needs more
+// registers per thread than the even form (D3Q19: 128, four warps per SM
+// sub-partition, where the even form keeps 80).
+template <class L> struct InplaceTile;
+template <> struct InplaceTile<D2Q9> { static constexpr int TX = 64, TY = 1, ODD_THREADS = 1024; };
+template <> struct InplaceTile<D3Q19> { static constexpr int TX = 32, TY = 4, ODD_THREADS = 512; };
 template <class L, int NT, int MODE>
-constexpr int inplace_min_blocks() { return (L::D == 3 && MODE == STEP_ODD) ? 576 / NT : fused_min_blocks<L, NT>(); }
+constexpr int inplace_min_blocks()
+{
+    return MODE == STEP_ODD ? InplaceTile<L>::ODD_THREADS / NT : fused_min_blocks<L, NT>();
+}
 
 // The fused step, A/B form: fA, gA -> fB, gB, one node per thread.
 template <class L, class S, int TX, int TY>
@@ -2176,7 +2216,7 @@ template <class L, class S> struct ABStep {
 template <class L, class S>
 cudaError_t Launch<L, S>::fused_geom(const DevParams& P, FusedGeom* G, int* nblocks, bool inplace)
 {
-    constexpr int TX = FusedTile<L>::TX, TY = FusedTile<L>::TY;
+    constexpr int TX = InplaceTile<L>::TX, TY = InplaceTile<L>::TY;
     using AB = ABStep<L, S>;
     constexpr int TX2 = AB::TX, TY2 = AB::TY;
     using Cfg = FusedCfg<L, TX, TY>;
@@ -2255,7 +2295,7 @@ cudaError_t Launch<L, S>::step_timed(const DevParams& P, const FusedGeom& G, int
                                      cudaStream_t s, MarkFn markfn, void* mctx)
 {
     auto mark = [&]() { return markfn ? markfn(mctx) : cudaSuccess; };
-    constexpr int TX = FusedTile<L>::TX, TY = FusedTile<L>::TY;
+    constexpr int TX = InplaceTile<L>::TX, TY = InplaceTile<L>::TY;     // in-place forms
     using Cfg = FusedCfg<L, TX, TY>;
     const T* fA = static_cast<const T*>(b.fA);
     const T* gA = static_cast<const T*>(b.gA);
