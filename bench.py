@@ -360,7 +360,8 @@ def run_gpu(args):
     achieved = bytes_per_lu * N / (step_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS,
-            "traffic": ncu_traffic(args.workload) if (args.storage == "fp32" and not args.grid and not inplace) else None,
+            "traffic": (ncu_traffic(args.workload + ("" if args.storage == "fp32" else "_" + args.storage))
+                        if (args.storage in ("fp32", "fp16") and not args.grid and not inplace) else None),
             "kernel": kname,
             "phi_prepass_ms_per_step": ms_phi / max(nrec, 1),
             "algorithmic_bytes_per_lu": bytes_per_lu, "peak_source": peak_kind + " hbm_gbs",
