@@ -822,6 +822,7 @@ struct FusedGeom {
     int tiles_x, tiles_y, ntiles;
     int nseg, seglen;      // segments of the last axis
     int items;             // ntiles * nseg
+    int blocks_even;       // in-place layout: persistent blocks of the even form (0: as the odd form)
 };
 
 template <class L, int TX, int TY>
@@ -2216,6 +2217,7 @@ template <class L, class S> struct ABStep {
 template <class L, class S>
 cudaError_t Launch<L, S>::fused_geom(const DevParams& P, FusedGeom* G, int* nblocks, bool inplace)
 {
+    G->blocks_even = 0;
     constexpr int TX = InplaceTile<L>::TX, TY = InplaceTile<L>::TY;
     using AB = ABStep<L, S>;
     constexpr int TX2 = AB::TX, TY2 = AB::TY;
@@ -2251,6 +2253,7 @@ cudaError_t Launch<L, S>::fused_geom(const DevParams& P, FusedGeom* G, int* nblo
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pe, ke, Cfg::NT, Cfg::smem)) != cudaSuccess) return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&po, ko, Cfg::NT, Cfg::smem)) != cudaSuccess) return e;
         per_sm = pe < po ? pe : po;
+        G->blocks_even = sms * (pe < 1 ? 1 : pe);       // the even form fills its own occupancy
     }
     per_sm = per_sm < 1 ? 1 : per_sm;
     const int slots = sms * per_sm;
@@ -2321,7 +2324,8 @@ cudaError_t Launch<L, S>::step_timed(const DevParams& P, const FusedGeom& G, int
         // odd (swapped -> natural) in-place form
         k_phi_pre<L, S><<<dim3((P.nx + 127) / 128, P.ny, (L::D == 3) ? P.nz : 1), 128, 0, s>>>(P, gA, b.par, b.phi);
         if ((e = mark()) != cudaSuccess) return e;
-        if (b.par == 0) k_step_inplace<L, S, TX, TY, STEP_EVEN><<<nblocks, blk, Cfg::smem, s>>>(P, G, fB, gB);
+        const int ne = G.blocks_even > 0 ? (G.blocks_even < G.items ? G.blocks_even : G.items) : nblocks;
+        if (b.par == 0) k_step_inplace<L, S, TX, TY, STEP_EVEN><<<ne, blk, Cfg::smem, s>>>(P, G, fB, gB);
         else k_step_inplace<L, S, TX, TY, STEP_ODD><<<nblocks, blk, Cfg::smem, s>>>(P, G, fB, gB);
         par = b.par ^ 1;
     }
